@@ -1,0 +1,494 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Every test here runs on the CPU.  None of them re-uses the oracle's loop code to
+produce its expectation: each compares the oracle with a printed value, a closed
+form, an invariant, or an independent brute-force / dense linear-algebra
+evaluation written in this file.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- kernels
+
+def _golden_kernel_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "delta_kernel_values.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, r, _expr, val = line.split(None, 3)
+            rows.append((k, float(r), float(val)))
+    return rows
+
+
+@pytest.mark.parametrize("kernel,r,value", _golden_kernel_rows())
+def test_kernel_breakpoints(oracle, kernel, r, value):
+    # Eq. (3pt-stencil) and Eq. (4pt-stencil), values worked by hand.
+    f = oracle.phi3 if kernel == "phi3" else oracle.phi4
+    assert f(r) == pytest.approx(value, abs=2e-16)
+
+
+@pytest.mark.parametrize("kernel", ["phi3", "phi4"])
+def test_kernel_continuity(oracle, kernel):
+    f = oracle.phi3 if kernel == "phi3" else oracle.phi4
+    brk = [0.5, 1.5] if kernel == "phi3" else [1.0, 2.0]
+    for b in brk:
+        for s in (1, -1):
+            x = s * b
+            assert abs(f(x - 1e-12) - f(x + 1e-12)) < 1e-5
+
+
+def _moments(f, xi):
+    i = np.arange(-4, 5)
+    r = (i + 0.5) - xi
+    w = np.array([f(v) for v in r])
+    return i, r, w
+
+
+@pytest.mark.parametrize("kernel", ["phi3", "phi4"])
+def test_kernel_moments(oracle, kernel):
+    # Partition of unity (Sec. 2.2.3 for phi3 and phi4), zero first moment, and
+    # the sum-of-squares condition of the cited kernels (1/2 for Roma's
+    # three-point, 3/8 for Peskin's four-point).
+    f = oracle.phi3 if kernel == "phi3" else oracle.phi4
+    sq = 0.5 if kernel == "phi3" else 3.0 / 8.0
+    rng = np.random.default_rng(5)
+    for xi in rng.uniform(0.0, 1.0, size=2000):
+        i, r, w = _moments(f, xi)
+        assert abs(w.sum() - 1.0) < 1e-14
+        assert abs((r * w).sum()) < 1e-14
+        assert abs((w * w).sum() - sq) < 1e-14
+
+
+def test_phi4_even_odd(oracle):
+    # Sec. 2.2.3: sums over even and over odd cells are each 1/2 for phi4 ...
+    rng = np.random.default_rng(6)
+    for xi in rng.uniform(0.0, 1.0, size=2000):
+        i, r, w = _moments(oracle.phi4, xi)
+        assert abs(w[i % 2 == 0].sum() - 0.5) < 1e-14
+        assert abs(w[i % 2 != 0].sum() - 0.5) < 1e-14
+
+
+def test_phi3_not_even_odd(oracle):
+    # ... while phi3 only satisfies the plain partition of unity.
+    i, r, w = _moments(oracle.phi3, 0.5)
+    assert abs(w[i % 2 == 0].sum() - 0.5) > 0.1
+
+
+@pytest.mark.parametrize("kernel", ["phi3", "phi4"])
+def test_kernel_derivative_fd(oracle, kernel):
+    f, df = (oracle.phi3, oracle.dphi3) if kernel == "phi3" else (oracle.phi4, oracle.dphi4)
+    rng = np.random.default_rng(7)
+    eps = 1e-6
+    for r in rng.uniform(-2.2, 2.2, size=500):
+        fd = (f(r + eps) - f(r - eps)) / (2 * eps)
+        assert abs(df(r) - fd) < 5e-6, (r, df(r), fd)
+
+
+def test_phi3_is_c1(oracle):
+    for b in (0.5, 1.5):
+        for s in (1, -1):
+            x = s * b
+            assert abs(oracle.dphi3(x - 1e-9) - oracle.dphi3(x + 1e-9)) < 1e-4
+
+
+# ----------------------------------------------------------------- markers
+
+@pytest.mark.parametrize("d,n", [(16.0, 804), (12.0, 452), (24.0, 1810)])
+def test_marker_counts(oracle, d, n):
+    # N_l = round(pi (d/h)^2): ~800 for D=16, ~450 for D=12, ~1800 for D=24.
+    assert oracle.marker_count(d, 1.0) == n
+
+
+@pytest.mark.parametrize("d,h", [(16.0, 1.0), (12.0, 1.0), (3.0, 0.25), (8.5, 0.5)])
+def test_marker_shell_volume(oracle, d, h):
+    # Sec. 2.1: N_l dV_l = (4/3) pi [(d/2 + h/2)^3 - (d/2 - h/2)^3], and dV_l ~ h^3.
+    nl = oracle.marker_count(d, h)
+    dv = oracle.marker_volume(d, h, nl)
+    shell = 4.0 / 3.0 * math.pi * ((d / 2 + h / 2) ** 3 - (d / 2 - h / 2) ** 3)
+    assert nl * dv == pytest.approx(shell, rel=1e-14)
+    assert dv / h ** 3 == pytest.approx(1.0, abs=0.02)
+
+
+@pytest.mark.parametrize("nl", [1, 2, 452, 804, 1810])
+def test_marker_dirs_unit_and_balanced(oracle, nl):
+    t = oracle.marker_dirs(nl)
+    assert np.allclose(np.linalg.norm(t, axis=1), 1.0, atol=1e-14)
+    assert abs(t[:, 2].sum()) < 1e-9
+    if nl > 100:
+        assert np.linalg.norm(t.mean(axis=0)) < 5.0 / nl
+
+
+@pytest.mark.parametrize("d", [12.0, 16.0, 24.0])
+def test_marker_spacing_is_h(oracle, d):
+    # Markers on a spiral lattice with spacing ~ h (the lattice of the workloads).
+    nl = oracle.marker_count(d, 1.0)
+    r = 0.5 * d * oracle.marker_dirs(nl)
+    dist = np.linalg.norm(r[:, None, :] - r[None, :, :], axis=-1)
+    np.fill_diagonal(dist, np.inf)
+    nn = dist.min(axis=1)
+    assert 0.8 < np.median(nn) < 1.2
+
+
+def test_marker_bases_are_floors(oracle):
+    x_p = np.array([[10.3, 7.9, 12.5], [30.0, 20.0, 5.25]])
+    d_p = np.array([8.0, 5.0])
+    xi, base = oracle.marker_positions(x_p, d_p)
+    assert np.array_equal(base, np.floor(xi).astype(np.int64))
+    # Independent reconstruction of the marker positions from the directions.
+    t0 = oracle.marker_dirs(oracle.marker_count(8.0))
+    assert np.allclose(xi[: len(t0)], x_p[0] + 4.0 * t0, atol=1e-13)
+
+
+# ------------------------------------------------- dense brute-force helpers
+
+def _dense_W(oracle, dims, x_p, d_p, kernel="phi3"):
+    """W[l, cell] built from delta at every cell with minimum-image distances."""
+    f = np.vectorize(oracle.phi3 if kernel == "phi3" else oracle.phi4)
+    nx, ny, nz = dims
+    xi, _ = oracle.marker_positions(x_p, d_p)
+    cz, cy, cx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    centres = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], 1) + 0.5
+    L = np.array([nx, ny, nz], dtype=float)
+    W = np.empty((xi.shape[0], centres.shape[0]))
+    for l in range(xi.shape[0]):
+        r = centres - xi[l]
+        r = r - L * np.floor(r / L + 0.5)
+        W[l] = f(r[:, 0]) * f(r[:, 1]) * f(r[:, 2])
+    return W
+
+
+def _small_problem(seed=3, dims=(10, 9, 11), n=2):
+    rng = np.random.default_rng(seed)
+    x_p = rng.uniform(0, 1, size=(n, 3)) * np.array(dims)
+    d_p = rng.uniform(1.2, 2.6, size=n)
+    u_p = rng.normal(0, 0.3, size=(n, 3))
+    om = rng.normal(0, 0.3, size=(n, 3))
+    u = rng.normal(0, 1, size=(3, dims[2], dims[1], dims[0]))
+    return x_p, d_p, u_p, om, u
+
+
+def test_stencil_equals_brute_force(oracle):
+    dims = (10, 9, 11)
+    x_p, d_p, u_p, om, u = _small_problem(dims=dims)
+    a = oracle.forcing_step(u, x_p, u_p, om, d_p, want_f=True)
+    b = oracle.forcing_step(u, x_p, u_p, om, d_p, want_f=True, brute=True)
+    for k in ("u", "F", "T", "f"):
+        assert np.allclose(a[k], b[k], rtol=0, atol=1e-12 * max(1.0, np.abs(b[k]).max()))
+
+
+def test_interp_matches_dense_W(oracle):
+    dims = (8, 9, 10)
+    x_p, d_p, u_p, om, u = _small_problem(seed=11, dims=dims, n=3)
+    W = _dense_W(oracle, dims, x_p, d_p)
+    U = oracle.interpolate(u, x_p, d_p)
+    Ud = np.stack([W @ u[c].ravel() for c in range(3)], 1)
+    assert np.allclose(U, Ud, atol=1e-13)
+
+
+def test_interp_constant_exact(oracle):
+    dims = (24, 20, 22)
+    x_p = np.array([[11.37, 9.91, 10.02]])
+    d_p = np.array([9.0])
+    u = np.empty((3, 22, 20, 24))
+    u[0], u[1], u[2] = 1.25, -3.5, 7.0
+    U = oracle.interpolate(u, x_p, d_p)
+    assert np.abs(U - np.array([1.25, -3.5, 7.0])).max() < 1e-14
+
+
+def test_interp_linear_exact(oracle):
+    # Zero first moment: a linear field is reproduced exactly away from the seam.
+    dims = (32, 32, 32)
+    x_p = np.array([[16.2, 15.7, 16.9]])
+    d_p = np.array([12.0])
+    z, y, x = np.meshgrid(*(np.arange(32) + 0.5,) * 3, indexing="ij")
+    A = np.array([[0.3, -1.2, 0.7], [2.0, 0.1, -0.4], [-0.5, 0.25, 1.5]])
+    b = np.array([0.2, -0.3, 1.1])
+    u = np.stack([A[c, 0] * x + A[c, 1] * y + A[c, 2] * z + b[c] for c in range(3)])
+    U = oracle.interpolate(u, x_p, d_p)
+    xi, _ = oracle.marker_positions(x_p, d_p)
+    assert np.abs(U - (xi @ A.T + b)).max() < 1e-12
+
+
+def test_interp_taylor_green_second_order(oracle):
+    # Taylor-Green field (Sec. 3.1) u = sin(kx x) cos(ky y), v = -cos(kx x) sin(ky y):
+    # the interpolation error decays as O(h^2).
+    L, k = 2.0, math.pi
+    errs = []
+    for n in (16, 32, 64):
+        h = L / n
+        c = (np.arange(n) + 0.5) * h
+        z, y, x = np.meshgrid(c, c, c, indexing="ij")
+        u = np.stack([np.sin(k * x) * np.cos(k * y), -np.cos(k * x) * np.sin(k * y), 0 * x])
+        x_p = np.array([[1.01, 0.97, 1.03]])
+        d_p = np.array([0.7])
+        U = oracle.interpolate(u, x_p, d_p, h=h)
+        xi, _ = oracle.marker_positions(x_p, d_p, h=h)
+        X = xi * h
+        ex = np.stack([np.sin(k * X[:, 0]) * np.cos(k * X[:, 1]),
+                       -np.cos(k * X[:, 0]) * np.sin(k * X[:, 1]), 0 * X[:, 0]], 1)
+        errs.append(np.abs(U - ex).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.2 < r1 < 5.0 and 3.2 < r2 < 5.0, errs
+
+
+def test_spread_is_weighted_adjoint(oracle):
+    # h^3 <W^T D F, v> = sum_l dV_l F_l . (W v)_l  (spreading is the D-weighted
+    # transpose of interpolation; Sec. 2.2.2 steps 1 and 3).
+    dims = (12, 10, 14)
+    h = 0.5
+    rng = np.random.default_rng(12)
+    x_p = rng.uniform(0, 1, size=(3, 3)) * np.array(dims) * h
+    d_p = np.array([2.0, 1.5, 2.5])
+    n = sum(oracle.marker_count(d, h) for d in d_p)
+    F = rng.normal(size=(n, 3))
+    v = rng.normal(size=(3, 14, 10, 12))
+    f = oracle.spread(F, dims, x_p, d_p, h=h)
+    Wv = oracle.interpolate(v, x_p, d_p, h=h)
+    dv = np.concatenate([[oracle.marker_volume(d, h)] * oracle.marker_count(d, h) for d in d_p])
+    lhs = h ** 3 * (f * v).sum()
+    rhs = (dv[:, None] * F * Wv).sum()
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+# ------------------------------------------------------- whole-loop pins
+
+def test_single_marker_closed_form(oracle):
+    # One marker (N_l = 1): sum_c w^2 = (sum phi3^2)^3 = 1/8, so each iteration
+    # multiplies the slip by (1 - D/8) exactly, and u^{n} - u^0 = w D sum_m e^m.
+    d = 0.56
+    assert oracle.marker_count(d) == 1
+    D = oracle.marker_volume(d, 1.0, 1)
+    q = 1.0 - D / 8.0
+    dims = (9, 8, 10)
+    rng = np.random.default_rng(21)
+    u0 = rng.normal(size=(3, 10, 8, 9))
+    x_p = np.array([[4.13, 3.77, 5.41]])
+    u_p = np.array([[0.4, -0.2, 0.9]])
+    om = np.array([[0.3, 0.1, -0.5]])
+    e1 = (u_p + np.cross(om, 0.5 * d * oracle.marker_dirs(1))) - oracle.interpolate(u0, x_p, [d])
+    W = _dense_W(oracle, dims, x_p, [d])[0]
+    for n in (1, 2, 3, 5):
+        out = oracle.forcing_step(u0, x_p, u_p, om, [d], n_forcing=n)
+        assert out["slip"][0] == pytest.approx(np.linalg.norm(e1) * q ** n, rel=1e-12)
+        geo = sum(q ** m for m in range(n))
+        du = np.stack([W * D * e1[0, c] * geo for c in range(3)]).reshape(u0.shape)
+        assert np.abs(out["u"] - u0 - du).max() < 1e-12
+
+
+def test_many_markers_dense_recursion(oracle):
+    # e^{m+1} = (I - W W^T D) e^m and u^{n} = u^0 + W^T D sum_m e^m, evaluated
+    # with dense numpy linear algebra on a tiny grid; F = e/tau; loads are
+    # sum_m sum_l F dV and sum_m sum_l r x F dV.
+    dims = (10, 9, 11)
+    x_p, d_p, u_p, om, u0 = _small_problem(seed=31, dims=dims, n=3)
+    tau, nf = 0.37, 3
+    W = _dense_W(oracle, dims, x_p, d_p)
+    counts = [oracle.marker_count(d) for d in d_p]
+    Dl = np.concatenate([[oracle.marker_volume(d)] * c for d, c in zip(d_p, counts)])
+    r = np.concatenate([0.5 * d * oracle.marker_dirs(c) for d, c in zip(d_p, counts)])
+    pid = np.repeat(np.arange(len(d_p)), counts)
+    Ud = u_p[pid] + np.cross(om[pid], r)
+    U0 = np.stack([W @ u0[c].ravel() for c in range(3)], 1)
+    e = Ud - U0
+    M = W @ W.T * Dl[None, :]
+    E = np.zeros_like(e)
+    for _ in range(nf):
+        E += e
+        e = e - M @ e
+    du = (W.T @ (Dl[:, None] * E)).T.reshape(u0.shape)
+    out = oracle.forcing_step(u0, x_p, u_p, om, d_p, n_forcing=nf, tau=tau)
+    assert np.abs(out["u"] - (u0 + du)).max() < 1e-12
+    Fp = np.zeros((3, 3)); Tp = np.zeros((3, 3))
+    np.add.at(Fp, pid, Dl[:, None] * E / tau)
+    np.add.at(Tp, pid, np.cross(r, Dl[:, None] * E / tau))
+    assert np.allclose(out["F"], Fp, rtol=1e-11, atol=1e-11)
+    assert np.allclose(out["T"], Tp, rtol=1e-11, atol=1e-11)
+    assert out["slip"][0] == pytest.approx(np.sqrt((np.linalg.norm(e, axis=1) ** 2).mean()), rel=1e-11)
+    assert out["slip"][1] == pytest.approx(np.linalg.norm(e, axis=1).max(), rel=1e-11)
+
+
+def test_tau_cancels_in_u(oracle):
+    dims = (10, 9, 11)
+    x_p, d_p, u_p, om, u0 = _small_problem(seed=41, dims=dims)
+    a = oracle.forcing_step(u0, x_p, u_p, om, d_p, tau=0.01)
+    b = oracle.forcing_step(u0, x_p, u_p, om, d_p, tau=0.5)
+    assert np.abs(a["u"] - b["u"]).max() < 1e-12
+    assert np.allclose(a["F"] * 0.01, b["F"] * 0.5, rtol=1e-10)
+
+
+def test_load_identities_isolated(oracle):
+    # Partition of unity: sum_c f_c h^3 = sum F dV.  Zero first moment: the
+    # Eulerian torque about x_p (minimum-image arms) equals sum r x F dV.
+    dims = (40, 36, 44)
+    h = 1.0
+    x_p = np.array([[19.3, 17.6, 21.9]])
+    d_p = np.array([12.0])
+    rng = np.random.default_rng(51)
+    u0 = rng.normal(size=(3, 44, 36, 40))
+    out = oracle.forcing_step(u0, x_p, [[0.1, 0.2, -0.3]], [[0.5, -0.2, 0.1]], d_p, want_f=True)
+    f = out["f"]
+    assert np.allclose(f.reshape(3, -1).sum(1) * h ** 3, out["F"][0], rtol=1e-11, atol=1e-8)
+    z, y, x = np.meshgrid(*(np.arange(n) + 0.5 for n in (44, 36, 40)), indexing="ij")
+    arm = np.stack([x - x_p[0, 0], y - x_p[0, 1], z - x_p[0, 2]])
+    L = np.array([40, 36, 44]).reshape(3, 1, 1, 1)
+    arm = arm - L * np.floor(arm / L + 0.5)
+    T = np.cross(arm.reshape(3, -1).T, f.reshape(3, -1).T).sum(0) * h ** 3
+    assert np.allclose(T, out["T"][0], rtol=1e-10, atol=1e-7)
+
+
+def test_noop_constant_field(oracle):
+    dims = (24, 24, 24)
+    x_p = np.array([[3.3, 12.0, 20.7]])   # crosses the periodic seam
+    d_p = np.array([10.0])
+    Up = np.array([[0.3, -0.7, 1.1]])
+    u0 = np.empty((3, 24, 24, 24))
+    for c in range(3):
+        u0[c] = Up[0, c]
+    out = oracle.forcing_step(u0, x_p, Up, np.zeros((1, 3)), d_p)
+    assert np.abs(out["F"]).max() < 1e-9
+    assert np.abs(out["u"] - u0).max() < 1e-13
+
+
+def test_noop_rigid_motion(oracle):
+    dims = (32, 32, 32)
+    x_p = np.array([[16.2, 15.8, 16.4]])
+    d_p = np.array([12.0])
+    Up = np.array([0.2, -0.1, 0.3])
+    om = np.array([0.05, -0.02, 0.04])
+    z, y, x = np.meshgrid(*(np.arange(32) + 0.5,) * 3, indexing="ij")
+    arm = np.stack([x - x_p[0, 0], y - x_p[0, 1], z - x_p[0, 2]], -1)
+    u0 = np.moveaxis(Up + np.cross(om, arm), -1, 0).copy()
+    out = oracle.forcing_step(u0, x_p, Up[None], om[None], d_p)
+    assert np.abs(out["F"]).max() < 1e-8
+    assert np.abs(out["u"] - u0).max() < 1e-12
+
+
+def test_integer_shift_invariance(oracle):
+    dims = (20, 18, 22)
+    x_p, d_p, u_p, om, u0 = _small_problem(seed=61, dims=dims, n=3)
+    d_p = d_p * 2
+    a = oracle.forcing_step(u0, x_p, u_p, om, d_p)
+    s = np.array([3, -5, 7])
+    xs = x_p + s
+    us = np.roll(u0, shift=(s[2], s[1], s[0]), axis=(1, 2, 3))
+    b = oracle.forcing_step(us, xs, u_p, om, d_p)
+    ub = np.roll(b["u"], shift=(-s[2], -s[1], -s[0]), axis=(1, 2, 3))
+    assert np.abs(ub - a["u"]).max() < 1e-11
+    assert np.allclose(a["F"], b["F"], rtol=1e-9, atol=1e-8)
+
+
+def test_touched_count_brute(oracle):
+    dims = (30, 28, 26)
+    x_p, d_p, *_ = _small_problem(seed=71, dims=dims, n=4)
+    d_p = d_p * 3
+    _, base = oracle.marker_positions(x_p, d_p)
+    cells = set()
+    for b in base:
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    cells.add(((b[0] + dx) % 30, (b[1] + dy) % 28, (b[2] + dz) % 26))
+    assert oracle.touched_count(dims, x_p, d_p) == len(cells)
+
+
+# ----------------------------------------------------------- Newton-Euler
+
+def test_newton_euler_free_fall(oracle):
+    # No fluid load: constant acceleration g, trapezoidal position update is exact.
+    x, u, w = oracle.newton_euler([[1.0, 2.0, 3.0]], [[0.1, 0.2, 0.3]], [[0.0, 0.0, 0.0]],
+                                  [2.0], [5.0], 1.0, [0.0, 0.0, -9.81], 0.1,
+                                  np.zeros((1, 3)), np.zeros((1, 3)))
+    tau = 0.1
+    g = np.array([0.0, 0.0, -9.81])
+    assert np.allclose(u[0], [0.1, 0.2, 0.3] + tau * g, atol=1e-15)
+    assert np.allclose(x[0], [1.0, 2.0, 3.0] + tau * np.array([0.1, 0.2, 0.3]) + 0.5 * tau ** 2 * g,
+                       atol=1e-14)
+
+
+def test_newton_euler_momentum_balance(oracle):
+    # Rigid-body form (Sec. 2.1): m_p (1 - rho_f/rho_p) du/dt = -rho_f F + V_p (rho_p - rho_f) g,
+    # I_p (1 - rho_f/rho_p) dw/dt = -rho_f T with I_p = m_p d^2/10 (solid sphere).
+    rng = np.random.default_rng(81)
+    n = 5
+    x0, u0, w0 = rng.normal(size=(n, 3)), rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    d = rng.uniform(5, 20, n)
+    rho = rng.uniform(1.2, 3.0, n)
+    F, T = rng.normal(size=(n, 3)) * 100, rng.normal(size=(n, 3)) * 300
+    g = np.array([0.0, -0.3, -9.81])
+    rho_f, tau = 0.9, 0.02
+    x, u, w = oracle.newton_euler(x0, u0, w0, d, rho, rho_f, g, tau, F, T)
+    V = math.pi * d ** 3 / 6
+    m = rho * V
+    I = m * d ** 2 / 10
+    lhs_u = (m * (1 - rho_f / rho))[:, None] * (u - u0) / tau
+    rhs_u = -rho_f * F + (V * (rho - rho_f))[:, None] * g
+    assert np.allclose(lhs_u, rhs_u, rtol=1e-11, atol=1e-9)
+    lhs_w = (I * (1 - rho_f / rho))[:, None] * (w - w0) / tau
+    assert np.allclose(lhs_w, -rho_f * T, rtol=1e-11, atol=1e-9)
+    assert np.allclose(x, x0 + 0.5 * tau * (u + u0), atol=1e-13)
+
+
+# ------------------------------------------------------------- gradients
+
+def _grad_problem(seed=91):
+    dims = (12, 11, 13)
+    rng = np.random.default_rng(seed)
+    x_p = np.array([[5.3, 5.1, 6.2], [9.9, 2.8, 3.3]])
+    d_p = np.array([3.1, 2.4])
+    u_p = rng.normal(0, 0.3, (2, 3))
+    om = rng.normal(0, 0.3, (2, 3))
+    u0 = rng.normal(size=(3, 13, 11, 12))
+    wgt = rng.uniform(0, 1, size=(13, 11, 12))
+    return dims, x_p, d_p, u_p, om, u0, wgt
+
+
+def _loss(oracle, u0, x_p, u_p, om, d_p, wgt, nf=3):
+    out = oracle.forcing_step(u0, x_p, u_p, om, d_p, n_forcing=nf, want_slip=False)
+    return 0.5 * (wgt[None] * out["u"] ** 2).sum(), out["u"]
+
+
+def test_backward_dot_product(oracle):
+    # u^0 -> u^{n} is affine: <J v, w> = <v, J^T w> (the adjoint recursion).
+    dims, x_p, d_p, u_p, om, u0, wgt = _grad_problem()
+    rng = np.random.default_rng(92)
+    v = rng.normal(size=u0.shape)
+    w = rng.normal(size=u0.shape)
+    a = oracle.forcing_step(u0 + v, x_p, u_p, om, d_p)["u"]
+    b = oracle.forcing_step(u0, x_p, u_p, om, d_p)["u"]
+    Jv = a - b
+    JTw, *_ = oracle.backward(u0, x_p, u_p, om, d_p, w)
+    assert (Jv * w).sum() == pytest.approx((v * JTw).sum(), rel=1e-11)
+
+
+def test_backward_finite_differences(oracle):
+    dims, x_p, d_p, u_p, om, u0, wgt = _grad_problem()
+    L0, uN = _loss(oracle, u0, x_p, u_p, om, d_p, wgt)
+    gi, gU, gW, gX = oracle.backward(u0, x_p, u_p, om, d_p, wgt[None] * uN)
+    eps = 1e-6
+    for p in range(2):
+        for c in range(3):
+            for name, arr, g, tol in (("U", u_p, gU, 1e-6), ("W", om, gW, 1e-6), ("X", x_p, gX, 1e-5)):
+                a1 = arr.copy(); a1[p, c] += eps
+                a2 = arr.copy(); a2[p, c] -= eps
+                args1 = {"U": (x_p, a1, om), "W": (x_p, u_p, a1), "X": (a1, u_p, om)}[name]
+                args2 = {"U": (x_p, a2, om), "W": (x_p, u_p, a2), "X": (a2, u_p, om)}[name]
+                L1, _ = _loss(oracle, u0, args1[0], args1[1], args1[2], d_p, wgt)
+                L2, _ = _loss(oracle, u0, args2[0], args2[1], args2[2], d_p, wgt)
+                fd = (L1 - L2) / (2 * eps)
+                scale = max(1.0, np.abs(g).max())
+                assert abs(fd - g[p, c]) <= tol * scale, (name, p, c, fd, g[p, c])
+    rng = np.random.default_rng(93)
+    for _ in range(5):
+        k = tuple(rng.integers(0, s) for s in u0.shape)
+        a1 = u0.copy(); a1[k] += eps
+        a2 = u0.copy(); a2[k] -= eps
+        fd = (_loss(oracle, a1, x_p, u_p, om, d_p, wgt)[0] - _loss(oracle, a2, x_p, u_p, om, d_p, wgt)[0]) / (2 * eps)
+        assert abs(fd - gi[k]) <= 1e-6 * max(1.0, np.abs(gi).max())
