@@ -1,0 +1,178 @@
+/*
+ * ibm.h - C ABI of the GB300 immersed-boundary forcing-step library.
+ *
+ * The library implements the iterated direct-forcing immersed-boundary step of
+ * Yao et al., "Particle-resolved simulations of four-way coupled polydispersed,
+ * particle-laden flows" (arXiv 2109.03972), Sec. 2.2.2 "Outer forcing", on a
+ * periodic collocated grid (Sec. 2.2, Fig. 1b) with the three-point
+ * regularised delta kernel (Eq. 3pt-delta / 3pt-stencil), for spheres whose
+ * surface is represented by Lagrangian markers (Sec. 2.1).  For every outer
+ * forcing iteration m = 1..n_F it
+ *   1. interpolates the cell-centred velocity to every marker,
+ *   2. forms the marker force F = (U^d - U)/tau, U^d = u_p + w_p x r_l,
+ *   3. spreads F back onto the grid over the same stencil,
+ *   4. updates u += tau f,
+ * and sums the fluid-side particle force and torque (Eq. basic-particle a,b).
+ *
+ * Conventions shared by every call
+ *  - Every call returns an ibm_status; nothing aborts or exits.  After an error
+ *    ibm_last_error() describes it.  Kernels never trap: device-side problems
+ *    set an error word that the next synchronising call reports.
+ *  - Units: positions in the same length unit as h; the grid of scene s has
+ *    dims[s] = (nx, ny, nz) cells, cell (i,j,k) centred at ((i+1/2)h, ...),
+ *    periodic in all three directions.  Particle centres may lie anywhere;
+ *    they are taken modulo the box.
+ *  - Velocity fields are caller-owned DEVICE arrays, one per scene, layout
+ *    [3][nz][ny][nx] (component-major, x fastest), float (IBM_FP32) or double
+ *    (IBM_FP64) according to the context's precision.
+ *  - One context = one CUDA stream.  Calls on one context are not thread-safe
+ *    and are ordered on that stream.  Calls that return host data synchronise
+ *    the stream.
+ *  - The context owns all scratch memory.  The caller owns u, f and gradient
+ *    buffers and keeps ownership of every array it passes in.
+ */
+#ifndef IBM_H
+#define IBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IBM_OK = 0,
+    IBM_ERR_INVALID_ARG = 1,  /* a pointer, size or value is out of range     */
+    IBM_ERR_CUDA = 2,         /* a CUDA runtime call failed                   */
+    IBM_ERR_OOM = 3,          /* device or host allocation failed             */
+    IBM_ERR_CAPACITY = 4,     /* more particles than max_particles            */
+    IBM_ERR_NONFINITE = 5,    /* NaN/Inf in particle state                    */
+    IBM_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up           */
+    IBM_ERR_STATE = 7         /* call out of order (e.g. backward w/o forward)*/
+} ibm_status;
+
+/* precision */
+enum { IBM_FP64 = 0, IBM_FP32 = 1 };
+
+/* spread_mode
+ *  IBM_SPREAD_CLUSTER        FP32 only.  Particles whose marker stencils share
+ *                            a cell are grouped; each group's touched cells
+ *                            stay in shared memory for all n_F iterations
+ *                            (spreading by shared-memory atomics; the FP32
+ *                            summation order is unspecified).
+ *  IBM_SPREAD_DETERMINISTIC  As CLUSTER, but spreading accumulates in integer
+ *                            fixed point, so results are bit-reproducible.
+ *  IBM_SPREAD_PLAIN          One thread per marker, global atomics into u, two
+ *                            kernels per iteration.  The only mode for FP64
+ *                            ("plain FP64 form"). */
+enum { IBM_SPREAD_CLUSTER = 0, IBM_SPREAD_DETERMINISTIC = 1, IBM_SPREAD_PLAIN = 2 };
+
+typedef struct {
+    int n_scenes;            /* >= 1; independent periodic boxes               */
+    const int32_t *dims;     /* HOST [n_scenes][3] = nx, ny, nz (each >= 8)    */
+    double h;                /* grid spacing (> 0), isotropic (Sec. 2.1)       */
+    int kernel_width;        /* 3: three-point kernel, Eq. (3pt-stencil)       */
+    int n_forcing;           /* n_F >= 1 outer forcing iterations (Sec. 2.2.2) */
+    int precision;           /* IBM_FP32 or IBM_FP64                           */
+    int spread_mode;         /* IBM_SPREAD_*                                   */
+    int newton_euler;        /* 1: apply Eq. (basic-particle a-c) after loop   */
+    double rho_f;            /* fluid density (Newton-Euler only)              */
+    double g[3];             /* gravity vector (Newton-Euler only)             */
+    int max_particles;       /* capacity of the context                        */
+    int requires_grad;       /* 1: keep what ibm_backward needs                */
+    int threads_per_block;   /* 0 = autotune; else 256, 512 or 1024 (CLUSTER)  */
+} ibm_config;
+
+typedef struct ibm_ctx ibm_ctx;
+
+/* Create a context.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  cfg->dims is copied.  On success *out owns device scratch sized for
+ * cfg->max_particles; release it with ibm_destroy.
+ * Errors: INVALID_ARG (bad config; kernel_width other than 3; FP64 with a mode
+ * other than PLAIN), OOM, CUDA. */
+ibm_status ibm_create(const ibm_config *cfg, void *cuda_stream, ibm_ctx **out);
+
+/* Release a context and all memory it owns.  NULL is accepted. */
+ibm_status ibm_destroy(ibm_ctx *ctx);
+
+/* Set the particle state used by the following forcing steps (Sec. 2.1: centre
+ * x_p, velocity u_p, angular velocity w_p, diameter d_p, density rho_p).
+ * Arrays are double, [n_p][3] or [n_p], in host memory (on_device = 0) or device
+ * memory (on_device = 1); they are copied.  scene_of[n_p] (int32, same memory
+ * space) gives each particle's scene and may be NULL when n_scenes == 1.
+ * rho_p may be NULL when newton_euler == 0.
+ * Marker set (reading of Sec. 2.1): N_l = round(pi (d_p/h)^2) markers on a
+ * golden spiral of diameter d_p, each of volume dV_l = pi (d_p^2 h + h^3/3)/N_l.
+ * Errors: INVALID_ARG (n_p < 0, NULL arrays, d_p <= 0 or d_p/h + 4 > the
+ * smallest grid edge of its scene, scene index out of range, rho_p == rho_f
+ * within 1e-6 relative with newton_euler), CAPACITY (n_p > max_particles),
+ * NONFINITE (NaN/Inf anywhere), CUDA. */
+ibm_status ibm_set_particles(ibm_ctx *ctx, int n_p, const double *x_p, const double *u_p,
+                             const double *omega_p, const double *d_p, const double *rho_p,
+                             const int32_t *scene_of, int on_device);
+
+/* One immersed-boundary forcing step: the outer forcing loop of Sec. 2.2.2
+ * (n_F iterations of interpolate -> force -> spread -> update), then the
+ * fluid-side particle loads summed over the iterations, then (if enabled) the
+ * rigid-body Newton-Euler update of Eq. (basic-particle a-c) with F_c = T_c = 0.
+ * u_ptrs[n_scenes]: HOST array of DEVICE pointers to each scene's velocity
+ *   field, updated in place (u^0 -> u^{n_F}).
+ * tau = 2 alpha_k dt > 0 (the paper divides the slip by 2 alpha_k dt and
+ *   multiplies the force by it, Sec. 2.2.2); u^{n_F} does not depend on tau.
+ * f_out: NULL, or HOST array of DEVICE pointers (same layout/type as u) that
+ *   receive the total IBM force sum_m f^m = (u^{n_F} - u^0)/tau on every cell
+ *   (zero where no marker stencil reaches).
+ * slip_out: NULL, or HOST double[2] receiving the RMS and the maximum over all
+ *   markers of |U^d - W u^{n_F}| after the loop (the error eps of Sec. 2.2.2);
+ *   requesting it synchronises the stream.
+ * Asynchronous on the context's stream unless slip_out is given.
+ * Errors: INVALID_ARG, STATE (no particles set), CUDA, TIMEOUT. */
+ibm_status ibm_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau,
+                            void *const *f_out, double *slip_out);
+
+/* Fluid-side loads of the last forcing step, double [n_p][3] each:
+ *   F_p = sum_m sum_l F^m_l dV_l,  T_p = sum_m sum_l r_l x F^m_l dV_l,
+ * with r_l = X_l - x_p (Eq. basic-particle a,b; the load on the particle is
+ * -rho_f times these).  x_p/u_p/omega_p, if non-NULL, receive the particle
+ * state after the Newton-Euler update (or the unchanged state if it is off).
+ * Destinations are host (on_device = 0; synchronises) or device memory.
+ * Any pointer may be NULL.  Errors: STATE (no step yet), CUDA. */
+ibm_status ibm_particle_loads(ibm_ctx *ctx, double *F, double *T, double *x_p, double *u_p,
+                              double *omega_p, int on_device);
+
+/* Backward pass of the last forcing step (requires requires_grad = 1 at
+ * create).  For a loss L(u^{n_F}) with grad_u_out[s] = dL/du^{n_F} (DEVICE,
+ * same layout/type as u), writes grad_u_in[s] = dL/du^0 (DEVICE, may alias
+ * grad_u_out) and the FP64 particle gradients dL/du_p, dL/dw_p, dL/dx_p
+ * ([n_p][3] each, DEVICE memory, any may be NULL).  The adjoint follows the
+ * loop algebra of Sec. 2.2.2: spreading is the adjoint of interpolation and
+ * vice versa, plus delta-kernel derivative terms for the marker positions.
+ * Markers and weights are recomputed per iteration from the saved u^0.
+ * Errors: STATE (requires_grad off or no forward step), INVALID_ARG, CUDA. */
+ibm_status ibm_backward(ibm_ctx *ctx, void *const *grad_u_out, void *const *grad_u_in,
+                        double *gU, double *gOmega, double *gX);
+
+/* Diagnostics.  Stencil base cell of every marker, in particle-then-l order,
+ * as the active precision path computes it: floor(X_l/h) per axis, NOT wrapped
+ * (int64 [n_markers][3], HOST).  *n_markers receives the count; pass base_out
+ * = NULL to query it.  Synchronises.  Errors: STATE, INVALID_ARG, CUDA. */
+ibm_status ibm_marker_bases(ibm_ctx *ctx, int64_t *base_out, int64_t *n_markers);
+
+/* Diagnostics of the last forcing step (HOST int64[8], synchronises):
+ * [0] markers, [1] particle clusters, [2] clusters on the shared-memory path,
+ * [3] markers on the fallback path, [4] largest cluster (cells, upper bound),
+ * [5] distinct touched cells on the shared-memory path, [6] kernel launches
+ * per step, [7] threads per block used. */
+ibm_status ibm_step_stats(ibm_ctx *ctx, int64_t *stats);
+
+/* Human-readable status name; never NULL. */
+const char *ibm_status_string(ibm_status s);
+
+/* Description of the last error on ctx (empty string if none); never NULL. */
+const char *ibm_last_error(const ibm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBM_H */

@@ -394,6 +394,8 @@ long ora_touched_count(int width, long nx, long ny, long nz, double h, long np,
  * slip   optional [2]: RMS and max over markers of |U^d - W u^{n_f}| after
  *        the loop (reading of the pointwise error eps of Sec. 2.2.2).
  * mode   0 = stencil sums, 1 = brute force over every cell (tiny grids).
+ * Fabs_out optional [np]: sum over m and l of |F^m_l| dV_l (the scale the
+ *        load tolerances are stated against).
  * Returns 0, or -1 on allocation failure.
  * Parity: pinned by the single-marker closed form, the dense linear-algebra
  * recursion, the no-op cases and the load identities (tests). */
@@ -401,7 +403,7 @@ int ora_forcing_step(int width, int mode, long nx, long ny, long nz, double h,
                      int n_forcing, double tau, long np,
                      const double *x_p, const double *u_p, const double *om_p,
                      const double *d_p, double *u, double *F_out, double *T_out,
-                     double *f_tot, double *slip)
+                     double *f_tot, double *slip, double *Fabs_out)
 {
     const long ncell = nx * ny * nz;
     ora_markers M;
@@ -411,6 +413,7 @@ int ora_forcing_step(int width, int mode, long nx, long ny, long nz, double h,
     double *f = (double *)malloc(sizeof(double) * 3 * (size_t)ncell);
     if (!U || !F || !f) return -1;
     for (long i = 0; i < 3 * np; ++i) { F_out[i] = 0.0; T_out[i] = 0.0; }
+    if (Fabs_out) for (long i = 0; i < np; ++i) Fabs_out[i] = 0.0;
     if (f_tot) memset(f_tot, 0, sizeof(double) * 3 * (size_t)ncell);
     const double h3 = h * h * h;
 
@@ -432,6 +435,8 @@ int ora_forcing_step(int width, int mode, long nx, long ny, long nz, double h,
             T_out[3 * p + 0] += (r[1] * Fm[2] - r[2] * Fm[1]) * dv;
             T_out[3 * p + 1] += (r[2] * Fm[0] - r[0] * Fm[2]) * dv;
             T_out[3 * p + 2] += (r[0] * Fm[1] - r[1] * Fm[0]) * dv;
+            if (Fabs_out)
+                Fabs_out[p] += sqrt(Fm[0] * Fm[0] + Fm[1] * Fm[1] + Fm[2] * Fm[2]) * dv;
         }
     }
     if (slip) {

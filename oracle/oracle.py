@@ -58,7 +58,7 @@ def lib():
         L.ora_touched_count.argtypes = [_i, _l, _l, _l, _d, _l, _p, _p]
         L.ora_forcing_step.restype = _i
         L.ora_forcing_step.argtypes = [_i, _i, _l, _l, _l, _d, _i, _d, _l,
-                                       _p, _p, _p, _p, _p, _p, _p, _p, _p]
+                                       _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
         L.ora_newton_euler.restype = None
         L.ora_newton_euler.argtypes = [_l, _p, _p, _p, _p, _p, _d, _p, _d, _p, _p]
         L.ora_backward.restype = _i
@@ -154,12 +154,13 @@ def forcing_step(u, x_p, u_p, om_p, d_p, h=1.0, n_forcing=3, tau=0.01, width=3,
     T = np.zeros((np_, 3))
     f = np.zeros_like(u) if want_f else None
     slip = np.zeros(2) if want_slip else None
+    Fabs = np.zeros(np_)
     rc = lib().ora_forcing_step(width, int(brute), nx, ny, nz, h, n_forcing, tau, np_,
                                 _ptr(x_p), _ptr(u_p), _ptr(om_p), _ptr(d_p), _ptr(u),
-                                _ptr(F), _ptr(T), _ptr(f), _ptr(slip))
+                                _ptr(F), _ptr(T), _ptr(f), _ptr(slip), _ptr(Fabs))
     if rc != 0:
         raise MemoryError("oracle allocation failed")
-    return {"u": u, "F": F, "T": T, "f": f, "slip": slip}
+    return {"u": u, "F": F, "T": T, "f": f, "slip": slip, "Fabs": Fabs}
 
 
 def newton_euler(x_p, u_p, om_p, d_p, rho_p, rho_f, g, tau, F, T):

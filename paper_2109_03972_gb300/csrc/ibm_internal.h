@@ -1,0 +1,126 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ibm.h"
+
+// Error bits set by kernels in ctx->err_d (never a trap).
+enum : int {
+    IBM_EBIT_NONFINITE = 1,
+    IBM_EBIT_DIAMETER = 2,
+    IBM_EBIT_SCENE = 4,
+    IBM_EBIT_DENSITY = 8,
+    IBM_EBIT_TIMEOUT = 16,
+    IBM_EBIT_OVERFLOW = 32,   // a scratch capacity was exceeded (work skipped)
+    IBM_EBIT_INTERNAL = 64,
+};
+
+// Per-particle record derived from the FP64 state at every step (device).
+struct PInfo {
+    double xi[3];     // x_p / h  (grid units)
+    double a;         // (d_p / 2) / h
+    float  fracf[3];  // xi - floor(xi), float
+    float  af;        // a as float
+    float  ud[3];     // u_p (float)
+    float  om[3];     // omega_p in grid units per time (omega * h / h = omega)
+    int    base[3];   // floor(xi)
+    int    nl;        // markers
+    int    moff;      // first global marker index
+    int    toff;      // template offset (entries)
+    int    scene;
+    float  D;         // dV_l / h^3
+    float  rphys;     // (d_p / 2) (physical arm length)
+    double D64;       // dV_l / h^3 (FP64)
+    double rphys64;   // d_p / 2 (FP64)
+};
+
+struct SceneDesc {
+    int n[3];
+    long long off;    // unused (fields are separate pointers)
+};
+
+struct ibm_ctx {
+    ibm_config cfg;
+    std::vector<int32_t> dims_h;   // [n_scenes][3]
+    int32_t *dims_d = nullptr;
+    int min_edge = 0;
+    cudaStream_t stream = nullptr;
+
+    int n_p = 0;
+    int cap_p = 0;
+    // particle state (device, FP64)
+    double *x = nullptr, *up = nullptr, *om = nullptr, *d = nullptr, *rho = nullptr;
+    int32_t *scene = nullptr;
+    int *nl = nullptr, *moff = nullptr, *toff = nullptr;
+    PInfo *pinfo = nullptr;
+    long long n_markers = 0;
+    int max_nl = 0;
+
+    // marker templates (unit directions), indexed by toff
+    double *tmpl64 = nullptr;
+    float *tmpl32 = nullptr;
+    long long tmpl_cap = 0, tmpl_used = 0;
+    int *tmpl_of_nl = nullptr;     // device [nl_cap], -1 = not generated
+    int nl_cap = 0;
+    std::vector<int> tmpl_of_nl_h; // host mirror
+
+    // loads / state outputs (device FP64)
+    double *FD = nullptr, *TD = nullptr;     // sum e*D, sum r x e*D (per particle)
+    double *Fout = nullptr, *Tout = nullptr; // F_p, T_p in physical units
+    double *x_new = nullptr, *u_new = nullptr, *om_new = nullptr;
+    double *slip_acc = nullptr;              // [2]
+
+    // plain-path scratch
+    void *ebuf = nullptr;     // [markers][3] real
+    long long ebuf_cap = 0;
+    void **uptr_d = nullptr;  // device copy of the scene field pointers
+    void **fptr_d = nullptr;
+    std::vector<void *> uptr_h, fptr_h;
+    int launches = 0;         // kernel launches of the last step
+
+    // cluster-path scratch (see ibm_cluster.cu)
+    void *cl = nullptr;
+
+    // backward
+    std::vector<void *> u0_saved;            // per scene copy of u^0
+    std::vector<void *> bw_work;             // per scene work field
+    void *e_hist = nullptr, *gu_hist = nullptr, *gmk = nullptr;
+    long long hist_cap = 0;
+    bool have_forward = false;
+    double last_tau = 0.0;
+
+    int *err_d = nullptr;
+    int *err_h = nullptr;     // pinned
+    bool have_step = false;
+    int64_t stats[8] = {0};
+    std::string last_error;
+};
+
+// helpers (ibm_context.cu)
+ibm_status ibm_fail(ibm_ctx *ctx, ibm_status s, const std::string &msg);
+ibm_status ibm_cuda_check(ibm_ctx *ctx, cudaError_t e, const char *what);
+ibm_status ibm_check_err_word(ibm_ctx *ctx);   // synchronises
+
+// plain path (ibm_plain.cu)
+ibm_status plain_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out);
+ibm_status plain_slip(ibm_ctx *ctx, void *const *u_ptrs);
+ibm_status finalize_particles(ibm_ctx *ctx, double tau);
+ibm_status plain_backward(ibm_ctx *ctx, void *const *grad_u_out, void *const *grad_u_in,
+                          double *gU, double *gOmega, double *gX);
+ibm_status launch_setup_particles(ibm_ctx *ctx);      // nl, validation
+ibm_status launch_templates(ibm_ctx *ctx, int lo_nl, int hi_nl);
+ibm_status launch_pinfo(ibm_ctx *ctx);
+ibm_status launch_marker_bases(ibm_ctx *ctx, int64_t *base_d);
+ibm_status launch_scan_int(ibm_ctx *ctx, const int *in, int *out_excl, int n, long long *total_d);
+
+ibm_status ensure_field_ptrs(ibm_ctx *ctx, void *const *u_ptrs, void *const *f_out);
+ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, double tau, bool with_f, int n_it);
+
+// cluster path (ibm_cluster.cu)
+ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out);
+void cluster_free(ibm_ctx *ctx);

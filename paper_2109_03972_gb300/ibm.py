@@ -1,0 +1,227 @@
+"""Thin Python binding of the C ABI in ``include/ibm.h``.
+
+Argument marshalling only: every step of the forcing loop runs in the CUDA
+kernels of ``libibm.so``.  PyTorch supplies device memory and the stream.  If
+the library is missing this module raises on import: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libibm.so")
+
+IBM_FP64, IBM_FP32 = 0, 1
+IBM_SPREAD_CLUSTER, IBM_SPREAD_DETERMINISTIC, IBM_SPREAD_PLAIN = 0, 1, 2
+
+STATUS = {0: "IBM_OK", 1: "IBM_ERR_INVALID_ARG", 2: "IBM_ERR_CUDA", 3: "IBM_ERR_OOM",
+          4: "IBM_ERR_CAPACITY", 5: "IBM_ERR_NONFINITE", 6: "IBM_ERR_TIMEOUT", 7: "IBM_ERR_STATE"}
+
+EXPORTED = ["ibm_create", "ibm_destroy", "ibm_set_particles", "ibm_forcing_step",
+            "ibm_particle_loads", "ibm_backward", "ibm_marker_bases", "ibm_step_stats",
+            "ibm_status_string", "ibm_last_error"]
+
+
+class IBMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n_scenes", ctypes.c_int), ("dims", ctypes.POINTER(ctypes.c_int32)),
+                ("h", ctypes.c_double), ("kernel_width", ctypes.c_int), ("n_forcing", ctypes.c_int),
+                ("precision", ctypes.c_int), ("spread_mode", ctypes.c_int),
+                ("newton_euler", ctypes.c_int), ("rho_f", ctypes.c_double),
+                ("g", ctypes.c_double * 3), ("max_particles", ctypes.c_int),
+                ("requires_grad", ctypes.c_int), ("threads_per_block", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libibm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libibm.so not found at {path}; build it with "
+                          "paper_2109_03972_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.ibm_create.argtypes = [ctypes.POINTER(_Config), vp, ctypes.POINTER(vp)]
+    L.ibm_destroy.argtypes = [vp]
+    L.ibm_set_particles.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, i]
+    L.ibm_forcing_step.argtypes = [vp, vp, d, vp, vp]
+    L.ibm_particle_loads.argtypes = [vp, vp, vp, vp, vp, vp, i]
+    L.ibm_backward.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.ibm_marker_bases.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
+    L.ibm_step_stats.argtypes = [vp, vp]
+    L.ibm_status_string.argtypes = [i]
+    L.ibm_status_string.restype = ctypes.c_char_p
+    L.ibm_last_error.argtypes = [vp]
+    L.ibm_last_error.restype = ctypes.c_char_p
+    for n in EXPORTED[:8]:
+        getattr(L, n).restype = i
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr())
+    return t.ctypes.data_as(ctypes.c_void_p)
+
+
+def _ptr_array(ts):
+    arr = (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+    return arr
+
+
+@dataclass
+class Config:
+    dims: list                       # [(nx, ny, nz), ...] one per scene
+    h: float = 1.0
+    n_forcing: int = 3
+    precision: int = IBM_FP32
+    spread_mode: int = IBM_SPREAD_CLUSTER
+    newton_euler: bool = False
+    rho_f: float = 1.0
+    g: tuple = (0.0, 0.0, 0.0)
+    max_particles: int = 1
+    requires_grad: bool = False
+    kernel_width: int = 3
+    threads_per_block: int = 0
+    extra: dict = field(default_factory=dict)
+
+
+class Context:
+    """Owns one ibm_ctx on a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, cfg: Config, stream: torch.cuda.Stream | None = None):
+        self.L = load_library()
+        self.cfg = cfg
+        self.stream = stream or torch.cuda.current_stream()
+        dims = np.ascontiguousarray(np.asarray(cfg.dims, dtype=np.int32).reshape(-1, 3))
+        self._dims = dims
+        c = _Config()
+        c.n_scenes = dims.shape[0]
+        c.dims = dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        c.h = cfg.h
+        c.kernel_width = cfg.kernel_width
+        c.n_forcing = cfg.n_forcing
+        c.precision = cfg.precision
+        c.spread_mode = cfg.spread_mode
+        c.newton_euler = int(cfg.newton_euler)
+        c.rho_f = cfg.rho_f
+        c.g = (ctypes.c_double * 3)(*cfg.g)
+        c.max_particles = cfg.max_particles
+        c.requires_grad = int(cfg.requires_grad)
+        c.threads_per_block = cfg.threads_per_block
+        h = ctypes.c_void_p()
+        st = self.L.ibm_create(ctypes.byref(c), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise IBMError(st, "ibm_create rejected the configuration")
+        self.h = h
+        self.n_p = 0
+        self.dtype = torch.float64 if cfg.precision == IBM_FP64 else torch.float32
+
+    def _check(self, st):
+        if st != 0:
+            raise IBMError(st, self.L.ibm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ibm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_particles(self, x_p, u_p, omega_p, d_p, rho_p=None, scene_of=None):
+        """Arrays: numpy (host) or torch tensors (device), float64."""
+        on_dev = isinstance(x_p, torch.Tensor) and x_p.is_cuda
+        conv = (lambda a: a.contiguous()) if on_dev else (lambda a: np.ascontiguousarray(a, dtype=np.float64))
+        arrs = [conv(a) for a in (x_p, u_p, omega_p, d_p)]
+        rho = None if rho_p is None else conv(rho_p)
+        sc = None
+        if scene_of is not None:
+            sc = scene_of.contiguous() if on_dev else np.ascontiguousarray(scene_of, dtype=np.int32)
+        n = int(arrs[3].shape[0])
+        self._keep = (arrs, rho, sc)
+        self._check(self.L.ibm_set_particles(self.h, n, *[_ptr(a) for a in arrs], _ptr(rho), _ptr(sc),
+                                             int(on_dev)))
+        self.n_p = n
+
+    def forcing_step(self, u_fields, tau, f_out=None, want_slip=False):
+        u_fields = list(u_fields) if isinstance(u_fields, (list, tuple)) else [u_fields]
+        up = _ptr_array(u_fields)
+        fp = _ptr_array(list(f_out)) if f_out is not None else None
+        slip = (ctypes.c_double * 2)() if want_slip else None
+        self._check(self.L.ibm_forcing_step(self.h, up, float(tau), fp, slip))
+        return (slip[0], slip[1]) if want_slip else None
+
+    def particle_loads(self, device=False):
+        n = self.n_p
+        if device:
+            out = [torch.empty((n, 3), dtype=torch.float64, device="cuda") for _ in range(5)]
+        else:
+            out = [np.empty((n, 3)) for _ in range(5)]
+        self._check(self.L.ibm_particle_loads(self.h, *[_ptr(o) for o in out], int(device)))
+        keys = ("F", "T", "x_p", "u_p", "omega_p")
+        return dict(zip(keys, out))
+
+    def backward(self, grad_u_out, grad_u_in=None):
+        gos = list(grad_u_out) if isinstance(grad_u_out, (list, tuple)) else [grad_u_out]
+        gis = [torch.empty_like(g) for g in gos] if grad_u_in is None else list(grad_u_in)
+        gU, gW, gX = (torch.empty((self.n_p, 3), dtype=torch.float64, device="cuda") for _ in range(3))
+        self._check(self.L.ibm_backward(self.h, _ptr_array(gos), _ptr_array(gis), _ptr(gU), _ptr(gW), _ptr(gX)))
+        return gis, gU, gW, gX
+
+    def marker_bases(self):
+        n = ctypes.c_int64()
+        self._check(self.L.ibm_marker_bases(self.h, None, ctypes.byref(n)))
+        out = np.empty((n.value, 3), dtype=np.int64)
+        self._check(self.L.ibm_marker_bases(self.h, _ptr(out), ctypes.byref(n)))
+        return out
+
+    def stats(self):
+        out = np.zeros(8, dtype=np.int64)
+        self._check(self.L.ibm_step_stats(self.h, _ptr(out)))
+        keys = ("markers", "clusters", "clusters_smem", "markers_fallback", "largest_cluster_cells",
+                "touched_cells", "launches", "threads_per_block")
+        return dict(zip(keys, (int(v) for v in out)))
+
+
+class IBMForcing(torch.autograd.Function):
+    """u^{n_F} = IBM forcing loop(u^0; U_p, omega_p, x_p) with the hand-written adjoint.
+
+    ``ctx_obj`` must be a Context created with requires_grad=True.  Gradients flow to
+    u0 (all scenes' fields concatenated is not supported: one scene) and to the FP64
+    particle tensors u_p, omega_p, x_p (device, [n_p, 3]).
+    """
+
+    @staticmethod
+    def forward(ctx, u0, u_p, omega_p, x_p, d_p, ibm_ctx, tau):
+        ibm_ctx.set_particles(x_p.detach().contiguous(), u_p.detach().contiguous(),
+                              omega_p.detach().contiguous(), d_p.detach().contiguous())
+        u = u0.detach().clone()
+        ibm_ctx.forcing_step([u], tau)
+        ctx.ibm_ctx = ibm_ctx
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        gis, gU, gW, gX = ctx.ibm_ctx.backward([grad_u.contiguous()])
+        return gis[0], gU, gW, gX, None, None, None

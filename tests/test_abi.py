@@ -1,0 +1,59 @@
+"""CPU checks of the C-ABI library: it builds, loads, and exports every entry
+point that include/ibm.h declares.  No compute call (no GPU here)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ibm.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(ibm_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("ibm_create", "ibm_destroy", "ibm_set_particles", "ibm_forcing_step",
+              "ibm_particle_loads", "ibm_backward"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2109_03972_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for n in _declared():
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_without_gpu():
+    from paper_2109_03972_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    lib.ibm_status_string.restype = ctypes.c_char_p
+    assert lib.ibm_status_string(0) == b"IBM_OK"
+    assert lib.ibm_status_string(6) == b"IBM_ERR_TIMEOUT"
+    lib.ibm_last_error.restype = ctypes.c_char_p
+    assert lib.ibm_last_error(None) == b""
+
+
+def test_create_rejects_bad_config_without_touching_gpu():
+    # Invalid configurations are rejected before any CUDA call.
+    from paper_2109_03972_gb300 import build, ibm
+    L = ibm.load_library(build.build())
+    dims = (ctypes.c_int32 * 3)(32, 32, 32)
+    for bad in ({"h": -1.0}, {"kernel_width": 5}, {"n_forcing": 0}, {"precision": 9},
+                {"max_particles": 0}, {"precision": ibm.IBM_FP64, "spread_mode": ibm.IBM_SPREAD_CLUSTER}):
+        c = ibm._Config()
+        c.n_scenes, c.dims, c.h, c.kernel_width, c.n_forcing = 1, dims, 1.0, 3, 3
+        c.precision, c.spread_mode, c.max_particles = ibm.IBM_FP32, ibm.IBM_SPREAD_PLAIN, 4
+        for k, v in bad.items():
+            setattr(c, k, v)
+        out = ctypes.c_void_p()
+        assert L.ibm_create(ctypes.byref(c), None, ctypes.byref(out)) == 1
+    # dims below 8 cells
+    c = ibm._Config()
+    small = (ctypes.c_int32 * 3)(4, 32, 32)
+    c.n_scenes, c.dims, c.h, c.kernel_width, c.n_forcing = 1, small, 1.0, 3, 3
+    c.precision, c.spread_mode, c.max_particles = ibm.IBM_FP32, ibm.IBM_SPREAD_PLAIN, 4
+    assert L.ibm_create(ctypes.byref(c), None, ctypes.byref(ctypes.c_void_p())) == 1

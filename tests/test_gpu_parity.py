@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (stated here, derived in the design doc):
+  FP64 path : |u - u_oracle|_inf <= 1e-12 |u0|_inf; loads <= 1e-12 sum|F|dV.
+  FP32 paths: |u - u_oracle|_inf <= 2e-5 |u0|_inf; force <= 1e-4 sum|F|dV,
+              torque <= 1e-4 (d/2) sum|F|dV; slip RMS <= 1e-3 relative.
+  Stencil base cells: bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests._helpers import f32_round, load_err, rel_err_u, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2109_03972_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_2109_03972_gb300 import ibm, synth  # noqa: E402
+
+FP32_MODES = [ibm.IBM_SPREAD_PLAIN, ibm.IBM_SPREAD_CLUSTER, ibm.IBM_SPREAD_DETERMINISTIC]
+U_TOL32, LOAD_TOL32, SLIP_TOL32 = 2e-5, 1e-4, 1e-3
+
+
+def _scene(name):
+    return synth.workload(name).scenes[0]
+
+
+def _chain_scene():
+    # Spheres at the minimum gap of 1h in a chain that crosses the periodic seam:
+    # one particle cluster whose stencils overlap everywhere.
+    dims = (48, 40, 44)
+    d = np.array([10.0, 12.0, 9.0, 11.0, 10.0])
+    x = np.array([[5.2, 20.3, 22.1]])
+    pts = [x[0]]
+    rng = np.random.default_rng(4)
+    for i in range(1, len(d)):
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+        pts.append(pts[-1] + v * (0.5 * (d[i] + d[i - 1]) + 1.0))
+    x = np.array(pts) % np.array(dims)
+    u_p, om, rho = synth.particle_state(len(d), 9)
+    return synth.Scene(dims, x, d, u_p, om, rho, field_seed=17)
+
+
+SCENES = {"small": lambda: _scene("small"), "single64": lambda: _scene("single64"), "chain": _chain_scene}
+
+
+@pytest.fixture(scope="module")
+def oracle_mod():
+    from oracle import oracle as O
+    O.build()
+    return O
+
+
+def _oracle_run(O, sc, u0, nf=3, tau=0.01, want_f=False):
+    return O.forcing_step(u0, sc.x_p, sc.u_p, sc.omega_p, sc.d_p, n_forcing=nf, tau=tau, want_f=want_f)
+
+
+@pytest.mark.parametrize("name", ["small", "single64", "chain"])
+def test_fp64_plain_matches_oracle(oracle_mod, name):
+    sc = SCENES[name]()
+    u0 = sc.field()
+    ref = _oracle_run(oracle_mod, sc, u0, want_f=True)
+    got = run_gpu(sc, u0, ibm.IBM_FP64, ibm.IBM_SPREAD_PLAIN, want_f=True)
+    assert rel_err_u(got["u"], ref["u"], u0) <= 1e-12
+    assert load_err(got["F"], ref["F"], ref["Fabs"]) <= 1e-12
+    assert load_err(got["T"], ref["T"], 0.5 * sc.d_p * ref["Fabs"]) <= 1e-12
+    assert np.abs(got["f"] - ref["f"]).max() <= 1e-12 * np.abs(u0).max() / 0.01
+    assert got["slip"][0] == pytest.approx(ref["slip"][0], rel=1e-10)
+    assert got["slip"][1] == pytest.approx(ref["slip"][1], rel=1e-10)
+
+
+@pytest.mark.parametrize("mode", FP32_MODES)
+@pytest.mark.parametrize("name", ["small", "single64", "chain"])
+def test_fp32_matches_oracle(oracle_mod, name, mode):
+    sc = SCENES[name]()
+    u0 = f32_round(sc.field())
+    ref = _oracle_run(oracle_mod, sc, u0, want_f=True)
+    got = run_gpu(sc, u0, ibm.IBM_FP32, mode, want_f=True)
+    assert rel_err_u(got["u"], ref["u"], u0) <= U_TOL32
+    assert load_err(got["F"], ref["F"], ref["Fabs"]) <= LOAD_TOL32
+    assert load_err(got["T"], ref["T"], 0.5 * sc.d_p * ref["Fabs"]) <= LOAD_TOL32
+    assert np.abs(got["f"] - ref["f"]).max() <= U_TOL32 * np.abs(u0).max() / 0.01
+    assert got["slip"][0] == pytest.approx(ref["slip"][0], rel=SLIP_TOL32)
+
+
+@pytest.mark.parametrize("precision", [ibm.IBM_FP64, ibm.IBM_FP32])
+@pytest.mark.parametrize("name", ["small", "single64", "chain"])
+def test_bins_bit_exact(oracle_mod, name, precision):
+    sc = SCENES[name]()
+    mode = ibm.IBM_SPREAD_PLAIN if precision == ibm.IBM_FP64 else ibm.IBM_SPREAD_CLUSTER
+    from tests._helpers import gpu_context
+    ctx = gpu_context([sc.dims], sc.n_p, precision, mode)
+    ctx.set_particles(sc.x_p, sc.u_p, sc.omega_p, sc.d_p)
+    got = ctx.marker_bases()
+    xi, base = oracle_mod.marker_positions(sc.x_p, sc.d_p)
+    ties = np.abs(xi - np.round(xi)) < 1e-9
+    assert ties.sum() == 0
+    assert np.array_equal(got, base)
+
+
+def test_newton_euler_matches_oracle(oracle_mod):
+    sc = _scene("small")
+    u0 = sc.field()
+    g = (0.0, 0.0, -1e-3)
+    ref = _oracle_run(oracle_mod, sc, u0)
+    x, u, w = oracle_mod.newton_euler(sc.x_p, sc.u_p, sc.omega_p, sc.d_p, sc.rho_p, 1.0, g, 0.01,
+                                      ref["F"], ref["T"])
+    got = run_gpu(sc, u0, ibm.IBM_FP64, ibm.IBM_SPREAD_PLAIN, newton_euler=True)
+    assert np.allclose(got["u_p"], u, rtol=1e-11, atol=1e-13)
+    assert np.allclose(got["omega_p"], w, rtol=1e-11, atol=1e-13)
+    assert np.allclose(got["x_p"], x, rtol=1e-13, atol=1e-12)
+    got32 = run_gpu(sc, f32_round(u0), ibm.IBM_FP32, ibm.IBM_SPREAD_CLUSTER, newton_euler=True)
+    ref32 = _oracle_run(oracle_mod, sc, f32_round(u0))
+    x, u, w = oracle_mod.newton_euler(sc.x_p, sc.u_p, sc.omega_p, sc.d_p, sc.rho_p, 1.0, g, 0.01,
+                                      ref32["F"], ref32["T"])
+    scale = np.abs(u - sc.u_p).max()
+    assert np.abs(got32["u_p"] - u).max() <= LOAD_TOL32 * 10 * scale
+
+
+def test_empty_particle_set():
+    from tests._helpers import gpu_context
+    ctx = gpu_context([(32, 32, 32)], 4, ibm.IBM_FP32, ibm.IBM_SPREAD_CLUSTER)
+    ctx.set_particles(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0))
+    u = torch.randn(3, 32, 32, 32, device="cuda")
+    u0 = u.clone()
+    slip = ctx.forcing_step([u], 0.01, want_slip=True)
+    assert torch.equal(u, u0)
+    assert slip == (0.0, 0.0)
+
+
+@pytest.mark.parametrize("mode", FP32_MODES)
+def test_multi_scene_matches_oracle(oracle_mod, mode):
+    # Three independent periodic scenes of different sizes in one context.
+    W = synth.workload("batched")
+    scenes = [s for s in W.scenes[:40] if s.n_p > 0][:3]
+    from tests._helpers import gpu_context
+    n = sum(s.n_p for s in scenes)
+    ctx = gpu_context([s.dims for s in scenes], n, ibm.IBM_FP32, mode)
+    x = np.concatenate([s.x_p for s in scenes])
+    up = np.concatenate([s.u_p for s in scenes])
+    om = np.concatenate([s.omega_p for s in scenes])
+    d = np.concatenate([s.d_p for s in scenes])
+    so = np.concatenate([np.full(s.n_p, i, dtype=np.int32) for i, s in enumerate(scenes)])
+    u0s = [f32_round(s.field()) for s in scenes]
+    us = [torch.from_numpy(a).float().cuda() for a in u0s]
+    ctx.set_particles(x, up, om, d, scene_of=so)
+    ctx.forcing_step(us, 0.01)
+    loads = ctx.particle_loads()
+    off = 0
+    for s, u0, u in zip(scenes, u0s, us):
+        ref = _oracle_run(oracle_mod, s, u0)
+        assert rel_err_u(u.double().cpu().numpy(), ref["u"], u0) <= U_TOL32
+        sl = slice(off, off + s.n_p)
+        assert load_err(loads["F"][sl], ref["F"], ref["Fabs"]) <= LOAD_TOL32
+        off += s.n_p
+
+
+def test_invalid_arguments_are_reported():
+    from tests._helpers import gpu_context
+    ctx = gpu_context([(32, 32, 32)], 2, ibm.IBM_FP32, ibm.IBM_SPREAD_CLUSTER)
+    good = dict(x_p=np.array([[16.0, 16.0, 16.0]]), u_p=np.zeros((1, 3)), omega_p=np.zeros((1, 3)),
+                d_p=np.array([8.0]))
+    with pytest.raises(ibm.IBMError) as e:
+        ctx.set_particles(**{**good, "x_p": np.array([[np.nan, 1.0, 1.0]])})
+    assert e.value.status == 5
+    with pytest.raises(ibm.IBMError) as e:
+        ctx.set_particles(**{**good, "d_p": np.array([29.0])})
+    assert e.value.status == 1
+    with pytest.raises(ibm.IBMError) as e:
+        ctx.set_particles(**{**good, "d_p": np.array([-1.0])})
+    assert e.value.status == 1
+    with pytest.raises(ibm.IBMError) as e:
+        ctx.set_particles(np.zeros((3, 3)), np.zeros((3, 3)), np.zeros((3, 3)), np.full(3, 8.0))
+    assert e.value.status == 4
+    with pytest.raises(ibm.IBMError) as e:
+        ctx.particle_loads()
+    assert e.value.status == 7
+    with pytest.raises(ibm.IBMError) as e:
+        ctx.backward([torch.zeros(3, 32, 32, 32, device="cuda")])
+    assert e.value.status == 7
+    ctx.set_particles(**good)
+    with pytest.raises(ibm.IBMError) as e:
+        ctx.forcing_step([torch.zeros(3, 32, 32, 32, device="cuda")], -1.0)
+    assert e.value.status == 1
+    ne = gpu_context([(32, 32, 32)], 2, ibm.IBM_FP64, ibm.IBM_SPREAD_PLAIN, newton_euler=True)
+    with pytest.raises(ibm.IBMError) as e:
+        ne.set_particles(**good, rho_p=np.array([1.0]))
+    assert e.value.status == 1
+
+
+def _grad_case():
+    sc = _scene("small")
+    rng = np.random.default_rng(5)
+    wgt = rng.uniform(0, 1, size=(sc.dims[2], sc.dims[1], sc.dims[0]))
+    return sc, sc.field(), wgt
+
+
+def test_backward_fp64_matches_oracle(oracle_mod):
+    sc, u0, wgt = _grad_case()
+    ref_u = _oracle_run(oracle_mod, sc, u0)["u"]
+    go = wgt[None] * ref_u
+    gi, gU, gW, gX = oracle_mod.backward(u0, sc.x_p, sc.u_p, sc.omega_p, sc.d_p, go)
+    from tests._helpers import gpu_context
+    ctx = gpu_context([sc.dims], sc.n_p, ibm.IBM_FP64, ibm.IBM_SPREAD_PLAIN, requires_grad=True)
+    ctx.set_particles(sc.x_p, sc.u_p, sc.omega_p, sc.d_p)
+    u = torch.from_numpy(u0).cuda()
+    ctx.forcing_step([u], 0.01)
+    g = torch.from_numpy(wgt[None]).cuda() * u
+    gis, tU, tW, tX = ctx.backward([g])
+    torch.cuda.synchronize()
+    assert np.abs(gis[0].cpu().numpy() - gi).max() <= 1e-11 * np.abs(gi).max()
+    for a, b in ((tU, gU), (tW, gW), (tX, gX)):
+        assert np.abs(a.cpu().numpy() - b).max() <= 1e-10 * max(1.0, np.abs(b).max())
+
+
+def test_backward_fp32_vs_fp64():
+    sc, u0, wgt = _grad_case()
+    from tests._helpers import gpu_context
+    res = {}
+    for prec, mode in ((ibm.IBM_FP64, ibm.IBM_SPREAD_PLAIN), (ibm.IBM_FP32, ibm.IBM_SPREAD_CLUSTER)):
+        ctx = gpu_context([sc.dims], sc.n_p, prec, mode, requires_grad=True)
+        ctx.set_particles(sc.x_p, sc.u_p, sc.omega_p, sc.d_p)
+        dt = torch.float64 if prec == ibm.IBM_FP64 else torch.float32
+        u = torch.from_numpy(f32_round(u0)).to(dtype=dt, device="cuda")
+        ctx.forcing_step([u], 0.01)
+        g = torch.from_numpy(wgt[None]).to(dtype=dt, device="cuda") * u
+        res[prec] = [t.double().cpu().numpy() if hasattr(t, "cpu") else t
+                     for t in (lambda r: [r[0][0], r[1], r[2], r[3]])(ctx.backward([g]))]
+    for a, b in zip(res[ibm.IBM_FP32], res[ibm.IBM_FP64]):
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b)
+
+
+def test_autograd_function_fd():
+    # torch.autograd.Function over the hand-written adjoint, FP64 central FD at eps = 1e-6.
+    sc, u0, wgt = _grad_case()
+    from tests._helpers import gpu_context
+    ctx = gpu_context([sc.dims], sc.n_p, ibm.IBM_FP64, ibm.IBM_SPREAD_PLAIN, requires_grad=True)
+    w = torch.from_numpy(wgt[None]).cuda()
+    dev = dict(device="cuda", dtype=torch.float64)
+    up = torch.tensor(sc.u_p, **dev, requires_grad=True)
+    om = torch.tensor(sc.omega_p, **dev, requires_grad=True)
+    xp = torch.tensor(sc.x_p, **dev, requires_grad=True)
+    d = torch.tensor(sc.d_p, **dev)
+    uu = torch.from_numpy(u0).cuda().requires_grad_(True)
+
+    def loss(uu, up, om, xp):
+        out = ibm.IBMForcing.apply(uu, up, om, xp, d, ctx, 0.01)
+        return 0.5 * (w * out * out).sum()
+
+    L = loss(uu, up, om, xp)
+    L.backward()
+    eps = 1e-6
+    for t, grad in ((up, up.grad), (om, om.grad), (xp, xp.grad)):
+        for (p, c) in ((0, 0), (1, 2), (3, 1)):
+            with torch.no_grad():
+                t[p, c] += eps
+                Lp = loss(uu, up, om, xp).item()
+                t[p, c] -= 2 * eps
+                Lm = loss(uu, up, om, xp).item()
+                t[p, c] += eps
+            fd = (Lp - Lm) / (2 * eps)
+            tol = 1e-5 if t is xp else 1e-6
+            assert abs(fd - grad[p, c].item()) <= tol * max(1.0, grad.abs().max().item())
