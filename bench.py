@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Benchmark of the immersed-boundary forcing step (one step = the n_F = 3
+outer forcing iterations of Sec. 2.2.2 plus particle loads and the
+Newton-Euler update) on the synthetic bidisperse bed: periodic 512x512x1024
+grid, 1500 spheres D = 24h and 12000 spheres D = 12h (8,139,000 markers).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead (a bounded sample of the same workload).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torchrun; every rank runs its own replica (no collective
+on the data path), so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IBM marker-iterations/s and HBM GB/s, FP32 vs plain FP64 form at stated slip"
+UNIT = "marker-iterations/s"
+WORKLOAD_DESC = {
+    "bidisperse": "bidisperse bed: periodic 512x512x1024, 12000 spheres D=12h + 1500 D=24h, n_F=3, FP32",
+    "mono": "monodisperse bed: periodic 256x256x512, 2000 spheres D=16h, n_F=3, FP32",
+    "single64": "single sphere D=16h in a periodic 64^3 grid, n_F=3, FP32",
+}
+KERNEL_SOURCES = ["paper_2109_03972_gb300/csrc/ibm_cluster.cu", "paper_2109_03972_gb300/csrc/ibm_device.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bidisperse", choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--mode", default="cluster", choices=["cluster", "deterministic", "plain"])
+    ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = default)")
+    ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, mode):
+    """DRAM bytes per launch of the cluster kernel from the committed ncu summary,
+    or None if the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"ibm_cluster_forcing_{workload}.md")
+    try:
+        with open(path) as fh:
+            for line in fh:
+                if line.startswith("traffic_per_launch:"):
+                    parts = dict(kv.split("=") for kv in line.split(":", 1)[1].split())
+                    if parts.get("source_hash") == kernel_source_hash() and parts.get("mode") == mode:
+                        return float(parts["bytes"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def scene_arrays(W):
+    sc = W.scenes
+    x = np.concatenate([s.x_p for s in sc])
+    up = np.concatenate([s.u_p for s in sc])
+    om = np.concatenate([s.omega_p for s in sc])
+    d = np.concatenate([s.d_p for s in sc])
+    rho = np.concatenate([s.rho_p for s in sc])
+    so = np.concatenate([np.full(s.n_p, i, dtype=np.int32) for i, s in enumerate(sc)])
+    return x, up, om, d, rho, so
+
+
+def cpu_sample(W, target_s, rng_seed=7):
+    """Bounded sample of the workload for the oracle: the particles whose centres
+    lie in a cubic sub-box of edge S (a periodic S^3 grid of its own), S chosen so
+    one oracle step takes about target_s seconds on one core."""
+    from oracle import oracle as O
+    from paper_2109_03972_gb300 import synth
+    sc = W.scenes[0]
+    nx, ny, nz = sc.dims
+    dmax = float(sc.d_p.max())
+
+    def sub(S):
+        keep = np.all(sc.x_p < S, axis=1) & np.all(sc.x_p >= 0, axis=1)
+        return synth.Scene((S, S, S), sc.x_p[keep], sc.d_p[keep], sc.u_p[keep], sc.omega_p[keep],
+                           sc.rho_p[keep], field_seed=rng_seed)
+
+    S = int(min(nx, ny, nz, max(2 * dmax + 8, 64)))
+    probe = sub(S)
+    u = probe.field()
+    t0 = time.perf_counter()
+    O.forcing_step(u, probe.x_p, probe.u_p, probe.omega_p, probe.d_p, n_forcing=W.n_forcing, tau=W.tau,
+                   want_slip=False)
+    t1 = time.perf_counter() - t0
+    grow = (target_s / max(t1, 1e-3)) ** (1.0 / 3.0)
+    S2 = int(min(min(nx, ny, nz), max(S, int(S * grow) // 16 * 16)))
+    return sub(S2), S2
+
+
+def time_oracle(scene, W, steps):
+    from oracle import oracle as O
+    u = scene.field()
+    n_mark = O.total_markers(scene.d_p)
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        O.forcing_step(u, scene.x_p, scene.u_p, scene.omega_p, scene.d_p, n_forcing=W.n_forcing, tau=W.tau,
+                       want_slip=False)
+        t.append(time.perf_counter() - t0)
+    return n_mark, t
+
+
+def reference_arm(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2109_03972_gb300 import synth
+    O.build()
+    W = synth.workload(args.workload)
+    per_step = max(0.05, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    scene, S = cpu_sample(W, per_step)
+    _, _ = time_oracle(scene, W, max(0, min(args.warmup, 1)))
+    n_mark, t = time_oracle(scene, W, args.steps)
+    ms = 1e3 * float(np.mean(t))
+    value = n_mark * W.n_forcing / (ms / 1e3)
+    sample = (f"particles with centres in a {S}^3 sub-box of the {args.workload} bed "
+              f"({scene.n_p} spheres, {n_mark} markers), periodic {S}^3 grid, one step per timed step")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD_DESC[args.workload], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def our_arm(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2109_03972_gb300 import build, synth
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2109_03972_gb300 import ibm
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    W = synth.workload(args.workload, seed=2109 + rank)
+    dims = [s.dims for s in W.scenes]
+    x, up, om, d, rho, so = scene_arrays(W)
+    n_p = len(d)
+    fields64 = [s.field() for s in W.scenes]
+    u_host = [torch.from_numpy(f.astype(np.float32)) for f in fields64]
+    mode = {"cluster": ibm.IBM_SPREAD_CLUSTER, "deterministic": ibm.IBM_SPREAD_DETERMINISTIC,
+            "plain": ibm.IBM_SPREAD_PLAIN}[args.mode]
+    cfg = ibm.Config(dims=dims, n_forcing=W.n_forcing, precision=ibm.IBM_FP32, spread_mode=mode,
+                     max_particles=n_p, newton_euler=True, rho_f=W.rho_f, g=W.g, profile=True,
+                     threads_per_block=args.threads)
+    stream = torch.cuda.current_stream()
+    ctx = ibm.Context(cfg, stream)
+    ctx.set_particles(x, up, om, d, rho, so if len(dims) > 1 else None)
+    us = [t.cuda() for t in u_host]
+    for _ in range(args.warmup):
+        ctx.forcing_step(us, W.tau)
+    torch.cuda.synchronize()
+    stats = ctx.stats()
+    n_mark = stats["markers"]
+    ctx.kernel_timing(reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.forcing_step(us, W.tau)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    k_ms, k_n = ctx.kernel_timing(reset=True)
+    k_avg = k_ms / max(1, k_n)
+    stats = ctx.stats()
+    value = world * n_mark * W.n_forcing / (ms / 1e3)
+
+    peaks, peak_kind = measured_peaks()
+    touched = stats["touched_cells"]
+    n_p_smem = n_p   # particle records read/written by the kernel (upper bound: all particles)
+    alg_bytes = touched * 3 * 4 * 2 * W.n_forcing + n_p_smem * (104 + 48)
+    achieved = alg_bytes / (k_avg / 1e3) / 1e9 if k_avg > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
+                "traffic": profiled_traffic(args.workload, args.mode),
+                "kernel": "k_cluster_forcing" if mode != ibm.IBM_SPREAD_PLAIN else "k_plain_interp+k_plain_spread",
+                "kernel_ms": k_avg, "algorithmic_bytes_per_launch": alg_bytes,
+                "peak_kind": f"{peak_kind} hbm_gbs (STREAM-style copy)"}
+    slip = ctx.forcing_step(us, W.tau, want_slip=True)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC[args.workload], "markers": n_mark, "particles": n_p,
+                       "spread_mode": args.mode, "n_forcing": W.n_forcing,
+                       "l2": "inputs larger than L2 (u field %.1f GB, touched cells %.0f MB)" % (
+                           sum(t.numel() for t in us) * 4 / 1e9, touched * 12 / 1e6),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "hbm_gbs_algorithmic_step": alg_bytes / (ms / 1e3) / 1e9,
+            "slip": {"rms": slip[0], "max": slip[1]},
+            "stats": stats,
+            "gpu_launches": int(stats["launches"]) * args.steps,
+            "clocks": clocks}
+
+    if not args.quick:
+        # end to end through the C ABI with host buffers: H2D of u and the particle
+        # state, the step, D2H of u and the loads, every step
+        pinned = [t.pin_memory() for t in u_host]
+        back = [torch.empty_like(t).pin_memory() for t in u_host]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for dst, src in zip(us, pinned):
+                dst.copy_(src, non_blocking=True)
+            ctx.set_particles(x, up, om, d, rho, so if len(dims) > 1 else None)
+            ctx.forcing_step(us, W.tau)
+            loads = ctx.particle_loads()
+            for dst, src in zip(back, us):
+                dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        ubytes = sum(t.numel() * 4 for t in u_host)
+        pbytes = n_p * 8 * (3 * 3 + 2) + (n_p * 4 if len(dims) > 1 else 0)
+        line["e2e"] = {"value": world * n_mark * W.n_forcing / e2e_s, "unit": UNIT,
+                       "h2d_bytes_per_step": ubytes + pbytes, "d2h_bytes_per_step": ubytes + n_p * 8 * 15,
+                       "ms_per_step": e2e_s * 1e3}
+        # plain FP64 form (the denominator of the speed-up), same workload
+        cfg64 = ibm.Config(dims=dims, n_forcing=W.n_forcing, precision=ibm.IBM_FP64,
+                           spread_mode=ibm.IBM_SPREAD_PLAIN, max_particles=n_p, newton_euler=True,
+                           rho_f=W.rho_f, g=W.g)
+        c64 = ibm.Context(cfg64, stream)
+        c64.set_particles(x, up, om, d, rho, so if len(dims) > 1 else None)
+        u64 = [torch.from_numpy(f).cuda() for f in fields64]
+        c64.forcing_step(u64, W.tau)
+        torch.cuda.synchronize()
+        n64 = 3
+        e0.record(stream)
+        for _ in range(n64):
+            c64.forcing_step(u64, W.tau)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / n64
+        slip64 = c64.forcing_step(u64, W.tau, want_slip=True)
+        line["fp64_plain"] = {"value": world * n_mark * W.n_forcing / (ms64 / 1e3), "unit": UNIT,
+                              "ms_per_step": ms64, "slip": {"rms": slip64[0], "max": slip64[1]}}
+        line["speedup_vs_fp64_plain"] = ms64 / ms
+        del u64, c64
+        if rank == 0:
+            from oracle import oracle as O
+            O.build()
+            scene, S = cpu_sample(W, 4.0)
+            nm_cpu, t = time_oracle(scene, W, 3)
+            cms = float(np.mean(t)) * 1e3
+            line["cpu_baseline"] = {
+                "value": nm_cpu * W.n_forcing / (cms / 1e3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"particles with centres in a {S}^3 sub-box of the bed ({scene.n_p} spheres, "
+                          f"{nm_cpu} markers) on a periodic {S}^3 grid; 3 steps, {cms:.0f} ms/step"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -81,6 +81,7 @@ typedef struct {
     int max_particles;       /* capacity of the context                        */
     int requires_grad;       /* 1: keep what ibm_backward needs                */
     int threads_per_block;   /* 0 = autotune; else 256, 512 or 1024 (CLUSTER)  */
+    int profile;             /* 1: time the main forcing kernel with CUDA events */
 } ibm_config;
 
 typedef struct ibm_ctx ibm_ctx;
@@ -164,6 +165,14 @@ ibm_status ibm_marker_bases(ibm_ctx *ctx, int64_t *base_out, int64_t *n_markers)
  * [5] distinct touched cells on the shared-memory path, [6] kernel launches
  * per step, [7] threads per block used. */
 ibm_status ibm_step_stats(ibm_ctx *ctx, int64_t *stats);
+
+/* Device time of the main forcing kernel (the shared-memory cluster kernel,
+ * or the plain interpolation+spreading kernels in PLAIN mode), measured with
+ * CUDA events recorded on the context's stream around each launch since the
+ * last reset; requires profile = 1 at create.  *total_ms and *count receive the
+ * summed time and the number of timed steps.  reset = 1 clears the record after
+ * reading.  Synchronises.  Errors: STATE (profile off), CUDA. */
+ibm_status ibm_kernel_timing(ibm_ctx *ctx, double *total_ms, int64_t *count, int reset);
 
 /* Human-readable status name; never NULL. */
 const char *ibm_status_string(ibm_status s);

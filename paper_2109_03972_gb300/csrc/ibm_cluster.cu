@@ -1,11 +1,950 @@
-// Cluster path (placeholder until the shared-memory kernel lands): FP32 plain
-// iterations over all particles.
+// Cluster path of the FP32 forcing step.
+//
+// Two particles interact within one forcing iteration only when a grid cell
+// lies in the stencils of markers of both (the 3x3x3 supports of Eq.
+// 3pt-stencil overlap).  Connected components of that relation ("clusters")
+// are independent for all n_F iterations of the outer forcing loop (Sec.
+// 2.2.2): no cell of one cluster is read or written by another.  So each
+// cluster is processed by one CTA that
+//   1. builds the exact set of touched cells (union of marker stencils) as
+//      per-row bitmasks over the cluster's box, and a compact slot for each
+//      touched cell (prefix sums of the masks),
+//   2. gathers u at the touched cells from HBM into shared memory once,
+//   3. runs all n_F iterations (interpolate -> force -> spread -> update)
+//      on the shared-memory copy, with __syncthreads between the phases,
+//   4. writes the touched cells back once, and the particle loads.
+// HBM sees one read and one write per touched cell per step instead of one
+// per iteration.  Clusters too large for one CTA's shared memory run the plain
+// FP32 path (one thread per marker, global atomics), which touches disjoint
+// cells and can therefore follow in any order.
+//
+// Clustering per step: particles are binned on a coarse grid, candidate pairs
+// (centre distance < a_p + a_q + 3 sqrt 3, the largest distance at which two
+// markers can have base cells within 2 of each other) are tested exactly
+// (some marker pair with |b_l - b_l'|_inf <= 2), and joined by a lock-free
+// union-find.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <vector>
+
+#include "ibm_device.cuh"
 #include "ibm_internal.h"
 
-ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
-    ibm_status s = ensure_field_ptrs(ctx, u_ptrs, f_out);
-    if (s != IBM_OK) return s;
-    return plain_iterations_f32(ctx, nullptr, ctx->n_p, tau, f_out != nullptr, ctx->cfg.n_forcing);
+#define CK(call, what)                                                  \
+    do {                                                                \
+        ibm_status _s = ibm_cuda_check(ctx, (call), what);              \
+        if (_s != IBM_OK) return _s;                                    \
+    } while (0)
+
+namespace {
+
+constexpr int kCapP = 64;        // particles per shared-memory cluster
+constexpr int kCapR = 3072;      // (row, 32-cell word) entries of the box bitmask
+constexpr int kBuckets = 1024;   // work-order buckets
+constexpr int kPairThreads = 128;
+constexpr int kPairCap = 1024;   // near-marker list in the exact pair test
+constexpr int kUnionSpin = 1 << 22;
+
+enum {
+    C_NCAND = 0,
+    C_NCLUST,
+    C_NFB,        // particles on the fallback path
+    C_WORK,       // persistent-kernel work counter
+    C_NITEMS,     // clusters on the shared-memory path
+    C_OVERFLOW,   // clusters that overflowed shared memory at run time
+    C_MAXCELLS,
+    C_TOUCHED,
+    C_FBMARK,     // markers on the fallback path
+    C_COUNT
+};
+
+struct ClusterScratch {
+    int cap_p = 0, cap_bins = 0, cap_cand = 0;
+    int nbins = 0, max_nl = -1, n_scenes = 0;
+    double bin_w = 0.0;
+    int *scene_bin_off = nullptr, *scene_nb = nullptr;
+    int *bin_cnt = nullptr, *bin_start = nullptr, *bin_cur = nullptr, *bin_items = nullptr;
+    int *parent = nullptr, *cand = nullptr, *cnt = nullptr;
+    long long *tot = nullptr;
+    int *root_flag = nullptr, *cid = nullptr, *pcl = nullptr, *poff = nullptr;
+    int *cl_np = nullptr, *cl_nm = nullptr, *cl_first = nullptr, *cl_cur = nullptr, *cl_box = nullptr;
+    int *cl_plist = nullptr, *cl_bkt = nullptr;
+    int *bkt_cnt = nullptr, *bkt_start = nullptr, *order = nullptr, *fb_list = nullptr;
+    int smem_bytes = 0, cap_c = 0, tpb = 0, kmax = 0;
+};
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *((const volatile int *)p); }
+
+__device__ int uf_find(int *parent, int x) {
+    for (int it = 0; it < kUnionSpin; ++it) {
+        const int p = ld_volatile(parent + x);
+        if (p == x) return x;
+        const int gp = ld_volatile(parent + p);
+        if (gp != p) atomicCAS(parent + x, p, gp);  // path halving; parents only decrease
+        x = p;
+    }
+    return -1;
 }
 
-void cluster_free(ibm_ctx *) {}
+__device__ bool uf_unite(int *parent, int a, int b) {
+    for (int it = 0; it < kUnionSpin; ++it) {
+        a = uf_find(parent, a);
+        b = uf_find(parent, b);
+        if (a < 0 || b < 0) return false;
+        if (a == b) return true;
+        if (a > b) { const int t = a; a = b; b = t; }
+        const int old = atomicCAS(parent + b, b, a);   // link the larger root under the smaller
+        if (old == b) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int scene_bin(const int *scene_nb, const int *scene_bin_off, const int32_t *dims,
+                                         int s, const double xi[3], int bc[3]) {
+    for (int c = 0; c < 3; ++c) {
+        const int n = dims[3 * s + c], nb = scene_nb[3 * s + c];
+        double w = xi[c] - floor(xi[c] / n) * n;          // wrapped into [0, n)
+        int b = (int)(w * nb / n);
+        b = min(max(b, 0), nb - 1);
+        bc[c] = b;
+    }
+    return scene_bin_off[s] + (bc[2] * scene_nb[3 * s + 1] + bc[1]) * scene_nb[3 * s] + bc[0];
+}
+
+// ------------------------------------------------------------- clustering
+
+__global__ void k_bin_count(int n_p, const PInfo *P, const int *scene_nb, const int *scene_bin_off,
+                            const int32_t *dims, int *bin_cnt, int *parent) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_p; p += gridDim.x * blockDim.x) {
+        int bc[3];
+        const int b = scene_bin(scene_nb, scene_bin_off, dims, P[p].scene, P[p].xi, bc);
+        atomicAdd(bin_cnt + b, 1);
+        parent[p] = p;
+    }
+}
+
+__global__ void k_bin_fill(int n_p, const PInfo *P, const int *scene_nb, const int *scene_bin_off,
+                           const int32_t *dims, const int *bin_start, int *bin_cur, int *bin_items) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_p; p += gridDim.x * blockDim.x) {
+        int bc[3];
+        const int b = scene_bin(scene_nb, scene_bin_off, dims, P[p].scene, P[p].xi, bc);
+        bin_items[bin_start[b] + atomicAdd(bin_cur + b, 1)] = p;
+    }
+}
+
+// Minimum-image offset of q relative to p, in whole periods (grid units).
+__device__ __forceinline__ void min_image_shift(const double xp[3], const double xq[3], const int32_t *dims,
+                                                int s, int sh[3]) {
+    for (int c = 0; c < 3; ++c) {
+        const int n = dims[3 * s + c];
+        sh[c] = -(int)llrint((xq[c] - xp[c]) / n) * n;
+    }
+}
+
+__global__ void k_candidates(int n_p, const PInfo *P, const int *scene_nb, const int *scene_bin_off,
+                             const int32_t *dims, const int *bin_start, const int *bin_items, int *cand,
+                             int cap_cand, int *cnt) {
+    const double lim = 3.0 * 1.7320508075688772 + 1e-6;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_p; p += gridDim.x * blockDim.x) {
+        const PInfo Pp = P[p];
+        const int s = Pp.scene;
+        int bc[3];
+        scene_bin(scene_nb, scene_bin_off, dims, s, Pp.xi, bc);
+        const int nbx = scene_nb[3 * s], nby = scene_nb[3 * s + 1], nbz = scene_nb[3 * s + 2];
+        const int lox = nbx >= 3 ? -1 : 0, hix = nbx >= 3 ? 1 : nbx - 1;
+        const int loy = nby >= 3 ? -1 : 0, hiy = nby >= 3 ? 1 : nby - 1;
+        const int loz = nbz >= 3 ? -1 : 0, hiz = nbz >= 3 ? 1 : nbz - 1;
+        for (int oz = loz; oz <= hiz; ++oz)
+            for (int oy = loy; oy <= hiy; ++oy)
+                for (int ox = lox; ox <= hix; ++ox) {
+                    const int bx = (bc[0] + ox + nbx) % nbx, by = (bc[1] + oy + nby) % nby,
+                              bz = (bc[2] + oz + nbz) % nbz;
+                    const int b = scene_bin_off[s] + (bz * nby + by) * nbx + bx;
+                    for (int i = bin_start[b]; i < bin_start[b + 1]; ++i) {
+                        const int q = bin_items[i];
+                        if (q <= p) continue;
+                        const PInfo &Pq = P[q];
+                        int sh[3];
+                        min_image_shift(Pp.xi, Pq.xi, dims, s, sh);
+                        double d2 = 0.0;
+                        for (int c = 0; c < 3; ++c) {
+                            const double dv = Pq.xi[c] + sh[c] - Pp.xi[c];
+                            d2 += dv * dv;
+                        }
+                        const double r = Pp.a + Pq.a + lim;
+                        if (d2 < r * r) {
+                            const int k = atomicAdd(cnt + C_NCAND, 1);
+                            if (k < cap_cand) {
+                                cand[2 * k] = p;
+                                cand[2 * k + 1] = q;
+                            }
+                        }
+                    }
+                }
+    }
+}
+
+// Exact test of one candidate pair: some markers l of p and l' of q with
+// |b_l - b_l'|_inf <= 2 (then their 3x3x3 stencils share a cell).  Uses the
+// same FP32-path base cells as the forcing kernels.
+__global__ void __launch_bounds__(kPairThreads) k_pair_test(const PInfo *P, const float *t32, const double *t64,
+                                                            const int32_t *dims, const int *cand, const int *cnt,
+                                                            int cap_cand, int *parent, int *err) {
+    __shared__ int3 qb[kPairCap];
+    __shared__ int nq, found, over;
+    const int ncand = min(cnt[C_NCAND], cap_cand);
+    for (int k = blockIdx.x; k < ncand; k += gridDim.x) {
+        const int p = cand[2 * k], q = cand[2 * k + 1];
+        const PInfo Pp = P[p], Pq = P[q];
+        int sh[3];
+        min_image_shift(Pp.xi, Pq.xi, dims, Pp.scene, sh);
+        if (threadIdx.x == 0) { nq = 0; found = 0; over = 0; }
+        __syncthreads();
+        const float rp = (float)(Pp.a + 3.0 * 1.7320508075688772 + 1.0);
+        const float rq = (float)(Pq.a + 3.0 * 1.7320508075688772 + 1.0);
+        for (int l = threadIdx.x; l < Pq.nl; l += blockDim.x) {
+            const float *t = t32 + 3ll * (Pq.toff + l);
+            float dd = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                const float v = (float)(Pq.xi[c] + sh[c] - Pp.xi[c]) + Pq.af * t[c];
+                dd += v * v;
+            }
+            if (dd > rp * rp) continue;
+            int3 b;
+            float fr;
+            b.x = marker_split32(Pq, t, t64 + 3ll * (Pq.toff + l), 0, &fr) + sh[0];
+            b.y = marker_split32(Pq, t, t64 + 3ll * (Pq.toff + l), 1, &fr) + sh[1];
+            b.z = marker_split32(Pq, t, t64 + 3ll * (Pq.toff + l), 2, &fr) + sh[2];
+            const int i = atomicAdd(&nq, 1);
+            if (i < kPairCap) qb[i] = b;
+            else over = 1;
+        }
+        __syncthreads();
+        if (over) {
+            if (threadIdx.x == 0 && !uf_unite(parent, p, q)) set_err(err, IBM_EBIT_TIMEOUT);
+            __syncthreads();
+            continue;
+        }
+        const int n = nq;
+        for (int l = threadIdx.x; l < Pp.nl && !found; l += blockDim.x) {
+            const float *t = t32 + 3ll * (Pp.toff + l);
+            float dd = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                const float v = (float)(Pp.xi[c] - Pq.xi[c] - sh[c]) + Pp.af * t[c];
+                dd += v * v;
+            }
+            if (dd > rq * rq) continue;
+            float fr;
+            const int bx = marker_split32(Pp, t, t64 + 3ll * (Pp.toff + l), 0, &fr);
+            const int by = marker_split32(Pp, t, t64 + 3ll * (Pp.toff + l), 1, &fr);
+            const int bz = marker_split32(Pp, t, t64 + 3ll * (Pp.toff + l), 2, &fr);
+            for (int j = 0; j < n; ++j) {
+                const int3 b = qb[j];
+                if (abs(b.x - bx) <= 2 && abs(b.y - by) <= 2 && abs(b.z - bz) <= 2) {
+                    found = 1;
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && found && !uf_unite(parent, p, q)) set_err(err, IBM_EBIT_TIMEOUT);
+        __syncthreads();
+    }
+}
+
+__global__ void k_roots(int n_p, int *parent, int *root_flag, int *err) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_p; p += gridDim.x * blockDim.x) {
+        const int r = uf_find(parent, p);
+        if (r < 0) { set_err(err, IBM_EBIT_TIMEOUT); root_flag[p] = 0; continue; }
+        root_flag[p] = (r == p);
+    }
+}
+
+__global__ void k_cluster_init(int n, int *cl_np, int *cl_nm, int *cl_cur, int *cl_box) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        cl_np[c] = 0;
+        cl_nm[c] = 0;
+        cl_cur[c] = 0;
+        for (int k = 0; k < 3; ++k) {
+            cl_box[12 * c + k] = INT_MAX;        // stencil box lo
+            cl_box[12 * c + 3 + k] = INT_MIN;    // stencil box hi
+            cl_box[12 * c + 6 + k] = INT_MAX;    // centre box lo
+            cl_box[12 * c + 9 + k] = INT_MIN;    // centre box hi
+        }
+    }
+}
+
+// Per particle: its cluster, the whole-period shift that unwraps it next to
+// the cluster's root, and the cluster's stencil box (floor(xi -+ a) -+ 1).
+__global__ void k_cluster_stats(int n_p, const PInfo *P, const int32_t *dims, int *parent, const int *cid,
+                                int *pcl, int *poff, int *cl_np, int *cl_nm, int *cl_box) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_p; p += gridDim.x * blockDim.x) {
+        const int r = uf_find(parent, p);
+        const int c = cid[r < 0 ? p : r];
+        pcl[p] = c;
+        const PInfo &Pp = P[p];
+        int sh[3];
+        min_image_shift(P[r < 0 ? p : r].xi, Pp.xi, dims, Pp.scene, sh);
+        atomicAdd(cl_np + c, 1);
+        atomicAdd(cl_nm + c, Pp.nl);
+        for (int k = 0; k < 3; ++k) {
+            poff[3 * p + k] = sh[k];
+            const int lo = (int)floor(Pp.xi[k] - Pp.a) - 1 + sh[k];
+            const int hi = (int)floor(Pp.xi[k] + Pp.a) + 1 + sh[k];
+            atomicMin(cl_box + 12 * c + k, lo);
+            atomicMax(cl_box + 12 * c + 3 + k, hi);
+            atomicMin(cl_box + 12 * c + 6 + k, Pp.base[k] + sh[k]);
+            atomicMax(cl_box + 12 * c + 9 + k, Pp.base[k] + sh[k]);
+        }
+    }
+}
+
+__global__ void k_cluster_fill(int n_p, const int *pcl, const int *cl_first, int *cl_cur, int *cl_plist) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_p; p += gridDim.x * blockDim.x) {
+        const int c = pcl[p];
+        cl_plist[cl_first[c] + atomicAdd(cl_cur + c, 1)] = p;
+    }
+}
+
+// Route each cluster: shared-memory path if it fits the CTA's capacities and
+// its box is consistently unwrapped, else the plain fallback.
+__global__ void k_cluster_route(const long long *n_clust_d, const PInfo *P, const int32_t *dims, const int *cl_np,
+                                const int *cl_nm, const int *cl_first, const int *cl_plist, const int *cl_box,
+                                int cap_m, int *cl_bkt, int *bkt_cnt, int *fb_list, int *cnt) {
+    const int n = (int)*n_clust_d;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const int np = cl_np[c], nm = cl_nm[c];
+        const int s = P[cl_plist[cl_first[c]]].scene;
+        bool ok = np <= kCapP && nm <= cap_m;
+        int R = 1;
+        for (int k = 0; k < 3; ++k) {
+            const int n_k = dims[3 * s + k];
+            const int ext = cl_box[12 * c + 3 + k] - cl_box[12 * c + k] + 1;
+            const int cext = cl_box[12 * c + 9 + k] - cl_box[12 * c + 6 + k] + 1;
+            ok = ok && ext <= n_k && 2 * cext < n_k;
+            R *= (k == 0) ? (ext + 31) / 32 : ext;
+        }
+        ok = ok && R <= kCapR;
+        if (ok) {
+            const int b = min(kBuckets - 1, nm / 8);
+            cl_bkt[c] = kBuckets - 1 - b;   // larger clusters first
+            atomicAdd(bkt_cnt + (kBuckets - 1 - b), 1);
+            atomicAdd(cnt + C_NITEMS, 1);
+        } else {
+            cl_bkt[c] = -1;
+            const int k0 = atomicAdd(cnt + C_NFB, np);
+            atomicAdd(cnt + C_FBMARK, nm);
+            for (int i = 0; i < np; ++i) fb_list[k0 + i] = cl_plist[cl_first[c] + i];
+        }
+    }
+}
+
+__global__ void k_order_fill(const long long *n_clust_d, const int *cl_bkt, const int *bkt_start, int *bkt_cur,
+                             int *order) {
+    const int n = (int)*n_clust_d;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const int b = cl_bkt[c];
+        if (b < 0) continue;
+        order[bkt_start[b] + atomicAdd(bkt_cur + b, 1)] = c;
+    }
+}
+
+// Single-block exclusive scan (same as the set-up scan), local copy.
+__global__ void k_scan1(const int *in, int *out, int n, long long *total) {
+    __shared__ long long part[1024];
+    const int t = threadIdx.x, T = blockDim.x;
+    const int chunk = (n + T - 1) / T;
+    const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
+    long long s = 0;
+    for (int i = lo; i < hi; ++i) s += in[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < T; o <<= 1) {
+        long long v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    long long run = part[t] - s;
+    for (int i = lo; i < hi; ++i) {
+        out[i] = (int)run;
+        run += in[i];
+    }
+    if (t == T - 1) {
+        *total = part[t];
+        out[n] = (int)part[t];
+    }
+}
+
+// --------------------------------------------------- shared-memory kernel
+
+struct PS {
+    PInfo P;
+    int off[3];     // add to an absolute base cell to get its box-relative cell
+    int mstart;     // first cluster-local marker
+    int gid;        // global particle index
+};
+
+struct KParams {
+    const PInfo *P;
+    const float *t32;
+    const double *t64;
+    const int32_t *dims;
+    float *const *uf;
+    float *const *ff;
+    const int *order, *cl_first, *cl_np, *cl_nm, *cl_box, *cl_plist, *poff;
+    int *cnt, *fb_list, *err;
+    double *FD, *TD;
+    int n_forcing, cap_c;
+    float finv;
+};
+
+// Block-wide exclusive scan of one int per thread; returns the prefix, and
+// the total through *total (valid after the call).
+template <int TPB>
+__device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < TPB / 32 ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < TPB / 32) sh[lane] = w;   // inclusive warp totals
+    }
+    __syncthreads();
+    const int pre = (wid ? sh[wid - 1] : 0) + x - v;
+    *total = sh[TPB / 32 - 1];
+    __syncthreads();
+    return pre;
+}
+
+struct MarkerLoc {
+    int ps;        // cluster-local particle
+    int l;         // marker within particle
+};
+
+__device__ __forceinline__ MarkerLoc locate(const PS *ps, int np, int m) {
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ps[mid].mstart <= m) lo = mid;
+        else hi = mid - 1;
+    }
+    MarkerLoc r;
+    r.ps = lo;
+    r.l = m - ps[lo].mstart;
+    return r;
+}
+
+// Box-relative base cell and weights of a marker (FP32 path).
+__device__ __forceinline__ void rel_stencil(const PS &s, const float *t32, const double *t64, int l, int b[3],
+                                            float w[3][3]) {
+    const float *t = t32 + 3ll * (s.P.toff + l);
+    const double *t6 = t64 + 3ll * (s.P.toff + l);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float fr;
+        b[c] = marker_split32(s.P, t, t6, c, &fr) + s.off[c];
+        phi3_weights(fr, w[c]);
+    }
+}
+
+__device__ __forceinline__ void row_slots(const uint2 *rt, int W, int By, const int b[3], int slot[9]) {
+    const int x = b[0] - 1;
+    const int wx = x >> 5;
+    const unsigned lowmask = (1u << (x & 31)) - 1u;
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const int row = (b[2] + dz - 1) * By + (b[1] + dy - 1);
+            const uint2 e = rt[row * W + wx];
+            slot[dz * 3 + dy] = (int)e.y + __popc(e.x & lowmask);
+        }
+}
+
+template <int TPB, int KMAX>
+__global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PS *s_ps = reinterpret_cast<PS *>(smem);
+    double *s_acc = reinterpret_cast<double *>(s_ps + kCapP);          // [kCapP][6]
+    uint2 *s_row = reinterpret_cast<uint2 *>(s_acc + 6 * kCapP);        // [kCapR]
+    float *s_u = reinterpret_cast<float *>(s_row + kCapR);              // [3][cap_c]
+    __shared__ int s_item, s_flag, s_scan[32], s_total;
+    const int cap_c = prm.cap_c;
+    const int tid = threadIdx.x, lane = tid & 31;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(prm.cnt + C_WORK, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= prm.cnt[C_NITEMS]) break;
+        const int c = prm.order[item];
+        const int np = prm.cl_np[c], nm = prm.cl_nm[c], first = prm.cl_first[c];
+        const int *box = prm.cl_box + 12 * c;
+        const int x0 = box[0], y0 = box[1], z0 = box[2];
+        const int Bx = box[3] - x0 + 1, By = box[4] - y0 + 1, Bz = box[5] - z0 + 1;
+        const int W = (Bx + 31) >> 5, R = By * Bz * W;
+        // particle table (sorted by global index so the marker order is fixed)
+        if (tid < np) {
+            const int p = prm.cl_plist[first + tid];
+            s_ps[tid].gid = p;
+        }
+        if (tid == 0) s_flag = 0;
+        __syncthreads();
+        if (tid == 0) {
+            for (int i = 1; i < np; ++i) {
+                const int v = s_ps[i].gid;
+                int j = i - 1;
+                while (j >= 0 && s_ps[j].gid > v) { s_ps[j + 1].gid = s_ps[j].gid; --j; }
+                s_ps[j + 1].gid = v;
+            }
+        }
+        __syncthreads();
+        if (tid < np) {
+            const int p = s_ps[tid].gid;
+            s_ps[tid].P = prm.P[p];
+            s_ps[tid].off[0] = prm.poff[3 * p] - x0;
+            s_ps[tid].off[1] = prm.poff[3 * p + 1] - y0;
+            s_ps[tid].off[2] = prm.poff[3 * p + 2] - z0;
+        }
+        for (int i = tid; i < 6 * np; i += TPB) s_acc[i] = 0.0;
+        for (int i = tid; i < R; i += TPB) s_row[i].x = 0u;
+        __syncthreads();
+        if (tid == 0) {
+            int m = 0;
+            for (int i = 0; i < np; ++i) { s_ps[i].mstart = m; m += s_ps[i].P.nl; }
+        }
+        __syncthreads();
+        const int scene = s_ps[0].P.scene;
+        const int nx = prm.dims[3 * scene], ny = prm.dims[3 * scene + 1], nz = prm.dims[3 * scene + 2];
+        const long long ncell = (long long)nx * ny * nz;
+
+        // 1. touched-cell bitmask (bounds-checked)
+        for (int m = tid; m < nm; m += TPB) {
+            const MarkerLoc L = locate(s_ps, np, m);
+            int b[3];
+            float w[3][3];
+            rel_stencil(s_ps[L.ps], prm.t32, prm.t64, L.l, b, w);
+            if (b[0] < 1 || b[0] > Bx - 2 || b[1] < 1 || b[1] > By - 2 || b[2] < 1 || b[2] > Bz - 2) {
+                s_flag = 1;
+                continue;
+            }
+            const int x = b[0] - 1, wx = x >> 5, bit = x & 31;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int row = (b[2] + dz) * By + (b[1] + dy);
+                    atomicOr(&s_row[row * W + wx].x, 7u << bit);
+                    if (bit > 29) atomicOr(&s_row[row * W + wx + 1].x, 7u >> (32 - bit));
+                }
+        }
+        __syncthreads();
+        // 2. compact slots: exclusive prefix of the popcounts
+        {
+            const int per = (R + TPB - 1) / TPB;
+            const int lo = min(R, tid * per), hi = min(R, lo + per);
+            int sum = 0;
+            for (int i = lo; i < hi; ++i) sum += __popc(s_row[i].x);
+            int total;
+            int run = block_excl_scan<TPB>(sum, s_scan, &total);
+            for (int i = lo; i < hi; ++i) {
+                s_row[i].y = (unsigned)run;
+                run += __popc(s_row[i].x);
+            }
+            if (tid == 0) s_total = total;
+        }
+        __syncthreads();
+        const int C = s_total;
+        if (s_flag || C > cap_c) {
+            // does not fit: hand the cluster to the plain path
+            if (tid == 0) {
+                const int k0 = atomicAdd(prm.cnt + C_NFB, np);
+                atomicAdd(prm.cnt + C_FBMARK, nm);
+                atomicAdd(prm.cnt + C_OVERFLOW, 1);
+                for (int i = 0; i < np; ++i) prm.fb_list[k0 + i] = s_ps[i].gid;
+            }
+            __syncthreads();
+            continue;
+        }
+        if (tid == 0) {
+            atomicMax(prm.cnt + C_MAXCELLS, C);
+            atomicAdd(prm.cnt + C_TOUCHED, C);
+        }
+        // 3. gather u at the touched cells
+        const float *__restrict__ ug = prm.uf[scene];
+        for (int i = tid; i < R; i += TPB) {
+            unsigned mask = s_row[i].x;
+            if (!mask) continue;
+            const int row = i / W, wx = i - row * W;
+            const int ry = row % By, rz = row / By;
+            const int gy = wrapi(y0 + ry, ny), gz = wrapi(z0 + rz, nz);
+            const long long rowbase = ((long long)gz * ny + gy) * nx;
+            int slot = (int)s_row[i].y;
+            while (mask) {
+                const int bit = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const long long g = rowbase + wrapi(x0 + 32 * wx + bit, nx);
+                s_u[slot] = ug[g];
+                s_u[cap_c + slot] = ug[ncell + g];
+                s_u[2 * cap_c + slot] = ug[2 * ncell + g];
+                ++slot;
+            }
+        }
+        __syncthreads();
+
+        // 4. the outer forcing loop on the shared-memory copy
+        for (int it = 0; it < prm.n_forcing; ++it) {
+            float ereg[KMAX][3];
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                const int m = tid + k * TPB;
+                float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                int pl = -1;
+                ereg[k][0] = ereg[k][1] = ereg[k][2] = 0.f;
+                if (m < nm) {
+                    const MarkerLoc L = locate(s_ps, np, m);
+                    const PS &s = s_ps[L.ps];
+                    int b[3];
+                    float w[3][3];
+                    rel_stencil(s, prm.t32, prm.t64, L.l, b, w);
+                    int slot[9];
+                    row_slots(s_row, W, By, b, slot);
+                    float U0 = 0.f, U1 = 0.f, U2 = 0.f;
+#pragma unroll
+                    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy) {
+                            const int sl = slot[dz * 3 + dy];
+                            const float wyz = w[2][dz] * w[1][dy];
+                            const float a0 = wyz * w[0][0], a1 = wyz * w[0][1], a2 = wyz * w[0][2];
+                            U0 += a0 * s_u[sl] + a1 * s_u[sl + 1] + a2 * s_u[sl + 2];
+                            U1 += a0 * s_u[cap_c + sl] + a1 * s_u[cap_c + sl + 1] + a2 * s_u[cap_c + sl + 2];
+                            U2 += a0 * s_u[2 * cap_c + sl] + a1 * s_u[2 * cap_c + sl + 1] +
+                                  a2 * s_u[2 * cap_c + sl + 2];
+                        }
+                    const float *t = prm.t32 + 3ll * (s.P.toff + L.l);
+                    const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
+                    const float ud0 = s.P.ud[0] + (s.P.om[1] * r2 - s.P.om[2] * r1);
+                    const float ud1 = s.P.ud[1] + (s.P.om[2] * r0 - s.P.om[0] * r2);
+                    const float ud2 = s.P.ud[2] + (s.P.om[0] * r1 - s.P.om[1] * r0);
+                    const float e0 = ud0 - U0, e1 = ud1 - U1, e2 = ud2 - U2;
+                    ereg[k][0] = e0; ereg[k][1] = e1; ereg[k][2] = e2;
+                    const float D = s.P.D;
+                    v[0] = e0 * D; v[1] = e1 * D; v[2] = e2 * D;
+                    v[3] = r1 * v[2] - r2 * v[1];
+                    v[4] = r2 * v[0] - r0 * v[2];
+                    v[5] = r0 * v[1] - r1 * v[0];
+                    pl = L.ps;
+                }
+                // per-particle loads: warp-segmented sums, FP64 accumulation
+                unsigned act = __ballot_sync(0xffffffffu, pl >= 0);
+                while (act) {
+                    const int leader = __ffs(act) - 1;
+                    const int lp = __shfl_sync(0xffffffffu, pl, leader);
+                    const bool mine = (pl == lp);
+                    act &= ~__ballot_sync(0xffffffffu, mine);
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const float x = warp_sum(mine ? v[q] : 0.f);
+                        if (lane == leader) atomicAdd(&s_acc[6 * lp + q], (double)x);
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                const int m = tid + k * TPB;
+                if (m < nm) {
+                    const MarkerLoc L = locate(s_ps, np, m);
+                    const PS &s = s_ps[L.ps];
+                    int b[3];
+                    float w[3][3];
+                    rel_stencil(s, prm.t32, prm.t64, L.l, b, w);
+                    int slot[9];
+                    row_slots(s_row, W, By, b, slot);
+                    const float D = s.P.D;
+                    const float g0 = ereg[k][0] * D, g1 = ereg[k][1] * D, g2 = ereg[k][2] * D;
+#pragma unroll
+                    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy) {
+                            const int sl = slot[dz * 3 + dy];
+                            const float wyz = w[2][dz] * w[1][dy];
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx) {
+                                const float a = wyz * w[0][dx];
+                                atomicAdd(&s_u[sl + dx], a * g0);
+                                atomicAdd(&s_u[cap_c + sl + dx], a * g1);
+                                atomicAdd(&s_u[2 * cap_c + sl + dx], a * g2);
+                            }
+                        }
+                }
+            }
+            __syncthreads();
+        }
+
+        // 5. write back the touched cells (and the total force if requested)
+        float *__restrict__ uo = prm.uf[scene];
+        float *__restrict__ fo = prm.ff ? prm.ff[scene] : nullptr;
+        for (int i = tid; i < R; i += TPB) {
+            unsigned mask = s_row[i].x;
+            if (!mask) continue;
+            const int row = i / W, wx = i - row * W;
+            const int ry = row % By, rz = row / By;
+            const int gy = wrapi(y0 + ry, ny), gz = wrapi(z0 + rz, nz);
+            const long long rowbase = ((long long)gz * ny + gy) * nx;
+            int slot = (int)s_row[i].y;
+            while (mask) {
+                const int bit = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const long long g = rowbase + wrapi(x0 + 32 * wx + bit, nx);
+                if (fo) {
+                    fo[g] = (s_u[slot] - uo[g]) * prm.finv;
+                    fo[ncell + g] = (s_u[cap_c + slot] - uo[ncell + g]) * prm.finv;
+                    fo[2 * ncell + g] = (s_u[2 * cap_c + slot] - uo[2 * ncell + g]) * prm.finv;
+                }
+                uo[g] = s_u[slot];
+                uo[ncell + g] = s_u[cap_c + slot];
+                uo[2 * ncell + g] = s_u[2 * cap_c + slot];
+                ++slot;
+            }
+        }
+        if (tid < np) {
+            const int p = s_ps[tid].gid;
+            for (int q = 0; q < 3; ++q) {
+                prm.FD[3 * p + q] = s_acc[6 * tid + q];
+                prm.TD[3 * p + q] = s_acc[6 * tid + 3 + q];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    return (int)std::max(1ll, std::min(g, 65535ll * 8));
+}
+
+template <int TPB, int KMAX>
+static int max_dyn_smem() {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int statics = 32 * 4 + 16;   // s_item, s_flag, s_scan, s_total
+    return optin - statics - 1024;
+}
+
+}  // namespace
+
+// ================================================================= host side
+
+void cluster_free(ibm_ctx *ctx) {
+    ClusterScratch *S = reinterpret_cast<ClusterScratch *>(ctx->cl);
+    if (!S) return;
+    int *ptrs[] = {S->scene_bin_off, S->scene_nb, S->bin_cnt, S->bin_start, S->bin_cur, S->bin_items,
+                   S->parent, S->cand, S->cnt, S->root_flag, S->cid, S->pcl, S->poff, S->cl_np, S->cl_nm,
+                   S->cl_first, S->cl_cur, S->cl_box, S->cl_plist, S->cl_bkt, S->bkt_cnt, S->bkt_start,
+                   S->order, S->fb_list};
+    for (int *p : ptrs)
+        if (p) cudaFree(p);
+    if (S->tot) cudaFree(S->tot);
+    delete S;
+    ctx->cl = nullptr;
+}
+
+static ibm_status cluster_alloc(ibm_ctx *ctx) {
+    ClusterScratch *S = reinterpret_cast<ClusterScratch *>(ctx->cl);
+    const int np = std::max(ctx->n_p, 1);
+    const bool realloc_p = !S || S->cap_p < ctx->cap_p;
+    if (!S) {
+        S = new ClusterScratch();
+        ctx->cl = S;
+    }
+    // bin layout from the largest particle: width >= 2 a_max + 3 sqrt 3 (+1)
+    const double q_max = std::sqrt((ctx->max_nl + 0.5) / M_PI) + 1e-9;
+    const double bw = q_max + 3.0 * std::sqrt(3.0) + 1.0;
+    if (realloc_p || S->max_nl != ctx->max_nl || S->n_scenes != ctx->cfg.n_scenes) {
+        std::vector<int> off(ctx->cfg.n_scenes + 1), nb(3 * ctx->cfg.n_scenes);
+        long long total = 0;
+        for (int s = 0; s < ctx->cfg.n_scenes; ++s) {
+            off[s] = (int)total;
+            long long cells = 1;
+            for (int c = 0; c < 3; ++c) {
+                nb[3 * s + c] = std::max(1, (int)std::floor(ctx->dims_h[3 * s + c] / bw));
+                cells *= nb[3 * s + c];
+            }
+            total += cells;
+        }
+        off[ctx->cfg.n_scenes] = (int)total;
+        if (total > (1 << 28)) return ibm_fail(ctx, IBM_ERR_CAPACITY, "too many particle bins");
+        if (S->scene_bin_off) cudaFree(S->scene_bin_off);
+        if (S->scene_nb) cudaFree(S->scene_nb);
+        CK(cudaMalloc(&S->scene_bin_off, off.size() * sizeof(int)), "alloc bins");
+        CK(cudaMalloc(&S->scene_nb, nb.size() * sizeof(int)), "alloc bins");
+        CK(cudaMemcpy(S->scene_bin_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(S->scene_nb, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice), "copy");
+        if ((int)total > S->cap_bins) {
+            for (int **p : {&S->bin_cnt, &S->bin_start, &S->bin_cur})
+                if (*p) cudaFree(*p);
+            CK(cudaMalloc(&S->bin_cnt, (total + 1) * sizeof(int)), "alloc bins");
+            CK(cudaMalloc(&S->bin_start, (total + 1) * sizeof(int)), "alloc bins");
+            CK(cudaMalloc(&S->bin_cur, (total + 1) * sizeof(int)), "alloc bins");
+            S->cap_bins = (int)total;
+        }
+        S->nbins = (int)total;
+        S->max_nl = ctx->max_nl;
+        S->n_scenes = ctx->cfg.n_scenes;
+        S->bin_w = bw;
+    }
+    if (realloc_p) {
+        const int cp = std::max(ctx->cap_p, np);
+        int **arrs[] = {&S->bin_items, &S->parent, &S->root_flag, &S->cid, &S->pcl, &S->cl_np, &S->cl_nm,
+                        &S->cl_first, &S->cl_cur, &S->cl_plist, &S->cl_bkt, &S->order, &S->fb_list};
+        for (int **p : arrs) {
+            if (*p) cudaFree(*p);
+            CK(cudaMalloc(p, (size_t)(cp + 1) * sizeof(int)), "alloc cluster scratch");
+        }
+        if (S->poff) cudaFree(S->poff);
+        if (S->cl_box) cudaFree(S->cl_box);
+        CK(cudaMalloc(&S->poff, 3 * (size_t)cp * sizeof(int)), "alloc cluster scratch");
+        CK(cudaMalloc(&S->cl_box, 12 * (size_t)cp * sizeof(int)), "alloc cluster scratch");
+        S->cap_cand = std::max(1 << 16, 16 * cp);
+        if (S->cand) cudaFree(S->cand);
+        CK(cudaMalloc(&S->cand, 2 * (size_t)S->cap_cand * sizeof(int)), "alloc candidates");
+        if (!S->cnt) CK(cudaMalloc(&S->cnt, C_COUNT * sizeof(int)), "alloc counters");
+        if (!S->tot) CK(cudaMalloc(&S->tot, 4 * sizeof(long long)), "alloc totals");
+        if (!S->bkt_cnt) CK(cudaMalloc(&S->bkt_cnt, (kBuckets + 1) * sizeof(int)), "alloc buckets");
+        if (!S->bkt_start) CK(cudaMalloc(&S->bkt_start, (kBuckets + 1) * sizeof(int) * 2), "alloc buckets");
+        S->cap_p = cp;
+    }
+    return IBM_OK;
+}
+
+template <int TPB, int KMAX>
+static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams &prm) {
+    auto kern = k_cluster_forcing<TPB, KMAX>;
+    if (S->smem_bytes == 0 || S->tpb != TPB) {
+        const int smem = max_dyn_smem<TPB, KMAX>();
+        const int fixed = (int)(sizeof(PS) * kCapP + sizeof(double) * 6 * kCapP + sizeof(uint2) * kCapR);
+        S->cap_c = ((smem - fixed) / 12) & ~31;
+        S->smem_bytes = fixed + 12 * S->cap_c;
+        S->tpb = TPB;
+        S->kmax = KMAX;
+        CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S->smem_bytes),
+           "set shared memory size");
+    }
+    prm.cap_c = S->cap_c;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, S->smem_bytes), "occupancy");
+    const int grid = std::max(1, nsm * std::max(per_sm, 1));
+    kern<<<grid, TPB, S->smem_bytes, ctx->stream>>>(prm);
+    return ibm_cuda_check(ctx, cudaGetLastError(), "cluster kernel");
+}
+
+ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
+    ibm_status st = ensure_field_ptrs(ctx, u_ptrs, f_out);
+    if (st != IBM_OK) return st;
+    st = cluster_alloc(ctx);
+    if (st != IBM_OK) return st;
+    ClusterScratch *S = reinterpret_cast<ClusterScratch *>(ctx->cl);
+    const int n = ctx->n_p;
+    cudaStream_t sm = ctx->stream;
+    const int tpb = ctx->cfg.threads_per_block ? ctx->cfg.threads_per_block : 512;
+    const int kmax = tpb == 1024 ? 4 : (tpb == 512 ? 8 : 16);
+    const int cap_m = tpb * kmax;
+
+    CK(cudaMemsetAsync(S->cnt, 0, C_COUNT * sizeof(int), sm), "zero counters");
+    CK(cudaMemsetAsync(S->bin_cnt, 0, (S->nbins + 1) * sizeof(int), sm), "zero bins");
+    CK(cudaMemsetAsync(S->bin_cur, 0, (S->nbins + 1) * sizeof(int), sm), "zero bins");
+    CK(cudaMemsetAsync(S->bkt_cnt, 0, (kBuckets + 1) * sizeof(int), sm), "zero buckets");
+    CK(cudaMemsetAsync(S->bkt_start + kBuckets + 1, 0, (kBuckets + 1) * sizeof(int), sm), "zero buckets");
+    const int gb = grid_for(n, 256);
+    k_bin_count<<<gb, 256, 0, sm>>>(n, ctx->pinfo, S->scene_nb, S->scene_bin_off, ctx->dims_d, S->bin_cnt,
+                                    S->parent);
+    k_scan1<<<1, 1024, 0, sm>>>(S->bin_cnt, S->bin_start, S->nbins, S->tot);
+    k_bin_fill<<<gb, 256, 0, sm>>>(n, ctx->pinfo, S->scene_nb, S->scene_bin_off, ctx->dims_d, S->bin_start,
+                                   S->bin_cur, S->bin_items);
+    k_candidates<<<gb, 256, 0, sm>>>(n, ctx->pinfo, S->scene_nb, S->scene_bin_off, ctx->dims_d, S->bin_start,
+                                     S->bin_items, S->cand, S->cap_cand, S->cnt);
+    k_pair_test<<<std::min(S->cap_cand, 152 * 16), kPairThreads, 0, sm>>>(
+        ctx->pinfo, ctx->tmpl32, ctx->tmpl64, ctx->dims_d, S->cand, S->cnt, S->cap_cand, S->parent, ctx->err_d);
+    k_roots<<<gb, 256, 0, sm>>>(n, S->parent, S->root_flag, ctx->err_d);
+    k_scan1<<<1, 1024, 0, sm>>>(S->root_flag, S->cid, n, S->tot + 1);
+    k_cluster_init<<<gb, 256, 0, sm>>>(n, S->cl_np, S->cl_nm, S->cl_cur, S->cl_box);
+    k_cluster_stats<<<gb, 256, 0, sm>>>(n, ctx->pinfo, ctx->dims_d, S->parent, S->cid, S->pcl, S->poff,
+                                        S->cl_np, S->cl_nm, S->cl_box);
+    k_scan1<<<1, 1024, 0, sm>>>(S->cl_np, S->cl_first, n, S->tot + 2);
+    k_cluster_fill<<<gb, 256, 0, sm>>>(n, S->pcl, S->cl_first, S->cl_cur, S->cl_plist);
+    k_cluster_route<<<gb, 256, 0, sm>>>(S->tot + 1, ctx->pinfo, ctx->dims_d, S->cl_np, S->cl_nm, S->cl_first,
+                                        S->cl_plist, S->cl_box, cap_m, S->cl_bkt, S->bkt_cnt, S->fb_list, S->cnt);
+    k_scan1<<<1, 1024, 0, sm>>>(S->bkt_cnt, S->bkt_start, kBuckets, S->tot + 3);
+    k_order_fill<<<gb, 256, 0, sm>>>(S->tot + 1, S->cl_bkt, S->bkt_start, S->bkt_start + kBuckets + 1, S->order);
+    ctx->launches += 13;
+
+    KParams prm;
+    prm.P = ctx->pinfo;
+    prm.t32 = ctx->tmpl32;
+    prm.t64 = ctx->tmpl64;
+    prm.dims = ctx->dims_d;
+    prm.uf = reinterpret_cast<float *const *>(ctx->uptr_d);
+    prm.ff = f_out ? reinterpret_cast<float *const *>(ctx->fptr_d) : nullptr;
+    prm.order = S->order;
+    prm.cl_first = S->cl_first;
+    prm.cl_np = S->cl_np;
+    prm.cl_nm = S->cl_nm;
+    prm.cl_box = S->cl_box;
+    prm.cl_plist = S->cl_plist;
+    prm.poff = S->poff;
+    prm.cnt = S->cnt;
+    prm.fb_list = S->fb_list;
+    prm.err = ctx->err_d;
+    prm.FD = ctx->FD;
+    prm.TD = ctx->TD;
+    prm.n_forcing = ctx->cfg.n_forcing;
+    prm.finv = (float)(1.0 / tau);
+    prof_begin(ctx);
+    if (tpb == 1024) st = launch_cluster_kernel<1024, 4>(ctx, S, prm);
+    else if (tpb == 512) st = launch_cluster_kernel<512, 8>(ctx, S, prm);
+    else st = launch_cluster_kernel<256, 16>(ctx, S, prm);
+    prof_end(ctx);
+    if (st != IBM_OK) return st;
+    ctx->launches += 1;
+    // clusters that did not fit: plain FP32 iterations over their particles
+    st = plain_iterations_f32(ctx, S->fb_list, n, S->cnt + C_NFB, tau, f_out != nullptr, ctx->cfg.n_forcing);
+    if (st != IBM_OK) return st;
+    return IBM_OK;
+}
+
+ibm_status cluster_stats(ibm_ctx *ctx, int64_t *stats) {
+    ClusterScratch *S = reinterpret_cast<ClusterScratch *>(ctx->cl);
+    if (!S) return IBM_OK;
+    int c[C_COUNT];
+    long long nclust = 0;
+    CK(cudaMemcpyAsync(c, S->cnt, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream), "read stats");
+    CK(cudaMemcpyAsync(&nclust, S->tot + 1, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream), "read stats");
+    CK(cudaStreamSynchronize(ctx->stream), "sync stats");
+    stats[1] = nclust;
+    stats[2] = c[C_NITEMS] - c[C_OVERFLOW];
+    stats[3] = c[C_FBMARK];
+    stats[4] = c[C_MAXCELLS];
+    stats[5] = c[C_TOUCHED];
+    stats[7] = S->tpb;
+    return IBM_OK;
+}

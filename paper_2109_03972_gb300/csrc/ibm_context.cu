@@ -57,7 +57,37 @@ static ibm_status dev_alloc(ibm_ctx *ctx, T **p, size_t n) {
     return ibm_cuda_check(ctx, cudaMalloc((void **)p, n * sizeof(T)), "cudaMalloc");
 }
 
+static const int kProfPairs = 512;
+
+static void prof_fold(ibm_ctx *ctx) {
+    // read the recorded pairs (synchronises on the last event)
+    if (ctx->prof_n == 0) return;
+    cudaEventSynchronize(ctx->prof_ev[2 * (ctx->prof_n - 1) + 1]);
+    for (int i = 0; i < ctx->prof_n; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]) == cudaSuccess) {
+            ctx->prof_ms += ms;
+            ctx->prof_count += 1;
+        }
+    }
+    ctx->prof_n = 0;
+}
+
+void prof_begin(ibm_ctx *ctx) {
+    if (!ctx->cfg.profile || ctx->prof_ev.empty()) return;
+    if (ctx->prof_n == kProfPairs) prof_fold(ctx);
+    cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], ctx->stream);
+}
+
+void prof_end(ibm_ctx *ctx) {
+    if (!ctx->cfg.profile || ctx->prof_ev.empty()) return;
+    cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);
+    ctx->prof_n += 1;
+}
+
 static void free_all(ibm_ctx *ctx) {
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    ctx->prof_ev.clear();
     void *ptrs[] = {ctx->dims_d, ctx->x, ctx->up, ctx->om, ctx->d, ctx->rho, ctx->scene,
                     ctx->nl, ctx->moff, ctx->toff, ctx->pinfo, ctx->tmpl64, ctx->tmpl32,
                     ctx->tmpl_of_nl, ctx->FD, ctx->TD, ctx->Fout, ctx->Tout, ctx->x_new,
@@ -161,6 +191,16 @@ ibm_status ibm_create(const ibm_config *cfg, void *cuda_stream, ibm_ctx **out) {
         return s;
     }
     ctx->cap_p = cp;
+    if (cfg->profile) {
+        ctx->prof_ev.resize(2 * kProfPairs);
+        for (auto &e : ctx->prof_ev) {
+            if ((s = ibm_cuda_check(ctx, cudaEventCreate(&e), "cudaEventCreate")) != IBM_OK) {
+                free_all(ctx);
+                delete ctx;
+                return s;
+            }
+        }
+    }
     *out = ctx;
     return IBM_OK;
 }
@@ -226,6 +266,7 @@ ibm_status ibm_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void 
     if (!(tau > 0.0) || !std::isfinite(tau)) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "tau must be > 0");
     ctx->have_step = false;
     ctx->last_tau = tau;
+    ctx->launches = 0;
     const size_t esz = ctx->cfg.precision == IBM_FP64 ? sizeof(double) : sizeof(float);
     if (ctx->cfg.requires_grad) {
         // keep u^0 for the backward pass
@@ -322,11 +363,26 @@ ibm_status ibm_marker_bases(ibm_ctx *ctx, int64_t *base_out, int64_t *n_markers)
     return s;
 }
 
+ibm_status ibm_kernel_timing(ibm_ctx *ctx, double *total_ms, int64_t *count, int reset) {
+    if (!ctx) return IBM_ERR_INVALID_ARG;
+    if (!ctx->cfg.profile) return ibm_fail(ctx, IBM_ERR_STATE, "context created without profile");
+    prof_fold(ctx);
+    if (total_ms) *total_ms = ctx->prof_ms;
+    if (count) *count = ctx->prof_count;
+    if (reset) {
+        ctx->prof_ms = 0.0;
+        ctx->prof_count = 0;
+    }
+    return IBM_OK;
+}
+
 ibm_status ibm_step_stats(ibm_ctx *ctx, int64_t *stats) {
     if (!ctx || !stats) return IBM_ERR_INVALID_ARG;
     ibm_status s = ibm_check_err_word(ctx);
-    for (int i = 0; i < 8; ++i) stats[i] = ctx->stats[i];
+    for (int i = 0; i < 8; ++i) stats[i] = 0;
     stats[0] = ctx->n_markers;
+    stats[6] = ctx->launches;
+    if (s == IBM_OK && ctx->cfg.spread_mode != IBM_SPREAD_PLAIN) s = cluster_stats(ctx, stats);
     return s;
 }
 

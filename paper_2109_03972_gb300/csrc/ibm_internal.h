@@ -94,6 +94,12 @@ struct ibm_ctx {
     bool have_forward = false;
     double last_tau = 0.0;
 
+    // profiling: event pairs around the main kernel of each step
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_n = 0;           // recorded pairs since reset
+    double prof_ms = 0.0;     // folded-in time of pairs already read
+    long long prof_count = 0;
+
     int *err_d = nullptr;
     int *err_h = nullptr;     // pinned
     bool have_step = false;
@@ -119,8 +125,14 @@ ibm_status launch_marker_bases(ibm_ctx *ctx, int64_t *base_d);
 ibm_status launch_scan_int(ibm_ctx *ctx, const int *in, int *out_excl, int n, long long *total_d);
 
 ibm_status ensure_field_ptrs(ibm_ctx *ctx, void *const *u_ptrs, void *const *f_out);
-ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, double tau, bool with_f, int n_it);
+ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
+                                bool with_f, int n_it);
+
+// profiling (ibm_context.cu): bracket the main kernel of a step
+void prof_begin(ibm_ctx *ctx);
+void prof_end(ibm_ctx *ctx);
 
 // cluster path (ibm_cluster.cu)
 ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out);
 void cluster_free(ibm_ctx *ctx);
+ibm_status cluster_stats(ibm_ctx *ctx, int64_t *stats);

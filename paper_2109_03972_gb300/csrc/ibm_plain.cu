@@ -235,10 +235,12 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[32]) {
 // adds sum e D and sum r x e D to the particle's load accumulators.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_plain_interp(
-    const PInfo *__restrict__ P, const int *__restrict__ plist, int n_list, const double *__restrict__ t64,
-    const float *__restrict__ t32, const double *__restrict__ up, const double *__restrict__ om,
-    const int32_t *__restrict__ dims, T *const *uf, T *__restrict__ ebuf, double *FD, double *TD) {
+    const PInfo *__restrict__ P, const int *__restrict__ plist, int n_list, const int *__restrict__ n_list_d,
+    const double *__restrict__ t64, const float *__restrict__ t32, const double *__restrict__ up,
+    const double *__restrict__ om, const int32_t *__restrict__ dims, T *const *uf, T *__restrict__ ebuf,
+    double *FD, double *TD) {
     __shared__ double sh[6][32];
+    if (n_list_d) n_list = *n_list_d;
     for (int k = blockIdx.x; k < n_list; k += gridDim.x) {
         const int p = plist ? plist[k] : k;
         const PInfo Pp = P[p];
@@ -302,9 +304,10 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
 // u += scale * sum_l w D_l v_l for v = e (scale 1).  Optional f_out += that / tau.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_plain_spread(
-    const PInfo *__restrict__ P, const int *__restrict__ plist, int n_list, const double *__restrict__ t64,
-    const float *__restrict__ t32, const int32_t *__restrict__ dims, const T *__restrict__ vbuf, T scale,
-    T *const *uf, T *const *ff, T finv) {
+    const PInfo *__restrict__ P, const int *__restrict__ plist, int n_list, const int *__restrict__ n_list_d,
+    const double *__restrict__ t64, const float *__restrict__ t32, const int32_t *__restrict__ dims,
+    const T *__restrict__ vbuf, T scale, T *const *uf, T *const *ff, T finv) {
+    if (n_list_d) n_list = *n_list_d;
     for (int k = blockIdx.x; k < n_list; k += gridDim.x) {
         const int p = plist ? plist[k] : k;
         const PInfo Pp = P[p];
@@ -764,33 +767,40 @@ ibm_status launch_marker_bases(ibm_ctx *ctx, int64_t *base_d) {
 
 // One plain iteration over the particles in plist (all when plist == NULL).
 template <typename T>
-static void plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, double tau, bool with_f) {
+static void plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
+                            bool with_f) {
     const int nb = blocks_for_particles(n_list);
     T *const *uf = reinterpret_cast<T *const *>(ctx->uptr_d);
     T *const *ff = with_f ? reinterpret_cast<T *const *>(ctx->fptr_d) : nullptr;
-    k_plain_interp<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, ctx->tmpl64, ctx->tmpl32,
-                                                      ctx->up, ctx->om, ctx->dims_d, uf,
+    k_plain_interp<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
+                                                      ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, uf,
                                                       reinterpret_cast<T *>(ctx->ebuf), ctx->FD, ctx->TD);
-    k_plain_spread<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, ctx->tmpl64, ctx->tmpl32,
-                                                      ctx->dims_d, reinterpret_cast<const T *>(ctx->ebuf), T(1),
-                                                      uf, ff, T(1.0 / tau));
+    k_plain_spread<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
+                                                      ctx->tmpl32, ctx->dims_d,
+                                                      reinterpret_cast<const T *>(ctx->ebuf), T(1), uf, ff,
+                                                      T(1.0 / tau));
     ctx->launches += 2;
 }
 
-ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, double tau, bool with_f, int n_it) {
-    for (int it = 0; it < n_it; ++it) plain_iteration<float>(ctx, plist, n_list, tau, with_f);
+// FP32 plain iterations over a particle list whose length is n_list, or, when
+// n_list_d is given, the device value *n_list_d (at most n_list).
+ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
+                                bool with_f, int n_it) {
+    for (int it = 0; it < n_it; ++it) plain_iteration<float>(ctx, plist, n_list, n_list_d, tau, with_f);
     return ibm_cuda_check(ctx, cudaGetLastError(), "plain iteration");
 }
 
 ibm_status plain_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
     ibm_status s = ensure_field_ptrs(ctx, u_ptrs, f_out);
     if (s != IBM_OK) return s;
+    prof_begin(ctx);
     for (int it = 0; it < ctx->cfg.n_forcing; ++it) {
         if (ctx->cfg.precision == IBM_FP64)
-            plain_iteration<double>(ctx, nullptr, ctx->n_p, tau, f_out != nullptr);
+            plain_iteration<double>(ctx, nullptr, ctx->n_p, nullptr, tau, f_out != nullptr);
         else
-            plain_iteration<float>(ctx, nullptr, ctx->n_p, tau, f_out != nullptr);
+            plain_iteration<float>(ctx, nullptr, ctx->n_p, nullptr, tau, f_out != nullptr);
     }
+    prof_end(ctx);
     return ibm_cuda_check(ctx, cudaGetLastError(), "plain forcing step");
 }
 
@@ -860,8 +870,8 @@ static ibm_status backward_impl(ibm_ctx *ctx, void *const *grad_u_out, void *con
         k_bw_fwd<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32, ctx->up, ctx->om,
                                                     ctx->dims_d, reinterpret_cast<T *const *>(ctx->uptr_d), hinv,
                                                     e_m, g_m);
-        k_plain_spread<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, nullptr, ctx->n_p, ctx->tmpl64, ctx->tmpl32,
-                                                          ctx->dims_d, e_m, T(1),
+        k_plain_spread<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, nullptr, ctx->n_p, nullptr, ctx->tmpl64,
+                                                          ctx->tmpl32, ctx->dims_d, e_m, T(1),
                                                           reinterpret_cast<T *const *>(ctx->uptr_d), nullptr, T(0));
     }
     // reverse sweep on the gradient field
@@ -873,8 +883,9 @@ static ibm_status backward_impl(ibm_ctx *ctx, void *const *grad_u_out, void *con
         k_bw_adj<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32, ctx->dims_d,
                                                     reinterpret_cast<T *const *>(ctx->uptr_d), hinv, e_m, g_m,
                                                     reinterpret_cast<T *>(ctx->ebuf), reinterpret_cast<double *>(ctx->gmk));
-        k_plain_spread<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, nullptr, ctx->n_p, ctx->tmpl64, ctx->tmpl32,
-                                                          ctx->dims_d, reinterpret_cast<const T *>(ctx->ebuf), T(-1),
+        k_plain_spread<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, nullptr, ctx->n_p, nullptr, ctx->tmpl64,
+                                                          ctx->tmpl32, ctx->dims_d,
+                                                          reinterpret_cast<const T *>(ctx->ebuf), T(-1),
                                                           reinterpret_cast<T *const *>(ctx->uptr_d), nullptr, T(0));
     }
     k_bw_reduce<<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64,

@@ -24,7 +24,7 @@ STATUS = {0: "IBM_OK", 1: "IBM_ERR_INVALID_ARG", 2: "IBM_ERR_CUDA", 3: "IBM_ERR_
 
 EXPORTED = ["ibm_create", "ibm_destroy", "ibm_set_particles", "ibm_forcing_step",
             "ibm_particle_loads", "ibm_backward", "ibm_marker_bases", "ibm_step_stats",
-            "ibm_status_string", "ibm_last_error"]
+            "ibm_kernel_timing", "ibm_status_string", "ibm_last_error"]
 
 
 class IBMError(RuntimeError):
@@ -39,7 +39,8 @@ class _Config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("spread_mode", ctypes.c_int),
                 ("newton_euler", ctypes.c_int), ("rho_f", ctypes.c_double),
                 ("g", ctypes.c_double * 3), ("max_particles", ctypes.c_int),
-                ("requires_grad", ctypes.c_int), ("threads_per_block", ctypes.c_int)]
+                ("requires_grad", ctypes.c_int), ("threads_per_block", ctypes.c_int),
+                ("profile", ctypes.c_int)]
 
 
 _lib = None
@@ -63,11 +64,12 @@ def load_library(path: str = LIB_PATH):
     L.ibm_backward.argtypes = [vp, vp, vp, vp, vp, vp]
     L.ibm_marker_bases.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
     L.ibm_step_stats.argtypes = [vp, vp]
+    L.ibm_kernel_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i]
     L.ibm_status_string.argtypes = [i]
     L.ibm_status_string.restype = ctypes.c_char_p
     L.ibm_last_error.argtypes = [vp]
     L.ibm_last_error.restype = ctypes.c_char_p
-    for n in EXPORTED[:8]:
+    for n in EXPORTED[:9]:
         getattr(L, n).restype = i
     _lib = L
     return L
@@ -100,6 +102,7 @@ class Config:
     requires_grad: bool = False
     kernel_width: int = 3
     threads_per_block: int = 0
+    profile: bool = False
     extra: dict = field(default_factory=dict)
 
 
@@ -126,6 +129,7 @@ class Context:
         c.max_particles = cfg.max_particles
         c.requires_grad = int(cfg.requires_grad)
         c.threads_per_block = cfg.threads_per_block
+        c.profile = int(cfg.profile)
         h = ctypes.c_void_p()
         st = self.L.ibm_create(ctypes.byref(c), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
         if st != 0:
@@ -195,6 +199,11 @@ class Context:
         out = np.empty((n.value, 3), dtype=np.int64)
         self._check(self.L.ibm_marker_bases(self.h, _ptr(out), ctypes.byref(n)))
         return out
+
+    def kernel_timing(self, reset=True):
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        self._check(self.L.ibm_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n), int(reset)))
+        return ms.value, n.value
 
     def stats(self):
         out = np.zeros(8, dtype=np.int64)
