@@ -159,11 +159,13 @@ ibm_status ibm_backward(ibm_ctx *ctx, void *const *grad_u_out, void *const *grad
  * = NULL to query it.  Synchronises.  Errors: STATE, INVALID_ARG, CUDA. */
 ibm_status ibm_marker_bases(ibm_ctx *ctx, int64_t *base_out, int64_t *n_markers);
 
-/* Diagnostics of the last forcing step (HOST int64[8], synchronises):
+/* Diagnostics of the last forcing step (HOST int64[10], synchronises):
  * [0] markers, [1] particle clusters, [2] clusters on the shared-memory path,
- * [3] markers on the fallback path, [4] largest cluster (cells, upper bound),
- * [5] distinct touched cells on the shared-memory path, [6] kernel launches
- * per step, [7] threads per block used. */
+ * [3] markers on the plain fallback path, [4] largest cluster held in shared
+ * memory (touched cells), [5] distinct touched cells on the shared-memory
+ * path, [6] kernel launches per step, [7] threads per block of the cluster
+ * kernel, [8] clusters run one velocity component at a time, [9] candidate
+ * particle pairs tested.  Entries [1]-[5], [7]-[9] are 0 in PLAIN mode. */
 ibm_status ibm_step_stats(ibm_ctx *ctx, int64_t *stats);
 
 /* Device time of the main forcing kernel (the shared-memory cluster kernel,

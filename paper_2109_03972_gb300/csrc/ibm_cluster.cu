@@ -42,7 +42,6 @@
 namespace {
 
 constexpr int kCapP = 64;        // particles per shared-memory cluster
-constexpr int kCapR = 3072;      // (row, 32-cell word) entries of the box bitmask
 constexpr int kBuckets = 1024;   // work-order buckets
 constexpr int kPairThreads = 128;
 constexpr int kPairCap = 1024;   // near-marker list in the exact pair test
@@ -58,6 +57,7 @@ enum {
     C_MAXCELLS,
     C_TOUCHED,
     C_FBMARK,     // markers on the fallback path
+    C_ONECOMP,    // clusters run one velocity component at a time
     C_COUNT
 };
 
@@ -73,7 +73,7 @@ struct ClusterScratch {
     int *cl_np = nullptr, *cl_nm = nullptr, *cl_first = nullptr, *cl_cur = nullptr, *cl_box = nullptr;
     int *cl_plist = nullptr, *cl_bkt = nullptr;
     int *bkt_cnt = nullptr, *bkt_start = nullptr, *order = nullptr, *fb_list = nullptr;
-    int smem_bytes = 0, cap_c = 0, tpb = 0, kmax = 0;
+    int smem_bytes = 0, cap_c = 0, tpb = 0, kmax = 0, det = -1;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -315,7 +315,7 @@ __global__ void k_cluster_fill(int n_p, const int *pcl, const int *cl_first, int
 // its box is consistently unwrapped, else the plain fallback.
 __global__ void k_cluster_route(const long long *n_clust_d, const PInfo *P, const int32_t *dims, const int *cl_np,
                                 const int *cl_nm, const int *cl_first, const int *cl_plist, const int *cl_box,
-                                int cap_m, int *cl_bkt, int *bkt_cnt, int *fb_list, int *cnt) {
+                                int cap_m, int max_rows, int *cl_bkt, int *bkt_cnt, int *fb_list, int *cnt) {
     const int n = (int)*n_clust_d;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const int np = cl_np[c], nm = cl_nm[c];
@@ -329,7 +329,7 @@ __global__ void k_cluster_route(const long long *n_clust_d, const PInfo *P, cons
             ok = ok && ext <= n_k && 2 * cext < n_k;
             R *= (k == 0) ? (ext + 31) / 32 : ext;
         }
-        ok = ok && R <= kCapR;
+        ok = ok && R <= max_rows;
         if (ok) {
             const int b = min(kBuckets - 1, nm / 8);
             cl_bkt[c] = kBuckets - 1 - b;   // larger clusters first
@@ -400,7 +400,7 @@ struct KParams {
     const int *order, *cl_first, *cl_np, *cl_nm, *cl_box, *cl_plist, *poff;
     int *cnt, *fb_list, *err;
     double *FD, *TD;
-    int n_forcing, cap_c;
+    int n_forcing, smem_bytes;
     float finv;
 };
 
@@ -478,16 +478,229 @@ __device__ __forceinline__ void row_slots(const uint2 *rt, int W, int By, const 
         }
 }
 
-template <int TPB, int KMAX>
+constexpr int kSlots = 2;   // particle segments per 32-marker chunk (N_l >= 32 keeps a chunk within 2)
+
+template <int TPB, int KM>
+constexpr int fixed_smem_bytes() {
+    return (int)(sizeof(PS) * kCapP + sizeof(double) * 6 * kCapP + sizeof(float) * (TPB * KM / 32) * kSlots * 6);
+}
+
+// Block-wide max of a non-negative float (valid in every thread afterwards).
+template <int TPB>
+__device__ __forceinline__ float block_max(float v, float *sh) {
+    v = warp_max(v);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = 0.f;
+#pragma unroll
+    for (int i = 0; i < TPB / 32; ++i) r = fmaxf(r, sh[i]);
+    __syncthreads();
+    return r;
+}
+
+struct Item {
+    int np, nm, W, By, R, C;
+    int x0, y0, z0;
+    int nx, ny, nz;
+    long long ncell;
+    float dmax;
+};
+
+// Gather (load = true) or write back the touched cells of components
+// q0..q0+NC-1.  Slots of one x-row run are consecutive.
+template <int TPB, int NC, bool LOAD>
+__device__ __forceinline__ void move_cells(const Item &it, const uint2 *s_row, float *s_u, const float *ug, float *uo,
+                                           float *fo, float finv, int q0) {
+    for (int i = threadIdx.x; i < it.R; i += TPB) {
+        unsigned mask = s_row[i].x;
+        if (!mask) continue;
+        const int row = i / it.W, wx = i - row * it.W;
+        const int ry = row % it.By, rz = row / it.By;
+        const int gy = wrapi(it.y0 + ry, it.ny), gz = wrapi(it.z0 + rz, it.nz);
+        const long long rowbase = ((long long)gz * it.ny + gy) * it.nx;
+        int slot = (int)s_row[i].y;
+        while (mask) {
+            const int bit = __ffs(mask) - 1;
+            mask &= mask - 1u;
+            const long long g = rowbase + wrapi(it.x0 + 32 * wx + bit, it.nx);
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                const long long gq = (long long)(q0 + q) * it.ncell + g;
+                if (LOAD) {
+                    s_u[q * it.C + slot] = ug[gq];
+                } else {
+                    if (fo) fo[gq] = (s_u[q * it.C + slot] - uo[gq]) * finv;
+                    uo[gq] = s_u[q * it.C + slot];
+                }
+            }
+            ++slot;
+        }
+    }
+}
+
+// The outer forcing loop (Sec. 2.2.2) for components q0..q0+NC-1 of one
+// cluster, on its touched cells in shared memory.  Components are independent
+// in the loop (F = (U^d - W u)/tau and the spreading act per component), so a
+// cluster too large for all three runs them one at a time.
+template <int TPB, int KM, bool DET, int NC>
+__device__ __forceinline__ void forcing_loop(const KParams &prm, const Item &it, const PS *s_ps, double *s_acc,
+                                             float *s_part, const uint2 *s_row, float *s_u, float *s_red, int q0) {
+    constexpr int KK = KM / NC;   // markers per thread in this pass
+    int *s_ui = reinterpret_cast<int *>(s_u);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int C = it.C, nm = it.nm, np = it.np;
+    for (int iter = 0; iter < prm.n_forcing; ++iter) {
+        float ereg[KK][NC];
+        float emax = 0.f;
+#pragma unroll
+        for (int k = 0; k < KK; ++k) {
+            const int m = tid + k * TPB;
+            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            int pl = -1;
+#pragma unroll
+            for (int q = 0; q < NC; ++q) ereg[k][q] = 0.f;
+            if (m < nm) {
+                const MarkerLoc L = locate(s_ps, np, m);
+                const PS &s = s_ps[L.ps];
+                int b[3];
+                float w[3][3];
+                rel_stencil(s, prm.t32, prm.t64, L.l, b, w);
+                int slot[9];
+                row_slots(s_row, it.W, it.By, b, slot);
+                float U[NC];
+#pragma unroll
+                for (int q = 0; q < NC; ++q) U[q] = 0.f;
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const int sl = slot[dz * 3 + dy];
+                        const float wyz = w[2][dz] * w[1][dy];
+                        const float a0 = wyz * w[0][0], a1 = wyz * w[0][1], a2 = wyz * w[0][2];
+#pragma unroll
+                        for (int q = 0; q < NC; ++q)
+                            U[q] += a0 * s_u[q * C + sl] + a1 * s_u[q * C + sl + 1] + a2 * s_u[q * C + sl + 2];
+                    }
+                const float *t = prm.t32 + 3ll * (s.P.toff + L.l);
+                const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
+                const float ud0 = s.P.ud[0] + (s.P.om[1] * r2 - s.P.om[2] * r1);
+                const float ud1 = s.P.ud[1] + (s.P.om[2] * r0 - s.P.om[0] * r2);
+                const float ud2 = s.P.ud[2] + (s.P.om[0] * r1 - s.P.om[1] * r0);
+                const float D = s.P.D;
+                float ed[3];
+                if (NC == 3) {
+                    const float e0 = ud0 - U[0], e1 = ud1 - U[NC > 1 ? 1 : 0], e2 = ud2 - U[NC > 2 ? 2 : 0];
+                    ereg[k][0] = e0;
+                    ereg[k][NC > 1 ? 1 : 0] = e1;
+                    ereg[k][NC > 2 ? 2 : 0] = e2;
+                    if (DET) emax = fmaxf(emax, fmaxf(fabsf(e0), fmaxf(fabsf(e1), fabsf(e2))));
+                    ed[0] = e0 * D; ed[1] = e1 * D; ed[2] = e2 * D;
+                } else {
+                    const float e = (q0 == 0 ? ud0 : (q0 == 1 ? ud1 : ud2)) - U[0];
+                    ereg[k][0] = e;
+                    if (DET) emax = fmaxf(emax, fabsf(e));
+                    ed[0] = q0 == 0 ? e * D : 0.f;
+                    ed[1] = q0 == 1 ? e * D : 0.f;
+                    ed[2] = q0 == 2 ? e * D : 0.f;
+                }
+                v[0] = ed[0]; v[1] = ed[1]; v[2] = ed[2];
+                v[3] = r1 * ed[2] - r2 * ed[1];
+                v[4] = r2 * ed[0] - r0 * ed[2];
+                v[5] = r0 * ed[1] - r1 * ed[0];
+                pl = L.ps;
+            }
+            // per-particle loads: warp-segment sums into this warp's chunk slots
+            const int chunk = (m - lane) >> 5;
+            const int pf = __shfl_sync(0xffffffffu, pl, 0);
+            unsigned act = __ballot_sync(0xffffffffu, pl >= 0);
+            while (act) {
+                const int leader = __ffs(act) - 1;
+                const int lp = __shfl_sync(0xffffffffu, pl, leader);
+                const bool mine = (pl == lp);
+                act &= ~__ballot_sync(0xffffffffu, mine);
+                const int sl = lp - pf;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    if (NC == 1 && (q == q0 || q == 3 + q0)) continue;   // identically zero in this pass
+                    const float x = warp_sum(mine ? v[q] : 0.f);
+                    if (lane == leader) {
+                        if (sl < kSlots) s_part[(chunk * kSlots + sl) * 6 + q] += x;
+                        else atomicAdd(&s_acc[6 * lp + q], (double)x);
+                    }
+                }
+            }
+        }
+        float S = 1.f, invS = 1.f;
+        if (DET) {
+            // fixed-point scale 2^k with (max|u| + 64 Dmax max|e|) 2^k < 2^30: every
+            // cell value and every partial sum of spread contributions fits in int32
+            float umax = 0.f;
+            for (int i = tid; i < NC * C; i += TPB) umax = fmaxf(umax, fabsf(s_u[i]));
+            umax = block_max<TPB>(umax, s_red);
+            emax = block_max<TPB>(emax, s_red);
+            const float range = umax + 64.f * it.dmax * emax;
+            int ex = 100;
+            if (range > 0.f) ex = min(100, max(-100, 29 - (int)ceilf(log2f(range))));
+            S = ldexpf(1.f, ex);
+            invS = ldexpf(1.f, -ex);
+            for (int i = tid; i < NC * C; i += TPB) s_ui[i] = __float2int_rn(s_u[i] * S);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KK; ++k) {
+            const int m = tid + k * TPB;
+            if (m < nm) {
+                const MarkerLoc L = locate(s_ps, np, m);
+                const PS &s = s_ps[L.ps];
+                int b[3];
+                float w[3][3];
+                rel_stencil(s, prm.t32, prm.t64, L.l, b, w);
+                int slot[9];
+                row_slots(s_row, it.W, it.By, b, slot);
+                const float D = s.P.D * S;
+                float g[NC];
+#pragma unroll
+                for (int q = 0; q < NC; ++q) g[q] = ereg[k][q] * D;
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const int sl = slot[dz * 3 + dy];
+                        const float wyz = w[2][dz] * w[1][dy];
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const float a = wyz * w[0][dx];
+#pragma unroll
+                            for (int q = 0; q < NC; ++q) {
+                                if (DET) atomicAdd(&s_ui[q * C + sl + dx], __float2int_rn(a * g[q]));
+                                else atomicAdd(&s_u[q * C + sl + dx], a * g[q]);
+                            }
+                        }
+                    }
+            }
+        }
+        __syncthreads();
+        if (DET) {
+            for (int i = tid; i < NC * C; i += TPB) s_u[i] = (float)s_ui[i] * invS;
+            __syncthreads();
+        }
+    }
+}
+
+// One persistent CTA per SM; clusters come from a work list ordered by size.
+// DET = fixed-point spreading (int32 shared-memory atomics, bit-reproducible).
+template <int TPB, int KM, bool DET>
 __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
+    constexpr int NCH = TPB * KM / 32;   // 32-marker chunks
     extern __shared__ __align__(16) unsigned char smem[];
     PS *s_ps = reinterpret_cast<PS *>(smem);
-    double *s_acc = reinterpret_cast<double *>(s_ps + kCapP);          // [kCapP][6]
-    uint2 *s_row = reinterpret_cast<uint2 *>(s_acc + 6 * kCapP);        // [kCapR]
-    float *s_u = reinterpret_cast<float *>(s_row + kCapR);              // [3][cap_c]
+    double *s_acc = reinterpret_cast<double *>(s_ps + kCapP);             // [kCapP][6] (rare overflow)
+    float *s_part = reinterpret_cast<float *>(s_acc + 6 * kCapP);         // [NCH][kSlots][6]
+    uint2 *s_row = reinterpret_cast<uint2 *>(s_part + NCH * kSlots * 6);  // [R] then the cells
+    unsigned char *dyn_end = smem + prm.smem_bytes;
     __shared__ int s_item, s_flag, s_scan[32], s_total;
-    const int cap_c = prm.cap_c;
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ float s_red[32];
+    const int tid = threadIdx.x;
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(prm.cnt + C_WORK, 1);
@@ -495,16 +708,21 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
         const int item = s_item;
         if (item >= prm.cnt[C_NITEMS]) break;
         const int c = prm.order[item];
-        const int np = prm.cl_np[c], nm = prm.cl_nm[c], first = prm.cl_first[c];
+        Item it;
+        it.np = prm.cl_np[c];
+        it.nm = prm.cl_nm[c];
+        const int first = prm.cl_first[c];
         const int *box = prm.cl_box + 12 * c;
-        const int x0 = box[0], y0 = box[1], z0 = box[2];
-        const int Bx = box[3] - x0 + 1, By = box[4] - y0 + 1, Bz = box[5] - z0 + 1;
-        const int W = (Bx + 31) >> 5, R = By * Bz * W;
-        // particle table (sorted by global index so the marker order is fixed)
-        if (tid < np) {
-            const int p = prm.cl_plist[first + tid];
-            s_ps[tid].gid = p;
-        }
+        it.x0 = box[0]; it.y0 = box[1]; it.z0 = box[2];
+        const int Bx = box[3] - it.x0 + 1, By = box[4] - it.y0 + 1, Bz = box[5] - it.z0 + 1;
+        it.W = (Bx + 31) >> 5;
+        it.By = By;
+        it.R = By * Bz * it.W;
+        const int np = it.np, nm = it.nm;
+        float *s_u = reinterpret_cast<float *>(s_row + ((it.R + 1) & ~1));
+        const int cap_cells = (int)((dyn_end - reinterpret_cast<unsigned char *>(s_u)) / 4);
+        // particle table, sorted by global index so the marker numbering is fixed
+        if (tid < np) s_ps[tid].gid = prm.cl_plist[first + tid];
         if (tid == 0) s_flag = 0;
         __syncthreads();
         if (tid == 0) {
@@ -519,12 +737,13 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
         if (tid < np) {
             const int p = s_ps[tid].gid;
             s_ps[tid].P = prm.P[p];
-            s_ps[tid].off[0] = prm.poff[3 * p] - x0;
-            s_ps[tid].off[1] = prm.poff[3 * p + 1] - y0;
-            s_ps[tid].off[2] = prm.poff[3 * p + 2] - z0;
+            s_ps[tid].off[0] = prm.poff[3 * p] - it.x0;
+            s_ps[tid].off[1] = prm.poff[3 * p + 1] - it.y0;
+            s_ps[tid].off[2] = prm.poff[3 * p + 2] - it.z0;
         }
         for (int i = tid; i < 6 * np; i += TPB) s_acc[i] = 0.0;
-        for (int i = tid; i < R; i += TPB) s_row[i].x = 0u;
+        for (int i = tid; i < ((nm + 31) >> 5) * kSlots * 6; i += TPB) s_part[i] = 0.f;
+        for (int i = tid; i < it.R; i += TPB) s_row[i].x = 0u;
         __syncthreads();
         if (tid == 0) {
             int m = 0;
@@ -532,8 +751,10 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
         }
         __syncthreads();
         const int scene = s_ps[0].P.scene;
-        const int nx = prm.dims[3 * scene], ny = prm.dims[3 * scene + 1], nz = prm.dims[3 * scene + 2];
-        const long long ncell = (long long)nx * ny * nz;
+        it.nx = prm.dims[3 * scene]; it.ny = prm.dims[3 * scene + 1]; it.nz = prm.dims[3 * scene + 2];
+        it.ncell = (long long)it.nx * it.ny * it.nz;
+        it.dmax = 0.f;
+        for (int i = 0; i < np; ++i) it.dmax = fmaxf(it.dmax, s_ps[i].P.D);
 
         // 1. touched-cell bitmask (bounds-checked)
         for (int m = tid; m < nm; m += TPB) {
@@ -549,15 +770,15 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy) {
                     const int row = (b[2] + dz) * By + (b[1] + dy);
-                    atomicOr(&s_row[row * W + wx].x, 7u << bit);
-                    if (bit > 29) atomicOr(&s_row[row * W + wx + 1].x, 7u >> (32 - bit));
+                    atomicOr(&s_row[row * it.W + wx].x, 7u << bit);
+                    if (bit > 29) atomicOr(&s_row[row * it.W + wx + 1].x, 7u >> (32 - bit));
                 }
         }
         __syncthreads();
         // 2. compact slots: exclusive prefix of the popcounts
         {
-            const int per = (R + TPB - 1) / TPB;
-            const int lo = min(R, tid * per), hi = min(R, lo + per);
+            const int per = (it.R + TPB - 1) / TPB;
+            const int lo = min(it.R, tid * per), hi = min(it.R, lo + per);
             int sum = 0;
             for (int i = lo; i < hi; ++i) sum += __popc(s_row[i].x);
             int total;
@@ -569,9 +790,10 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
             if (tid == 0) s_total = total;
         }
         __syncthreads();
-        const int C = s_total;
-        if (s_flag || C > cap_c) {
-            // does not fit: hand the cluster to the plain path
+        it.C = s_total;
+        const bool three = 3 * it.C <= cap_cells && nm <= TPB * (KM / 3);
+        if (s_flag || it.C > cap_cells) {
+            // does not fit even one component at a time: hand the cluster to the plain path
             if (tid == 0) {
                 const int k0 = atomicAdd(prm.cnt + C_NFB, np);
                 atomicAdd(prm.cnt + C_FBMARK, nm);
@@ -582,154 +804,39 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
             continue;
         }
         if (tid == 0) {
-            atomicMax(prm.cnt + C_MAXCELLS, C);
-            atomicAdd(prm.cnt + C_TOUCHED, C);
+            atomicMax(prm.cnt + C_MAXCELLS, it.C);
+            atomicAdd(prm.cnt + C_TOUCHED, it.C);
+            if (!three) atomicAdd(prm.cnt + C_ONECOMP, 1);
         }
-        // 3. gather u at the touched cells
-        const float *__restrict__ ug = prm.uf[scene];
-        for (int i = tid; i < R; i += TPB) {
-            unsigned mask = s_row[i].x;
-            if (!mask) continue;
-            const int row = i / W, wx = i - row * W;
-            const int ry = row % By, rz = row / By;
-            const int gy = wrapi(y0 + ry, ny), gz = wrapi(z0 + rz, nz);
-            const long long rowbase = ((long long)gz * ny + gy) * nx;
-            int slot = (int)s_row[i].y;
-            while (mask) {
-                const int bit = __ffs(mask) - 1;
-                mask &= mask - 1u;
-                const long long g = rowbase + wrapi(x0 + 32 * wx + bit, nx);
-                s_u[slot] = ug[g];
-                s_u[cap_c + slot] = ug[ncell + g];
-                s_u[2 * cap_c + slot] = ug[2 * ncell + g];
-                ++slot;
-            }
-        }
-        __syncthreads();
-
-        // 4. the outer forcing loop on the shared-memory copy
-        for (int it = 0; it < prm.n_forcing; ++it) {
-            float ereg[KMAX][3];
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k) {
-                const int m = tid + k * TPB;
-                float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                int pl = -1;
-                ereg[k][0] = ereg[k][1] = ereg[k][2] = 0.f;
-                if (m < nm) {
-                    const MarkerLoc L = locate(s_ps, np, m);
-                    const PS &s = s_ps[L.ps];
-                    int b[3];
-                    float w[3][3];
-                    rel_stencil(s, prm.t32, prm.t64, L.l, b, w);
-                    int slot[9];
-                    row_slots(s_row, W, By, b, slot);
-                    float U0 = 0.f, U1 = 0.f, U2 = 0.f;
-#pragma unroll
-                    for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-                        for (int dy = 0; dy < 3; ++dy) {
-                            const int sl = slot[dz * 3 + dy];
-                            const float wyz = w[2][dz] * w[1][dy];
-                            const float a0 = wyz * w[0][0], a1 = wyz * w[0][1], a2 = wyz * w[0][2];
-                            U0 += a0 * s_u[sl] + a1 * s_u[sl + 1] + a2 * s_u[sl + 2];
-                            U1 += a0 * s_u[cap_c + sl] + a1 * s_u[cap_c + sl + 1] + a2 * s_u[cap_c + sl + 2];
-                            U2 += a0 * s_u[2 * cap_c + sl] + a1 * s_u[2 * cap_c + sl + 1] +
-                                  a2 * s_u[2 * cap_c + sl + 2];
-                        }
-                    const float *t = prm.t32 + 3ll * (s.P.toff + L.l);
-                    const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
-                    const float ud0 = s.P.ud[0] + (s.P.om[1] * r2 - s.P.om[2] * r1);
-                    const float ud1 = s.P.ud[1] + (s.P.om[2] * r0 - s.P.om[0] * r2);
-                    const float ud2 = s.P.ud[2] + (s.P.om[0] * r1 - s.P.om[1] * r0);
-                    const float e0 = ud0 - U0, e1 = ud1 - U1, e2 = ud2 - U2;
-                    ereg[k][0] = e0; ereg[k][1] = e1; ereg[k][2] = e2;
-                    const float D = s.P.D;
-                    v[0] = e0 * D; v[1] = e1 * D; v[2] = e2 * D;
-                    v[3] = r1 * v[2] - r2 * v[1];
-                    v[4] = r2 * v[0] - r0 * v[2];
-                    v[5] = r0 * v[1] - r1 * v[0];
-                    pl = L.ps;
-                }
-                // per-particle loads: warp-segmented sums, FP64 accumulation
-                unsigned act = __ballot_sync(0xffffffffu, pl >= 0);
-                while (act) {
-                    const int leader = __ffs(act) - 1;
-                    const int lp = __shfl_sync(0xffffffffu, pl, leader);
-                    const bool mine = (pl == lp);
-                    act &= ~__ballot_sync(0xffffffffu, mine);
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        const float x = warp_sum(mine ? v[q] : 0.f);
-                        if (lane == leader) atomicAdd(&s_acc[6 * lp + q], (double)x);
-                    }
-                }
-            }
+        const float *ug = prm.uf[scene];
+        float *uo = prm.uf[scene];
+        float *fo = prm.ff ? prm.ff[scene] : nullptr;
+        if (three) {
+            move_cells<TPB, 3, true>(it, s_row, s_u, ug, uo, fo, prm.finv, 0);
             __syncthreads();
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k) {
-                const int m = tid + k * TPB;
-                if (m < nm) {
-                    const MarkerLoc L = locate(s_ps, np, m);
-                    const PS &s = s_ps[L.ps];
-                    int b[3];
-                    float w[3][3];
-                    rel_stencil(s, prm.t32, prm.t64, L.l, b, w);
-                    int slot[9];
-                    row_slots(s_row, W, By, b, slot);
-                    const float D = s.P.D;
-                    const float g0 = ereg[k][0] * D, g1 = ereg[k][1] * D, g2 = ereg[k][2] * D;
-#pragma unroll
-                    for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-                        for (int dy = 0; dy < 3; ++dy) {
-                            const int sl = slot[dz * 3 + dy];
-                            const float wyz = w[2][dz] * w[1][dy];
-#pragma unroll
-                            for (int dx = 0; dx < 3; ++dx) {
-                                const float a = wyz * w[0][dx];
-                                atomicAdd(&s_u[sl + dx], a * g0);
-                                atomicAdd(&s_u[cap_c + sl + dx], a * g1);
-                                atomicAdd(&s_u[2 * cap_c + sl + dx], a * g2);
-                            }
-                        }
-                }
-            }
-            __syncthreads();
-        }
-
-        // 5. write back the touched cells (and the total force if requested)
-        float *__restrict__ uo = prm.uf[scene];
-        float *__restrict__ fo = prm.ff ? prm.ff[scene] : nullptr;
-        for (int i = tid; i < R; i += TPB) {
-            unsigned mask = s_row[i].x;
-            if (!mask) continue;
-            const int row = i / W, wx = i - row * W;
-            const int ry = row % By, rz = row / By;
-            const int gy = wrapi(y0 + ry, ny), gz = wrapi(z0 + rz, nz);
-            const long long rowbase = ((long long)gz * ny + gy) * nx;
-            int slot = (int)s_row[i].y;
-            while (mask) {
-                const int bit = __ffs(mask) - 1;
-                mask &= mask - 1u;
-                const long long g = rowbase + wrapi(x0 + 32 * wx + bit, nx);
-                if (fo) {
-                    fo[g] = (s_u[slot] - uo[g]) * prm.finv;
-                    fo[ncell + g] = (s_u[cap_c + slot] - uo[ncell + g]) * prm.finv;
-                    fo[2 * ncell + g] = (s_u[2 * cap_c + slot] - uo[2 * ncell + g]) * prm.finv;
-                }
-                uo[g] = s_u[slot];
-                uo[ncell + g] = s_u[cap_c + slot];
-                uo[2 * ncell + g] = s_u[2 * cap_c + slot];
-                ++slot;
-            }
-        }
-        if (tid < np) {
-            const int p = s_ps[tid].gid;
+            forcing_loop<TPB, KM, DET, 3>(prm, it, s_ps, s_acc, s_part, s_row, s_u, s_red, 0);
+            move_cells<TPB, 3, false>(it, s_row, s_u, ug, uo, fo, prm.finv, 0);
+        } else {
             for (int q = 0; q < 3; ++q) {
-                prm.FD[3 * p + q] = s_acc[6 * tid + q];
-                prm.TD[3 * p + q] = s_acc[6 * tid + 3 + q];
+                move_cells<TPB, 1, true>(it, s_row, s_u, ug, uo, fo, prm.finv, q);
+                __syncthreads();
+                forcing_loop<TPB, KM, DET, 1>(prm, it, s_ps, s_acc, s_part, s_row, s_u, s_red, q);
+                move_cells<TPB, 1, false>(it, s_row, s_u, ug, uo, fo, prm.finv, q);
+                __syncthreads();
             }
+        }
+        // particle loads: chunk partials in a fixed order, FP64
+        for (int i = tid; i < 6 * np; i += TPB) {
+            const int pi = i / 6, q = i - 6 * pi;
+            const int ms = s_ps[pi].mstart, me = ms + s_ps[pi].P.nl;
+            double sum = s_acc[i];
+            for (int ch = ms >> 5; ch <= (me - 1) >> 5; ++ch) {
+                const int sl = pi - locate(s_ps, np, ch << 5).ps;
+                if (sl < kSlots) sum += (double)s_part[(ch * kSlots + sl) * 6 + q];
+            }
+            const int p = s_ps[pi].gid;
+            if (q < 3) prm.FD[3 * p + q] = sum;
+            else prm.TD[3 * p + q - 3] = sum;
         }
         __syncthreads();
     }
@@ -740,13 +847,12 @@ int grid_for(long long n, int block) {
     return (int)std::max(1ll, std::min(g, 65535ll * 8));
 }
 
-template <int TPB, int KMAX>
 static int max_dyn_smem() {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int statics = 32 * 4 + 16;   // s_item, s_flag, s_scan, s_total
-    return optin - statics - 1024;
+    const int statics = 64 * 4 + 64;   // s_item, s_flag, s_scan, s_total, s_red
+    return optin - statics - 256;
 }
 
 }  // namespace
@@ -835,20 +941,19 @@ static ibm_status cluster_alloc(ibm_ctx *ctx) {
     return IBM_OK;
 }
 
-template <int TPB, int KMAX>
+template <int TPB, int KM, bool DET>
 static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams &prm) {
-    auto kern = k_cluster_forcing<TPB, KMAX>;
-    if (S->smem_bytes == 0 || S->tpb != TPB) {
-        const int smem = max_dyn_smem<TPB, KMAX>();
-        const int fixed = (int)(sizeof(PS) * kCapP + sizeof(double) * 6 * kCapP + sizeof(uint2) * kCapR);
-        S->cap_c = ((smem - fixed) / 12) & ~31;
-        S->smem_bytes = fixed + 12 * S->cap_c;
+    auto kern = k_cluster_forcing<TPB, KM, DET>;
+    if (S->smem_bytes == 0 || S->tpb != TPB || S->det != (int)DET) {
+        S->smem_bytes = max_dyn_smem() & ~15;
+        S->cap_c = (S->smem_bytes - fixed_smem_bytes<TPB, KM>()) / 4;   // FP32 cell slots (all components)
         S->tpb = TPB;
-        S->kmax = KMAX;
+        S->kmax = KM;
+        S->det = (int)DET;
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S->smem_bytes),
            "set shared memory size");
     }
-    prm.cap_c = S->cap_c;
+    prm.smem_bytes = S->smem_bytes;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -858,6 +963,9 @@ static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams
     return ibm_cuda_check(ctx, cudaGetLastError(), "cluster kernel");
 }
 
+// markers per thread of the cluster kernel for a block size
+static int markers_per_thread(int tpb) { return tpb == 1024 ? 12 : (tpb == 512 ? 24 : 48); }
+
 ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
     ibm_status st = ensure_field_ptrs(ctx, u_ptrs, f_out);
     if (st != IBM_OK) return st;
@@ -866,9 +974,10 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     ClusterScratch *S = reinterpret_cast<ClusterScratch *>(ctx->cl);
     const int n = ctx->n_p;
     cudaStream_t sm = ctx->stream;
-    const int tpb = ctx->cfg.threads_per_block ? ctx->cfg.threads_per_block : 512;
-    const int kmax = tpb == 1024 ? 4 : (tpb == 512 ? 8 : 16);
-    const int cap_m = tpb * kmax;
+    const int tpb = ctx->cfg.threads_per_block ? ctx->cfg.threads_per_block : 1024;
+    const int cap_m = tpb * markers_per_thread(tpb);
+    // row table may take at most half of the dynamic shared memory
+    const int max_rows = (max_dyn_smem() - fixed_smem_bytes<1024, 12>()) / 16;
 
     CK(cudaMemsetAsync(S->cnt, 0, C_COUNT * sizeof(int), sm), "zero counters");
     CK(cudaMemsetAsync(S->bin_cnt, 0, (S->nbins + 1) * sizeof(int), sm), "zero bins");
@@ -893,7 +1002,8 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     k_scan1<<<1, 1024, 0, sm>>>(S->cl_np, S->cl_first, n, S->tot + 2);
     k_cluster_fill<<<gb, 256, 0, sm>>>(n, S->pcl, S->cl_first, S->cl_cur, S->cl_plist);
     k_cluster_route<<<gb, 256, 0, sm>>>(S->tot + 1, ctx->pinfo, ctx->dims_d, S->cl_np, S->cl_nm, S->cl_first,
-                                        S->cl_plist, S->cl_box, cap_m, S->cl_bkt, S->bkt_cnt, S->fb_list, S->cnt);
+                                        S->cl_plist, S->cl_box, cap_m, max_rows, S->cl_bkt, S->bkt_cnt,
+                                        S->fb_list, S->cnt);
     k_scan1<<<1, 1024, 0, sm>>>(S->bkt_cnt, S->bkt_start, kBuckets, S->tot + 3);
     k_order_fill<<<gb, 256, 0, sm>>>(S->tot + 1, S->cl_bkt, S->bkt_start, S->bkt_start + kBuckets + 1, S->order);
     ctx->launches += 13;
@@ -920,9 +1030,13 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prm.n_forcing = ctx->cfg.n_forcing;
     prm.finv = (float)(1.0 / tau);
     prof_begin(ctx);
-    if (tpb == 1024) st = launch_cluster_kernel<1024, 4>(ctx, S, prm);
-    else if (tpb == 512) st = launch_cluster_kernel<512, 8>(ctx, S, prm);
-    else st = launch_cluster_kernel<256, 16>(ctx, S, prm);
+    const bool det = ctx->cfg.spread_mode == IBM_SPREAD_DETERMINISTIC;
+    if (tpb == 1024)
+        st = det ? launch_cluster_kernel<1024, 12, true>(ctx, S, prm) : launch_cluster_kernel<1024, 12, false>(ctx, S, prm);
+    else if (tpb == 512)
+        st = det ? launch_cluster_kernel<512, 24, true>(ctx, S, prm) : launch_cluster_kernel<512, 24, false>(ctx, S, prm);
+    else
+        st = det ? launch_cluster_kernel<256, 48, true>(ctx, S, prm) : launch_cluster_kernel<256, 48, false>(ctx, S, prm);
     prof_end(ctx);
     if (st != IBM_OK) return st;
     ctx->launches += 1;
@@ -946,5 +1060,7 @@ ibm_status cluster_stats(ibm_ctx *ctx, int64_t *stats) {
     stats[4] = c[C_MAXCELLS];
     stats[5] = c[C_TOUCHED];
     stats[7] = S->tpb;
+    stats[8] = c[C_ONECOMP];
+    stats[9] = c[C_NCAND];
     return IBM_OK;
 }

@@ -206,10 +206,10 @@ class Context:
         return ms.value, n.value
 
     def stats(self):
-        out = np.zeros(8, dtype=np.int64)
+        out = np.zeros(10, dtype=np.int64)
         self._check(self.L.ibm_step_stats(self.h, _ptr(out)))
         keys = ("markers", "clusters", "clusters_smem", "markers_fallback", "largest_cluster_cells",
-                "touched_cells", "launches", "threads_per_block")
+                "touched_cells", "launches", "threads_per_block", "clusters_one_component", "candidate_pairs")
         return dict(zip(keys, (int(v) for v in out)))
 
 

@@ -271,3 +271,49 @@ def test_autograd_function_fd():
                 fd = (0.5 * (w * (up_f - um_f) * (up_f + um_f)).sum()).item() / (2 * eps)
             tol = 1e-5 if t is xp else 1e-6
             assert abs(fd - grad[p, c].item()) <= tol * max(1.0, grad.abs().max().item())
+
+
+def _big_chain_scene():
+    # Four D=24 spheres at the minimum gap: one cluster of ~29K touched cells and
+    # 7240 markers, too large to hold all three velocity components in shared
+    # memory, so the kernel runs the components one at a time.
+    dims = (128, 120, 112)
+    d = np.array([24.0, 24.0, 24.0, 24.0])
+    pts = [np.array([30.3, 60.7, 55.2])]
+    for v in ([1.0, 0.0, 0.0], [0.6, 0.8, 0.0], [0.0, 0.6, 0.8]):
+        pts.append(pts[-1] + np.array(v) * 25.0)
+    u_p, om, rho = synth.particle_state(4, 21)
+    return synth.Scene(dims, np.array(pts), d, u_p, om, rho, field_seed=23)
+
+
+@pytest.mark.parametrize("mode", [ibm.IBM_SPREAD_CLUSTER, ibm.IBM_SPREAD_DETERMINISTIC])
+def test_large_cluster_one_component_path(oracle_mod, mode):
+    sc = _big_chain_scene()
+    u0 = f32_round(sc.field())
+    ref = _oracle_run(oracle_mod, sc, u0)
+    got = run_gpu(sc, u0, ibm.IBM_FP32, mode)
+    st = got["ctx"].stats()
+    assert st["clusters"] == 1 and st["clusters_one_component"] == 1 and st["markers_fallback"] == 0
+    assert rel_err_u(got["u"], ref["u"], u0) <= U_TOL32
+    assert load_err(got["F"], ref["F"], ref["Fabs"]) <= LOAD_TOL32
+    assert load_err(got["T"], ref["T"], 0.5 * sc.d_p * ref["Fabs"]) <= LOAD_TOL32
+
+
+@pytest.mark.parametrize("name", ["small", "single64", "chain"])
+def test_touched_cells_match_oracle(oracle_mod, name):
+    sc = SCENES[name]()
+    got = run_gpu(sc, f32_round(sc.field()), ibm.IBM_FP32, ibm.IBM_SPREAD_DETERMINISTIC, want_slip=False)
+    st = got["ctx"].stats()
+    assert st["markers_fallback"] == 0
+    assert st["touched_cells"] == oracle_mod.touched_count(sc.dims, sc.x_p, sc.d_p)
+
+
+@pytest.mark.parametrize("name", ["small", "chain"])
+def test_deterministic_mode_is_bit_reproducible(name):
+    sc = SCENES[name]()
+    u0 = f32_round(sc.field())
+    a = run_gpu(sc, u0, ibm.IBM_FP32, ibm.IBM_SPREAD_DETERMINISTIC)
+    for _ in range(2):
+        b = run_gpu(sc, u0, ibm.IBM_FP32, ibm.IBM_SPREAD_DETERMINISTIC)
+        assert np.array_equal(a["u"], b["u"])
+        assert np.array_equal(a["F"], b["F"]) and np.array_equal(a["T"], b["T"])
