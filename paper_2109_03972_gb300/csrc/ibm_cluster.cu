@@ -73,6 +73,7 @@ struct ClusterScratch {
     int *cl_np = nullptr, *cl_nm = nullptr, *cl_first = nullptr, *cl_cur = nullptr, *cl_box = nullptr;
     int *cl_plist = nullptr, *cl_bkt = nullptr;
     int *bkt_cnt = nullptr, *bkt_start = nullptr, *order = nullptr, *fb_list = nullptr;
+    int *nm_ord = nullptr, *cum = nullptr;
     int smem_bytes = 0, cap_c = 0, tpb = 0, kmax = 0, det = -1;
 };
 
@@ -107,9 +108,12 @@ __device__ bool uf_unite(int *parent, int a, int b) {
 __device__ __forceinline__ int scene_bin(const int *scene_nb, const int *scene_bin_off, const int32_t *dims,
                                          int s, const double xi[3], int bc[3]) {
     for (int c = 0; c < 3; ++c) {
+        // FP32: bins are wider than the candidate distance by a margin (1h) that
+        // covers the rounding of the bin assignment
         const int n = dims[3 * s + c], nb = scene_nb[3 * s + c];
-        double w = xi[c] - floor(xi[c] / n) * n;          // wrapped into [0, n)
-        int b = (int)(w * nb / n);
+        const float f = (float)xi[c] * __frcp_rn((float)n);
+        const float w = f - floorf(f);                   // wrapped into [0, 1)
+        int b = (int)(w * nb);
         b = min(max(b, 0), nb - 1);
         bc[c] = b;
     }
@@ -142,14 +146,16 @@ __device__ __forceinline__ void min_image_shift(const double xp[3], const double
                                                 int s, int sh[3]) {
     for (int c = 0; c < 3; ++c) {
         const int n = dims[3 * s + c];
-        sh[c] = -(int)llrint((xq[c] - xp[c]) / n) * n;
+        // FP32 is enough: only the nearest whole number of periods matters, and a
+        // half-period tie gives the same distance either way
+        sh[c] = -__float2int_rn((float)(xq[c] - xp[c]) * __frcp_rn((float)n)) * n;
     }
 }
 
 __global__ void k_candidates(int n_p, const PInfo *P, const int *scene_nb, const int *scene_bin_off,
                              const int32_t *dims, const int *bin_start, const int *bin_items, int *cand,
                              int cap_cand, int *cnt) {
-    const double lim = 3.0 * 1.7320508075688772 + 1e-6;
+    const float lim = 3.0f * 1.7320508f + 1e-3f;   // margin covers the FP32 rounding of the distance
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_p; p += gridDim.x * blockDim.x) {
         const PInfo Pp = P[p];
         const int s = Pp.scene;
@@ -171,12 +177,12 @@ __global__ void k_candidates(int n_p, const PInfo *P, const int *scene_nb, const
                         const PInfo &Pq = P[q];
                         int sh[3];
                         min_image_shift(Pp.xi, Pq.xi, dims, s, sh);
-                        double d2 = 0.0;
+                        float d2 = 0.f;
                         for (int c = 0; c < 3; ++c) {
-                            const double dv = Pq.xi[c] + sh[c] - Pp.xi[c];
+                            const float dv = (float)(Pq.xi[c] - Pp.xi[c]) + (float)sh[c];
                             d2 += dv * dv;
                         }
-                        const double r = Pp.a + Pq.a + lim;
+                        const float r = Pp.af + Pq.af + lim;
                         if (d2 < r * r) {
                             const int k = atomicAdd(cnt + C_NCAND, 1);
                             if (k < cap_cand) {
@@ -291,7 +297,7 @@ __global__ void k_cluster_stats(int n_p, const PInfo *P, const int32_t *dims, in
         int sh[3];
         min_image_shift(P[r < 0 ? p : r].xi, Pp.xi, dims, Pp.scene, sh);
         atomicAdd(cl_np + c, 1);
-        atomicAdd(cl_nm + c, Pp.nl);
+        atomicAdd(cl_nm + c, (Pp.nl + 31) & ~31);   // padded to whole 32-marker chunks
         for (int k = 0; k < 3; ++k) {
             poff[3 * p + k] = sh[k];
             const int lo = (int)floor(Pp.xi[k] - Pp.a) - 1 + sh[k];
@@ -354,6 +360,13 @@ __global__ void k_order_fill(const long long *n_clust_d, const int *cl_bkt, cons
     }
 }
 
+// Padded marker counts in work order (zero past the end of the list).
+__global__ void k_gather_nm(int n_max, const int *cnt, const int *order, const int *cl_nm, int *out) {
+    const int n = cnt[C_NITEMS];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_max; i += gridDim.x * blockDim.x)
+        out[i] = i < n ? cl_nm[order[i]] : 0;
+}
+
 // Single-block exclusive scan (same as the set-up scan), local copy.
 __global__ void k_scan1(const int *in, int *out, int n, long long *total) {
     __shared__ long long part[1024];
@@ -382,12 +395,36 @@ __global__ void k_scan1(const int *in, int *out, int n, long long *total) {
 }
 
 // --------------------------------------------------- shared-memory kernel
+//
+// Work items.  Clusters on the shared-memory path are ordered by size
+// (largest first) and their marker counts, each particle's padded to a whole
+// number of 32-marker chunks, are prefix-summed.  The prefix is cut into
+// windows of kWindow markers; a CTA takes one window at a time and packs the
+// clusters that start in it into batches that fit its shared memory (up to
+// kCapCl clusters, kCapP particles, a row-table budget and the marker
+// capacity), so that small clusters (a single D = 12h sphere has 452 markers)
+// share a CTA instead of leaving most of its threads idle.
 
-struct PS {
+constexpr int kCapCl = 32;      // clusters per batch
+constexpr int kWindow = 2048;   // markers per packing window
+
+struct PS {          // particle record in shared memory
     PInfo P;
-    int off[3];     // add to an absolute base cell to get its box-relative cell
-    int mstart;     // first cluster-local marker
-    int gid;        // global particle index
+    int off[3];      // absolute base cell + off = cell relative to its cluster's box
+    int mstart;      // first marker of the particle in the batch (multiple of 32)
+    int gid;         // global particle index
+    int cl;          // cluster within the batch
+};
+
+struct CS {          // cluster record in shared memory
+    int x0, y0, z0, Bx, By, Bz, W, R;
+    int row0;        // first row-table entry
+    int slot0;       // first cell slot
+    int pstart;      // first particle of the cluster in the batch (before sorting)
+    int first, np;   // particles in cl_plist
+    int scene;
+    float dmax, S, invS;
+    unsigned umax, emax;   // float bits (non-negative), atomicMax
 };
 
 struct KParams {
@@ -397,10 +434,10 @@ struct KParams {
     const int32_t *dims;
     float *const *uf;
     float *const *ff;
-    const int *order, *cl_first, *cl_np, *cl_nm, *cl_box, *cl_plist, *poff;
+    const int *order, *cum, *cl_first, *cl_np, *cl_nm, *cl_box, *cl_plist, *poff;
     int *cnt, *fb_list, *err;
     double *FD, *TD;
-    int n_forcing, smem_bytes;
+    int n_forcing, smem_bytes, max_rows;
     float finv;
 };
 
@@ -433,22 +470,36 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
     return pre;
 }
 
-struct MarkerLoc {
-    int ps;        // cluster-local particle
-    int l;         // marker within particle
-};
-
-__device__ __forceinline__ MarkerLoc locate(const PS *ps, int np, int m) {
+// Particle of batch marker m (markers of particle i occupy [mstart_i, mstart_i + nl_i)).
+__device__ __forceinline__ int locate(const PS *ps, int np, int m) {
     int lo = 0, hi = np - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (ps[mid].mstart <= m) lo = mid;
         else hi = mid - 1;
     }
-    MarkerLoc r;
-    r.ps = lo;
-    r.l = m - ps[lo].mstart;
-    return r;
+    return lo;
+}
+
+// Largest j with key[j] <= v among n entries (key[0] <= v).
+__device__ __forceinline__ int upper_index(const CS *cs, int n, int v, bool by_slot) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((by_slot ? cs[mid].slot0 : cs[mid].row0) <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int lower_bound_int(const int *a, int n, int v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // Box-relative base cell and weights of a marker (FP32 path).
@@ -478,367 +529,430 @@ __device__ __forceinline__ void row_slots(const uint2 *rt, int W, int By, const 
         }
 }
 
-constexpr int kSlots = 2;   // particle segments per 32-marker chunk (N_l >= 32 keeps a chunk within 2)
+__device__ __forceinline__ void cp_async4(void *smem_ptr, const void *gmem_ptr) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_ptr);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_ptr) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <int TPB, int KM>
 constexpr int fixed_smem_bytes() {
-    return (int)(sizeof(PS) * kCapP + sizeof(double) * 6 * kCapP + sizeof(float) * (TPB * KM / 32) * kSlots * 6);
+    return (int)(sizeof(PS) * kCapP + sizeof(CS) * kCapCl + sizeof(double) * 6 * kCapP +
+                 sizeof(float) * (TPB * KM / 32) * 6);
 }
 
-// Block-wide max of a non-negative float (valid in every thread afterwards).
-template <int TPB>
-__device__ __forceinline__ float block_max(float v, float *sh) {
-    v = warp_max(v);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float r = 0.f;
-#pragma unroll
-    for (int i = 0; i < TPB / 32; ++i) r = fmaxf(r, sh[i]);
-    __syncthreads();
-    return r;
-}
-
-struct Item {
-    int np, nm, W, By, R, C;
-    int x0, y0, z0;
-    int nx, ny, nz;
-    long long ncell;
-    float dmax;
+struct Batch {
+    int nb, np, nm, R, C;
 };
 
-// Gather (load = true) or write back the touched cells of components
-// q0..q0+NC-1.  Slots of one x-row run are consecutive.
+// Gather (LOAD) or write back the touched cells of components q0..q0+NC-1 of
+// every cluster of the batch.  Slots of one x-row run are consecutive.
 template <int TPB, int NC, bool LOAD>
-__device__ __forceinline__ void move_cells(const Item &it, const uint2 *s_row, float *s_u, const float *ug, float *uo,
-                                           float *fo, float finv, int q0) {
-    for (int i = threadIdx.x; i < it.R; i += TPB) {
+__device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, const CS *s_cs, const uint2 *s_row,
+                                           float *s_u, int q0) {
+    for (int i = threadIdx.x; i < bt.R; i += TPB) {
         unsigned mask = s_row[i].x;
         if (!mask) continue;
-        const int row = i / it.W, wx = i - row * it.W;
-        const int ry = row % it.By, rz = row / it.By;
-        const int gy = wrapi(it.y0 + ry, it.ny), gz = wrapi(it.z0 + rz, it.nz);
-        const long long rowbase = ((long long)gz * it.ny + gy) * it.nx;
+        const CS &cs = s_cs[upper_index(s_cs, bt.nb, i, false)];
+        const int sc = cs.scene;
+        const int nx = prm.dims[3 * sc], ny = prm.dims[3 * sc + 1], nz = prm.dims[3 * sc + 2];
+        const long long ncell = (long long)nx * ny * nz;
+        const int li = i - cs.row0;
+        const int row = li / cs.W, wx = li - row * cs.W;
+        const int ry = row % cs.By, rz = row / cs.By;
+        const int gy = wrapi(cs.y0 + ry, ny), gz = wrapi(cs.z0 + rz, nz);
+        const long long rowbase = ((long long)gz * ny + gy) * nx;
+        float *u = prm.uf[sc];
+        float *f = prm.ff ? prm.ff[sc] : nullptr;
         int slot = (int)s_row[i].y;
         while (mask) {
             const int bit = __ffs(mask) - 1;
             mask &= mask - 1u;
-            const long long g = rowbase + wrapi(it.x0 + 32 * wx + bit, it.nx);
+            const long long g = rowbase + wrapi(cs.x0 + 32 * wx + bit, nx);
 #pragma unroll
             for (int q = 0; q < NC; ++q) {
-                const long long gq = (long long)(q0 + q) * it.ncell + g;
+                const long long gq = (long long)(q0 + q) * ncell + g;
                 if (LOAD) {
-                    s_u[q * it.C + slot] = ug[gq];
+                    cp_async4(s_u + q * bt.C + slot, u + gq);
                 } else {
-                    if (fo) fo[gq] = (s_u[q * it.C + slot] - uo[gq]) * finv;
-                    uo[gq] = s_u[q * it.C + slot];
+                    if (f) f[gq] = (s_u[q * bt.C + slot] - u[gq]) * prm.finv;
+                    u[gq] = s_u[q * bt.C + slot];
                 }
             }
             ++slot;
         }
     }
+    if (LOAD) cp_async_wait_all();
 }
 
-// The outer forcing loop (Sec. 2.2.2) for components q0..q0+NC-1 of one
-// cluster, on its touched cells in shared memory.  Components are independent
-// in the loop (F = (U^d - W u)/tau and the spreading act per component), so a
-// cluster too large for all three runs them one at a time.
+// The outer forcing loop (Sec. 2.2.2) for components q0..q0+NC-1 of a batch,
+// on its touched cells in shared memory.  Components are independent in the
+// loop (F = (U^d - W u)/tau and the spreading act per component), so a batch
+// too large for all three runs them one at a time.  Each warp handles 32
+// markers of one particle (particles are padded to whole chunks), so the
+// per-particle load sums are plain warp sums.
 template <int TPB, int KM, bool DET, int NC>
-__device__ __forceinline__ void forcing_loop(const KParams &prm, const Item &it, const PS *s_ps, double *s_acc,
-                                             float *s_part, const uint2 *s_row, float *s_u, float *s_red, int q0) {
-    constexpr int KK = KM / NC;   // markers per thread in this pass
+__device__ __forceinline__ void forcing_loop(const KParams &prm, const Batch &bt, const PS *s_ps, CS *s_cs,
+                                             float *s_part, const uint2 *s_row, float *s_u, int q0) {
+    constexpr int KK = KM / NC;   // marker slots per thread in this pass
     int *s_ui = reinterpret_cast<int *>(s_u);
     const int tid = threadIdx.x, lane = tid & 31;
-    const int C = it.C, nm = it.nm, np = it.np;
+    const int C = bt.C, nm = bt.nm, np = bt.np;
     for (int iter = 0; iter < prm.n_forcing; ++iter) {
         float ereg[KK][NC];
-        float emax = 0.f;
+        if (DET)
+            for (int j = tid; j < bt.nb; j += TPB) { s_cs[j].umax = 0u; s_cs[j].emax = 0u; }
+        if (DET) __syncthreads();
 #pragma unroll
         for (int k = 0; k < KK; ++k) {
             const int m = tid + k * TPB;
             float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            int pl = -1;
+            float emax = 0.f;
+            int pi = -1;
 #pragma unroll
             for (int q = 0; q < NC; ++q) ereg[k][q] = 0.f;
             if (m < nm) {
-                const MarkerLoc L = locate(s_ps, np, m);
-                const PS &s = s_ps[L.ps];
-                int b[3];
-                float w[3][3];
-                rel_stencil(s, prm.t32, prm.t64, L.l, b, w);
-                int slot[9];
-                row_slots(s_row, it.W, it.By, b, slot);
-                float U[NC];
+                pi = locate(s_ps, np, m);
+                const PS &s = s_ps[pi];
+                const int l = m - s.mstart;
+                if (l < s.P.nl) {
+                    const CS &cs = s_cs[s.cl];
+                    int b[3];
+                    float w[3][3];
+                    rel_stencil(s, prm.t32, prm.t64, l, b, w);
+                    int slot[9];
+                    row_slots(s_row + cs.row0, cs.W, cs.By, b, slot);
+                    float U[NC];
 #pragma unroll
-                for (int q = 0; q < NC; ++q) U[q] = 0.f;
+                    for (int q = 0; q < NC; ++q) U[q] = 0.f;
 #pragma unroll
-                for (int dz = 0; dz < 3; ++dz)
+                    for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-                    for (int dy = 0; dy < 3; ++dy) {
-                        const int sl = slot[dz * 3 + dy];
-                        const float wyz = w[2][dz] * w[1][dy];
-                        const float a0 = wyz * w[0][0], a1 = wyz * w[0][1], a2 = wyz * w[0][2];
+                        for (int dy = 0; dy < 3; ++dy) {
+                            const int sl = slot[dz * 3 + dy];
+                            const float wyz = w[2][dz] * w[1][dy];
+                            const float a0 = wyz * w[0][0], a1 = wyz * w[0][1], a2 = wyz * w[0][2];
 #pragma unroll
-                        for (int q = 0; q < NC; ++q)
-                            U[q] += a0 * s_u[q * C + sl] + a1 * s_u[q * C + sl + 1] + a2 * s_u[q * C + sl + 2];
+                            for (int q = 0; q < NC; ++q)
+                                U[q] += a0 * s_u[q * C + sl] + a1 * s_u[q * C + sl + 1] + a2 * s_u[q * C + sl + 2];
+                        }
+                    const float *t = prm.t32 + 3ll * (s.P.toff + l);
+                    const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
+                    const float ud0 = s.P.ud[0] + (s.P.om[1] * r2 - s.P.om[2] * r1);
+                    const float ud1 = s.P.ud[1] + (s.P.om[2] * r0 - s.P.om[0] * r2);
+                    const float ud2 = s.P.ud[2] + (s.P.om[0] * r1 - s.P.om[1] * r0);
+                    const float D = s.P.D;
+                    float ed[3];
+                    if (NC == 3) {
+                        const float e0 = ud0 - U[0], e1 = ud1 - U[NC > 1 ? 1 : 0], e2 = ud2 - U[NC > 2 ? 2 : 0];
+                        ereg[k][0] = e0;
+                        ereg[k][NC > 1 ? 1 : 0] = e1;
+                        ereg[k][NC > 2 ? 2 : 0] = e2;
+                        emax = fmaxf(fabsf(e0), fmaxf(fabsf(e1), fabsf(e2)));
+                        ed[0] = e0 * D; ed[1] = e1 * D; ed[2] = e2 * D;
+                    } else {
+                        const float e = (q0 == 0 ? ud0 : (q0 == 1 ? ud1 : ud2)) - U[0];
+                        ereg[k][0] = e;
+                        emax = fabsf(e);
+                        ed[0] = q0 == 0 ? e * D : 0.f;
+                        ed[1] = q0 == 1 ? e * D : 0.f;
+                        ed[2] = q0 == 2 ? e * D : 0.f;
                     }
-                const float *t = prm.t32 + 3ll * (s.P.toff + L.l);
-                const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
-                const float ud0 = s.P.ud[0] + (s.P.om[1] * r2 - s.P.om[2] * r1);
-                const float ud1 = s.P.ud[1] + (s.P.om[2] * r0 - s.P.om[0] * r2);
-                const float ud2 = s.P.ud[2] + (s.P.om[0] * r1 - s.P.om[1] * r0);
-                const float D = s.P.D;
-                float ed[3];
-                if (NC == 3) {
-                    const float e0 = ud0 - U[0], e1 = ud1 - U[NC > 1 ? 1 : 0], e2 = ud2 - U[NC > 2 ? 2 : 0];
-                    ereg[k][0] = e0;
-                    ereg[k][NC > 1 ? 1 : 0] = e1;
-                    ereg[k][NC > 2 ? 2 : 0] = e2;
-                    if (DET) emax = fmaxf(emax, fmaxf(fabsf(e0), fmaxf(fabsf(e1), fabsf(e2))));
-                    ed[0] = e0 * D; ed[1] = e1 * D; ed[2] = e2 * D;
-                } else {
-                    const float e = (q0 == 0 ? ud0 : (q0 == 1 ? ud1 : ud2)) - U[0];
-                    ereg[k][0] = e;
-                    if (DET) emax = fmaxf(emax, fabsf(e));
-                    ed[0] = q0 == 0 ? e * D : 0.f;
-                    ed[1] = q0 == 1 ? e * D : 0.f;
-                    ed[2] = q0 == 2 ? e * D : 0.f;
+                    v[0] = ed[0]; v[1] = ed[1]; v[2] = ed[2];
+                    v[3] = r1 * ed[2] - r2 * ed[1];
+                    v[4] = r2 * ed[0] - r0 * ed[2];
+                    v[5] = r0 * ed[1] - r1 * ed[0];
                 }
-                v[0] = ed[0]; v[1] = ed[1]; v[2] = ed[2];
-                v[3] = r1 * ed[2] - r2 * ed[1];
-                v[4] = r2 * ed[0] - r0 * ed[2];
-                v[5] = r0 * ed[1] - r1 * ed[0];
-                pl = L.ps;
             }
-            // per-particle loads: warp-segment sums into this warp's chunk slots
+            // the 32 lanes of a warp hold markers of one particle: warp sums into
+            // the chunk table (FP32 over 32 terms; FP64 across chunks at the end)
             const int chunk = (m - lane) >> 5;
-            const int pf = __shfl_sync(0xffffffffu, pl, 0);
-            unsigned act = __ballot_sync(0xffffffffu, pl >= 0);
-            while (act) {
-                const int leader = __ffs(act) - 1;
-                const int lp = __shfl_sync(0xffffffffu, pl, leader);
-                const bool mine = (pl == lp);
-                act &= ~__ballot_sync(0xffffffffu, mine);
-                const int sl = lp - pf;
+            const bool any = __any_sync(0xffffffffu, pi >= 0 && m < nm);
+            if (any) {
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
-                    if (NC == 1 && (q == q0 || q == 3 + q0)) continue;   // identically zero in this pass
-                    const float x = warp_sum(mine ? v[q] : 0.f);
-                    if (lane == leader) {
-                        if (sl < kSlots) s_part[(chunk * kSlots + sl) * 6 + q] += x;
-                        else atomicAdd(&s_acc[6 * lp + q], (double)x);
-                    }
+                    if (NC == 1 && ((q < 3 && q != q0) || q == 3 + q0)) continue;   // zero in this pass
+                    const float x = warp_sum(v[q]);
+                    if (lane == 0) s_part[chunk * 6 + q] += x;
+                }
+                if (DET) {
+                    const float wm = warp_max(emax);
+                    if (lane == 0) atomicMax(&s_cs[s_ps[pi].cl].emax, __float_as_uint(wm));
                 }
             }
         }
-        float S = 1.f, invS = 1.f;
         if (DET) {
-            // fixed-point scale 2^k with (max|u| + 64 Dmax max|e|) 2^k < 2^30: every
-            // cell value and every partial sum of spread contributions fits in int32
-            float umax = 0.f;
-            for (int i = tid; i < NC * C; i += TPB) umax = fmaxf(umax, fabsf(s_u[i]));
-            umax = block_max<TPB>(umax, s_red);
-            emax = block_max<TPB>(emax, s_red);
-            const float range = umax + 64.f * it.dmax * emax;
-            int ex = 100;
-            if (range > 0.f) ex = min(100, max(-100, 29 - (int)ceilf(log2f(range))));
-            S = ldexpf(1.f, ex);
-            invS = ldexpf(1.f, -ex);
-            for (int i = tid; i < NC * C; i += TPB) s_ui[i] = __float2int_rn(s_u[i] * S);
+            // per cluster: fixed-point scale 2^k with (max|u| + 64 Dmax max|e|) 2^k < 2^30,
+            // so every cell value and every partial sum of spread contributions fits in int32
+            for (int j = 0; j < bt.nb; ++j) {
+                const int s0 = s_cs[j].slot0, s1 = (j + 1 < bt.nb) ? s_cs[j + 1].slot0 : C;
+                float um = 0.f;
+                for (int q = 0; q < NC; ++q)
+                    for (int i = s0 + tid; i < s1; i += TPB) um = fmaxf(um, fabsf(s_u[q * C + i]));
+                um = warp_max(um);
+                if (lane == 0 && um > 0.f) atomicMax(&s_cs[j].umax, __float_as_uint(um));
+            }
+            __syncthreads();
+            for (int j = tid; j < bt.nb; j += TPB) {
+                const float range = __uint_as_float(s_cs[j].umax) + 64.f * s_cs[j].dmax * __uint_as_float(s_cs[j].emax);
+                int ex = 100;
+                if (range > 0.f) ex = min(100, max(-100, 29 - (int)ceilf(log2f(range))));
+                s_cs[j].S = ldexpf(1.f, ex);
+                s_cs[j].invS = ldexpf(1.f, -ex);
+            }
+            __syncthreads();
+            for (int j = 0; j < bt.nb; ++j) {
+                const int s0 = s_cs[j].slot0, s1 = (j + 1 < bt.nb) ? s_cs[j + 1].slot0 : C;
+                const float S = s_cs[j].S;
+                for (int q = 0; q < NC; ++q)
+                    for (int i = s0 + tid; i < s1; i += TPB) s_ui[q * C + i] = __float2int_rn(s_u[q * C + i] * S);
+            }
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < KK; ++k) {
             const int m = tid + k * TPB;
             if (m < nm) {
-                const MarkerLoc L = locate(s_ps, np, m);
-                const PS &s = s_ps[L.ps];
-                int b[3];
-                float w[3][3];
-                rel_stencil(s, prm.t32, prm.t64, L.l, b, w);
-                int slot[9];
-                row_slots(s_row, it.W, it.By, b, slot);
-                const float D = s.P.D * S;
-                float g[NC];
+                const int pi = locate(s_ps, np, m);
+                const PS &s = s_ps[pi];
+                const int l = m - s.mstart;
+                if (l < s.P.nl) {
+                    const CS &cs = s_cs[s.cl];
+                    int b[3];
+                    float w[3][3];
+                    rel_stencil(s, prm.t32, prm.t64, l, b, w);
+                    int slot[9];
+                    row_slots(s_row + cs.row0, cs.W, cs.By, b, slot);
+                    const float D = s.P.D * (DET ? cs.S : 1.f);
+                    float g[NC];
 #pragma unroll
-                for (int q = 0; q < NC; ++q) g[q] = ereg[k][q] * D;
+                    for (int q = 0; q < NC; ++q) g[q] = ereg[k][q] * D;
 #pragma unroll
-                for (int dz = 0; dz < 3; ++dz)
+                    for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-                    for (int dy = 0; dy < 3; ++dy) {
-                        const int sl = slot[dz * 3 + dy];
-                        const float wyz = w[2][dz] * w[1][dy];
+                        for (int dy = 0; dy < 3; ++dy) {
+                            const int sl = slot[dz * 3 + dy];
+                            const float wyz = w[2][dz] * w[1][dy];
 #pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) {
-                            const float a = wyz * w[0][dx];
+                            for (int dx = 0; dx < 3; ++dx) {
+                                const float a = wyz * w[0][dx];
 #pragma unroll
-                            for (int q = 0; q < NC; ++q) {
-                                if (DET) atomicAdd(&s_ui[q * C + sl + dx], __float2int_rn(a * g[q]));
-                                else atomicAdd(&s_u[q * C + sl + dx], a * g[q]);
+                                for (int q = 0; q < NC; ++q) {
+                                    if (DET) atomicAdd(&s_ui[q * C + sl + dx], __float2int_rn(a * g[q]));
+                                    else atomicAdd(&s_u[q * C + sl + dx], a * g[q]);
+                                }
                             }
                         }
-                    }
+                }
             }
         }
         __syncthreads();
         if (DET) {
-            for (int i = tid; i < NC * C; i += TPB) s_u[i] = (float)s_ui[i] * invS;
+            for (int j = 0; j < bt.nb; ++j) {
+                const int s0 = s_cs[j].slot0, s1 = (j + 1 < bt.nb) ? s_cs[j + 1].slot0 : C;
+                const float invS = s_cs[j].invS;
+                for (int q = 0; q < NC; ++q)
+                    for (int i = s0 + tid; i < s1; i += TPB) s_u[q * C + i] = (float)s_ui[q * C + i] * invS;
+            }
             __syncthreads();
         }
     }
 }
 
-// One persistent CTA per SM; clusters come from a work list ordered by size.
-// DET = fixed-point spreading (int32 shared-memory atomics, bit-reproducible).
+// One persistent CTA per SM.  DET = fixed-point spreading (int32 shared-memory
+// atomics, bit-reproducible and independent of how clusters are batched).
 template <int TPB, int KM, bool DET>
 __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
     constexpr int NCH = TPB * KM / 32;   // 32-marker chunks
     extern __shared__ __align__(16) unsigned char smem[];
     PS *s_ps = reinterpret_cast<PS *>(smem);
-    double *s_acc = reinterpret_cast<double *>(s_ps + kCapP);             // [kCapP][6] (rare overflow)
-    float *s_part = reinterpret_cast<float *>(s_acc + 6 * kCapP);         // [NCH][kSlots][6]
-    uint2 *s_row = reinterpret_cast<uint2 *>(s_part + NCH * kSlots * 6);  // [R] then the cells
+    CS *s_cs = reinterpret_cast<CS *>(s_ps + kCapP);
+    double *s_acc = reinterpret_cast<double *>(s_cs + kCapCl);           // [kCapP][6]
+    float *s_part = reinterpret_cast<float *>(s_acc + 6 * kCapP);        // [NCH][6]
+    uint2 *s_row = reinterpret_cast<uint2 *>(s_part + NCH * 6);          // [R] then the cells
     unsigned char *dyn_end = smem + prm.smem_bytes;
-    __shared__ int s_item, s_flag, s_scan[32], s_total;
-    __shared__ float s_red[32];
+    __shared__ int s_w, s_c0, s_c1, s_nb, s_np, s_nm, s_R, s_flag, s_scan[32], s_total;
     const int tid = threadIdx.x;
+    const int n_items = prm.cnt[C_NITEMS];
+    const int n_windows = (prm.cum[n_items] + kWindow - 1) / kWindow;
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(prm.cnt + C_WORK, 1);
+        if (tid == 0) s_w = atomicAdd(prm.cnt + C_WORK, 1);
         __syncthreads();
-        const int item = s_item;
-        if (item >= prm.cnt[C_NITEMS]) break;
-        const int c = prm.order[item];
-        Item it;
-        it.np = prm.cl_np[c];
-        it.nm = prm.cl_nm[c];
-        const int first = prm.cl_first[c];
-        const int *box = prm.cl_box + 12 * c;
-        it.x0 = box[0]; it.y0 = box[1]; it.z0 = box[2];
-        const int Bx = box[3] - it.x0 + 1, By = box[4] - it.y0 + 1, Bz = box[5] - it.z0 + 1;
-        it.W = (Bx + 31) >> 5;
-        it.By = By;
-        it.R = By * Bz * it.W;
-        const int np = it.np, nm = it.nm;
-        float *s_u = reinterpret_cast<float *>(s_row + ((it.R + 1) & ~1));
-        const int cap_cells = (int)((dyn_end - reinterpret_cast<unsigned char *>(s_u)) / 4);
-        // particle table, sorted by global index so the marker numbering is fixed
-        if (tid < np) s_ps[tid].gid = prm.cl_plist[first + tid];
-        if (tid == 0) s_flag = 0;
-        __syncthreads();
+        const int w = s_w;
+        if (w >= n_windows) break;
         if (tid == 0) {
-            for (int i = 1; i < np; ++i) {
-                const int v = s_ps[i].gid;
-                int j = i - 1;
-                while (j >= 0 && s_ps[j].gid > v) { s_ps[j + 1].gid = s_ps[j].gid; --j; }
-                s_ps[j + 1].gid = v;
+            s_c0 = lower_bound_int(prm.cum, n_items, w * kWindow);
+            s_c1 = lower_bound_int(prm.cum, n_items, (w + 1) * kWindow);
+        }
+        __syncthreads();
+        int c0 = s_c0;
+        const int c1 = s_c1;
+        while (c0 < c1) {
+            // greedy batch of consecutive clusters [c0, c) within the capacities
+            if (tid == 0) {
+                int nb = 0, np = 0, nm = 0, R = 0, c = c0;
+                while (c < c1 && nb < kCapCl) {
+                    const int id = prm.order[c];
+                    const int cnp = prm.cl_np[id], cnm = prm.cl_nm[id];
+                    const int *box = prm.cl_box + 12 * id;
+                    const int Bx = box[3] - box[0] + 1, By = box[4] - box[1] + 1, Bz = box[5] - box[2] + 1;
+                    const int W = (Bx + 31) >> 5, cR = By * Bz * W;
+                    if (nb > 0 && (np + cnp > kCapP || nm + cnm > TPB * (KM / 3) || R + cR > prm.max_rows)) break;
+                    CS &cs = s_cs[nb];
+                    cs.x0 = box[0]; cs.y0 = box[1]; cs.z0 = box[2];
+                    cs.Bx = Bx; cs.By = By; cs.Bz = Bz; cs.W = W; cs.R = cR; cs.row0 = R;
+                    cs.first = prm.cl_first[id]; cs.np = cnp; cs.pstart = np;
+                    np += cnp; nm += cnm; R += cR; ++nb; ++c;
+                }
+                s_nb = nb; s_np = np; s_R = R; s_c0 = c;
+                s_flag = 0;
             }
-        }
-        __syncthreads();
-        if (tid < np) {
-            const int p = s_ps[tid].gid;
-            s_ps[tid].P = prm.P[p];
-            s_ps[tid].off[0] = prm.poff[3 * p] - it.x0;
-            s_ps[tid].off[1] = prm.poff[3 * p + 1] - it.y0;
-            s_ps[tid].off[2] = prm.poff[3 * p + 2] - it.z0;
-        }
-        for (int i = tid; i < 6 * np; i += TPB) s_acc[i] = 0.0;
-        for (int i = tid; i < ((nm + 31) >> 5) * kSlots * 6; i += TPB) s_part[i] = 0.f;
-        for (int i = tid; i < it.R; i += TPB) s_row[i].x = 0u;
-        __syncthreads();
-        if (tid == 0) {
-            int m = 0;
-            for (int i = 0; i < np; ++i) { s_ps[i].mstart = m; m += s_ps[i].P.nl; }
-        }
-        __syncthreads();
-        const int scene = s_ps[0].P.scene;
-        it.nx = prm.dims[3 * scene]; it.ny = prm.dims[3 * scene + 1]; it.nz = prm.dims[3 * scene + 2];
-        it.ncell = (long long)it.nx * it.ny * it.nz;
-        it.dmax = 0.f;
-        for (int i = 0; i < np; ++i) it.dmax = fmaxf(it.dmax, s_ps[i].P.D);
+            __syncthreads();
+            Batch bt;
+            bt.nb = s_nb; bt.np = s_np; bt.R = s_R;
+            c0 = s_c0;
+            const int np = bt.np;
+            // particle table, sorted by global index (fixed marker numbering)
+            if (tid < np) {
+                const int j = [&] {
+                    int lo = 0, hi = bt.nb - 1;
+                    while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (s_cs[mid].pstart <= tid) lo = mid; else hi = mid - 1; }
+                    return lo;
+                }();
+                s_ps[tid].gid = prm.cl_plist[s_cs[j].first + tid - s_cs[j].pstart];
+                s_ps[tid].cl = j;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                for (int i = 1; i < np; ++i) {
+                    const int v = s_ps[i].gid, vc = s_ps[i].cl;
+                    int j = i - 1;
+                    while (j >= 0 && s_ps[j].gid > v) { s_ps[j + 1].gid = s_ps[j].gid; s_ps[j + 1].cl = s_ps[j].cl; --j; }
+                    s_ps[j + 1].gid = v;
+                    s_ps[j + 1].cl = vc;
+                }
+            }
+            __syncthreads();
+            if (tid < np) {
+                const int p = s_ps[tid].gid;
+                const CS &cs = s_cs[s_ps[tid].cl];
+                s_ps[tid].P = prm.P[p];
+                s_ps[tid].off[0] = prm.poff[3 * p] - cs.x0;
+                s_ps[tid].off[1] = prm.poff[3 * p + 1] - cs.y0;
+                s_ps[tid].off[2] = prm.poff[3 * p + 2] - cs.z0;
+            }
+            for (int i = tid; i < bt.R; i += TPB) s_row[i].x = 0u;
+            __syncthreads();
+            if (tid == 0) {
+                int m = 0;
+                for (int i = 0; i < np; ++i) { s_ps[i].mstart = m; m += (s_ps[i].P.nl + 31) & ~31; }
+                s_nm = m;
+                for (int j = 0; j < bt.nb; ++j) {
+                    s_cs[j].scene = s_ps[0].P.scene;
+                    s_cs[j].dmax = 0.f;
+                }
+                for (int i = 0; i < np; ++i) {
+                    CS &cs = s_cs[s_ps[i].cl];
+                    cs.scene = s_ps[i].P.scene;
+                    cs.dmax = fmaxf(cs.dmax, s_ps[i].P.D);
+                }
+            }
+            __syncthreads();
+            bt.nm = s_nm;
+            const int nm = bt.nm;
+            for (int i = tid; i < (nm >> 5) * 6; i += TPB) s_part[i] = 0.f;
 
-        // 1. touched-cell bitmask (bounds-checked)
-        for (int m = tid; m < nm; m += TPB) {
-            const MarkerLoc L = locate(s_ps, np, m);
-            int b[3];
-            float w[3][3];
-            rel_stencil(s_ps[L.ps], prm.t32, prm.t64, L.l, b, w);
-            if (b[0] < 1 || b[0] > Bx - 2 || b[1] < 1 || b[1] > By - 2 || b[2] < 1 || b[2] > Bz - 2) {
-                s_flag = 1;
+            // 1. touched-cell bitmask of every cluster (bounds-checked)
+            for (int m = tid; m < nm; m += TPB) {
+                const int pi = locate(s_ps, np, m);
+                const PS &s = s_ps[pi];
+                const int l = m - s.mstart;
+                if (l >= s.P.nl) continue;
+                const CS &cs = s_cs[s.cl];
+                int b[3];
+                float wt[3][3];
+                rel_stencil(s, prm.t32, prm.t64, l, b, wt);
+                if (b[0] < 1 || b[0] > cs.Bx - 2 || b[1] < 1 || b[1] > cs.By - 2 || b[2] < 1 || b[2] > cs.Bz - 2) {
+                    s_flag = 1;
+                    continue;
+                }
+                const int x = b[0] - 1, wx = x >> 5, bit = x & 31;
+                uint2 *rt = s_row + cs.row0;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        const int row = (b[2] + dz) * cs.By + (b[1] + dy);
+                        atomicOr(&rt[row * cs.W + wx].x, 7u << bit);
+                        if (bit > 29) atomicOr(&rt[row * cs.W + wx + 1].x, 7u >> (32 - bit));
+                    }
+            }
+            __syncthreads();
+            // 2. compact slots: exclusive prefix of the popcounts over all rows
+            {
+                const int per = (bt.R + TPB - 1) / TPB;
+                const int lo = min(bt.R, tid * per), hi = min(bt.R, lo + per);
+                int sum = 0;
+                for (int i = lo; i < hi; ++i) sum += __popc(s_row[i].x);
+                int total;
+                int run = block_excl_scan<TPB>(sum, s_scan, &total);
+                for (int i = lo; i < hi; ++i) {
+                    s_row[i].y = (unsigned)run;
+                    run += __popc(s_row[i].x);
+                }
+                if (tid == 0) s_total = total;
+            }
+            __syncthreads();
+            bt.C = s_total;
+            for (int j = tid; j < bt.nb; j += TPB) s_cs[j].slot0 = (int)s_row[s_cs[j].row0].y;
+            float *s_u = reinterpret_cast<float *>(s_row + ((bt.R + 3) & ~3));
+            const int cap_cells = (int)((dyn_end - reinterpret_cast<unsigned char *>(s_u)) / 4);
+            const bool three = 3 * bt.C <= cap_cells && nm <= TPB * (KM / 3);
+            if (s_flag || bt.C > cap_cells || nm > TPB * KM) {
+                // does not fit even one component at a time: hand it to the plain path
+                if (tid == 0) {
+                    int np_fb = 0;
+                    for (int j = 0; j < bt.nb; ++j) np_fb += s_cs[j].np;
+                    const int k0 = atomicAdd(prm.cnt + C_NFB, np_fb);
+                    atomicAdd(prm.cnt + C_FBMARK, nm);
+                    atomicAdd(prm.cnt + C_OVERFLOW, bt.nb);
+                    for (int i = 0; i < np; ++i) prm.fb_list[k0 + i] = s_ps[i].gid;
+                }
+                __syncthreads();
                 continue;
             }
-            const int x = b[0] - 1, wx = x >> 5, bit = x & 31;
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const int row = (b[2] + dz) * By + (b[1] + dy);
-                    atomicOr(&s_row[row * it.W + wx].x, 7u << bit);
-                    if (bit > 29) atomicOr(&s_row[row * it.W + wx + 1].x, 7u >> (32 - bit));
-                }
-        }
-        __syncthreads();
-        // 2. compact slots: exclusive prefix of the popcounts
-        {
-            const int per = (it.R + TPB - 1) / TPB;
-            const int lo = min(it.R, tid * per), hi = min(it.R, lo + per);
-            int sum = 0;
-            for (int i = lo; i < hi; ++i) sum += __popc(s_row[i].x);
-            int total;
-            int run = block_excl_scan<TPB>(sum, s_scan, &total);
-            for (int i = lo; i < hi; ++i) {
-                s_row[i].y = (unsigned)run;
-                run += __popc(s_row[i].x);
-            }
-            if (tid == 0) s_total = total;
-        }
-        __syncthreads();
-        it.C = s_total;
-        const bool three = 3 * it.C <= cap_cells && nm <= TPB * (KM / 3);
-        if (s_flag || it.C > cap_cells) {
-            // does not fit even one component at a time: hand the cluster to the plain path
             if (tid == 0) {
-                const int k0 = atomicAdd(prm.cnt + C_NFB, np);
-                atomicAdd(prm.cnt + C_FBMARK, nm);
-                atomicAdd(prm.cnt + C_OVERFLOW, 1);
-                for (int i = 0; i < np; ++i) prm.fb_list[k0 + i] = s_ps[i].gid;
+                atomicMax(prm.cnt + C_MAXCELLS, bt.C);
+                atomicAdd(prm.cnt + C_TOUCHED, bt.C);
+                if (!three) atomicAdd(prm.cnt + C_ONECOMP, bt.nb);
             }
             __syncthreads();
-            continue;
-        }
-        if (tid == 0) {
-            atomicMax(prm.cnt + C_MAXCELLS, it.C);
-            atomicAdd(prm.cnt + C_TOUCHED, it.C);
-            if (!three) atomicAdd(prm.cnt + C_ONECOMP, 1);
-        }
-        const float *ug = prm.uf[scene];
-        float *uo = prm.uf[scene];
-        float *fo = prm.ff ? prm.ff[scene] : nullptr;
-        if (three) {
-            move_cells<TPB, 3, true>(it, s_row, s_u, ug, uo, fo, prm.finv, 0);
+            if (three) {
+                move_cells<TPB, 3, true>(prm, bt, s_cs, s_row, s_u, 0);
+                __syncthreads();
+                forcing_loop<TPB, KM, DET, 3>(prm, bt, s_ps, s_cs, s_part, s_row, s_u, 0);
+                move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_u, 0);
+            } else {
+                for (int q = 0; q < 3; ++q) {
+                    move_cells<TPB, 1, true>(prm, bt, s_cs, s_row, s_u, q);
+                    __syncthreads();
+                    forcing_loop<TPB, KM, DET, 1>(prm, bt, s_ps, s_cs, s_part, s_row, s_u, q);
+                    move_cells<TPB, 1, false>(prm, bt, s_cs, s_row, s_u, q);
+                    __syncthreads();
+                }
+            }
+            // particle loads: sums of the particle's own chunks in marker order, FP64
+            for (int i = tid; i < 6 * np; i += TPB) {
+                const int pi = i / 6, q = i - 6 * pi;
+                const int ms = s_ps[pi].mstart, nl = s_ps[pi].P.nl;
+                double sum = 0.0;
+                for (int ch = ms >> 5; ch < (ms + nl + 31) >> 5; ++ch) sum += (double)s_part[ch * 6 + q];
+                const int p = s_ps[pi].gid;
+                if (q < 3) prm.FD[3 * p + q] = sum;
+                else prm.TD[3 * p + q - 3] = sum;
+            }
             __syncthreads();
-            forcing_loop<TPB, KM, DET, 3>(prm, it, s_ps, s_acc, s_part, s_row, s_u, s_red, 0);
-            move_cells<TPB, 3, false>(it, s_row, s_u, ug, uo, fo, prm.finv, 0);
-        } else {
-            for (int q = 0; q < 3; ++q) {
-                move_cells<TPB, 1, true>(it, s_row, s_u, ug, uo, fo, prm.finv, q);
-                __syncthreads();
-                forcing_loop<TPB, KM, DET, 1>(prm, it, s_ps, s_acc, s_part, s_row, s_u, s_red, q);
-                move_cells<TPB, 1, false>(it, s_row, s_u, ug, uo, fo, prm.finv, q);
-                __syncthreads();
-            }
         }
-        // particle loads: chunk partials in a fixed order, FP64
-        for (int i = tid; i < 6 * np; i += TPB) {
-            const int pi = i / 6, q = i - 6 * pi;
-            const int ms = s_ps[pi].mstart, me = ms + s_ps[pi].P.nl;
-            double sum = s_acc[i];
-            for (int ch = ms >> 5; ch <= (me - 1) >> 5; ++ch) {
-                const int sl = pi - locate(s_ps, np, ch << 5).ps;
-                if (sl < kSlots) sum += (double)s_part[(ch * kSlots + sl) * 6 + q];
-            }
-            const int p = s_ps[pi].gid;
-            if (q < 3) prm.FD[3 * p + q] = sum;
-            else prm.TD[3 * p + q - 3] = sum;
-        }
-        __syncthreads();
     }
 }
 
@@ -865,7 +979,7 @@ void cluster_free(ibm_ctx *ctx) {
     int *ptrs[] = {S->scene_bin_off, S->scene_nb, S->bin_cnt, S->bin_start, S->bin_cur, S->bin_items,
                    S->parent, S->cand, S->cnt, S->root_flag, S->cid, S->pcl, S->poff, S->cl_np, S->cl_nm,
                    S->cl_first, S->cl_cur, S->cl_box, S->cl_plist, S->cl_bkt, S->bkt_cnt, S->bkt_start,
-                   S->order, S->fb_list};
+                   S->order, S->fb_list, S->nm_ord, S->cum};
     for (int *p : ptrs)
         if (p) cudaFree(p);
     if (S->tot) cudaFree(S->tot);
@@ -920,7 +1034,8 @@ static ibm_status cluster_alloc(ibm_ctx *ctx) {
     if (realloc_p) {
         const int cp = std::max(ctx->cap_p, np);
         int **arrs[] = {&S->bin_items, &S->parent, &S->root_flag, &S->cid, &S->pcl, &S->cl_np, &S->cl_nm,
-                        &S->cl_first, &S->cl_cur, &S->cl_plist, &S->cl_bkt, &S->order, &S->fb_list};
+                        &S->cl_first, &S->cl_cur, &S->cl_plist, &S->cl_bkt, &S->order, &S->fb_list,
+                        &S->nm_ord, &S->cum};
         for (int **p : arrs) {
             if (*p) cudaFree(*p);
             CK(cudaMalloc(p, (size_t)(cp + 1) * sizeof(int)), "alloc cluster scratch");
@@ -1006,7 +1121,9 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
                                         S->fb_list, S->cnt);
     k_scan1<<<1, 1024, 0, sm>>>(S->bkt_cnt, S->bkt_start, kBuckets, S->tot + 3);
     k_order_fill<<<gb, 256, 0, sm>>>(S->tot + 1, S->cl_bkt, S->bkt_start, S->bkt_start + kBuckets + 1, S->order);
-    ctx->launches += 13;
+    k_gather_nm<<<gb, 256, 0, sm>>>(n, S->cnt, S->order, S->cl_nm, S->nm_ord);
+    k_scan1<<<1, 1024, 0, sm>>>(S->nm_ord, S->cum, n, S->tot + 3);
+    ctx->launches += 15;
 
     KParams prm;
     prm.P = ctx->pinfo;
@@ -1016,6 +1133,8 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prm.uf = reinterpret_cast<float *const *>(ctx->uptr_d);
     prm.ff = f_out ? reinterpret_cast<float *const *>(ctx->fptr_d) : nullptr;
     prm.order = S->order;
+    prm.cum = S->cum;
+    prm.max_rows = max_rows;
     prm.cl_first = S->cl_first;
     prm.cl_np = S->cl_np;
     prm.cl_nm = S->cl_nm;

@@ -372,26 +372,27 @@ __global__ void __launch_bounds__(kBlock) k_slip(const PInfo *__restrict__ P, in
             marker_stencil(Pp, tt64, tt32, S);
             T ud[3], r[3], D;
             marker_kinematics(up, om, p, Pp, tt64, tt32, ud, r, D);
-            double U[3] = {0, 0, 0};
+            // evaluated in the path's own precision T; summed over markers in FP64
+            T U[3] = {T(0), T(0), T(0)};
             for (int cz = 0; cz < 3; ++cz) {
                 const int kk = wrapi(S.b[2] - 1 + cz, g.nz);
                 for (int cy = 0; cy < 3; ++cy) {
                     const int jj = wrapi(S.b[1] - 1 + cy, g.ny);
                     const long long row = ((long long)kk * g.ny + jj) * g.nx;
                     for (int cx = 0; cx < 3; ++cx) {
-                        const double w = (double)S.w[2][cz] * (double)S.w[1][cy] * (double)S.w[0][cx];
+                        const T w = S.w[2][cz] * S.w[1][cy] * S.w[0][cx];
                         const long long idx = row + wrapi(S.b[0] - 1 + cx, g.nx);
-                        for (int q = 0; q < 3; ++q) U[q] += w * (double)u[q * g.ncell + idx];
+                        for (int q = 0; q < 3; ++q) U[q] += w * u[q * g.ncell + idx];
                     }
                 }
             }
-            double e2 = 0.0;
+            T e2 = T(0);
             for (int q = 0; q < 3; ++q) {
-                const double e = (double)ud[q] - U[q];
+                const T e = ud[q] - U[q];
                 e2 += e * e;
             }
-            s2[0] += e2;
-            mx = fmax(mx, sqrt(e2));
+            s2[0] += (double)e2;
+            mx = fmax(mx, sqrt((double)e2));
         }
         mx = warp_max(mx);
         if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mx;
