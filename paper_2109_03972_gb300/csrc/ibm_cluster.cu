@@ -58,6 +58,7 @@ enum {
     C_TOUCHED,
     C_FBMARK,     // markers on the fallback path
     C_ONECOMP,    // clusters run one velocity component at a time
+    C_NBATCH,     // shared-memory work items (batches of clusters)
     C_COUNT
 };
 
@@ -73,7 +74,8 @@ struct ClusterScratch {
     int *cl_np = nullptr, *cl_nm = nullptr, *cl_first = nullptr, *cl_cur = nullptr, *cl_box = nullptr;
     int *cl_plist = nullptr, *cl_bkt = nullptr;
     int *bkt_cnt = nullptr, *bkt_start = nullptr, *order = nullptr, *fb_list = nullptr;
-    int *nm_ord = nullptr, *cum = nullptr;
+    int *nm_ord = nullptr, *cum = nullptr, *cl_scene = nullptr;
+    int2 *batches = nullptr;
     int smem_bytes = 0, cap_c = 0, tpb = 0, kmax = 0, det = -1;
 };
 
@@ -321,11 +323,13 @@ __global__ void k_cluster_fill(int n_p, const int *pcl, const int *cl_first, int
 // its box is consistently unwrapped, else the plain fallback.
 __global__ void k_cluster_route(const long long *n_clust_d, const PInfo *P, const int32_t *dims, const int *cl_np,
                                 const int *cl_nm, const int *cl_first, const int *cl_plist, const int *cl_box,
-                                int cap_m, int max_rows, int *cl_bkt, int *bkt_cnt, int *fb_list, int *cnt) {
+                                int cap_m, int max_rows, int *cl_bkt, int *bkt_cnt, int *fb_list, int *cl_scene,
+                                int *cnt) {
     const int n = (int)*n_clust_d;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const int np = cl_np[c], nm = cl_nm[c];
         const int s = P[cl_plist[cl_first[c]]].scene;
+        cl_scene[c] = s;
         bool ok = np <= kCapP && nm <= cap_m;
         int R = 1;
         for (int k = 0; k < 3; ++k) {
@@ -367,6 +371,50 @@ __global__ void k_gather_nm(int n_max, const int *cnt, const int *order, const i
         out[i] = i < n ? cl_nm[order[i]] : 0;
 }
 
+__device__ __forceinline__ int lower_bound_int(const int *a, int n, int v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+constexpr int kCapCl = 32;      // clusters per batch
+constexpr int kWindow = 2048;   // markers per packing window
+
+// Work items of the shared-memory kernel.  The padded marker prefix of the
+// size-ordered cluster list is cut into windows of kWindow markers; the
+// clusters that start in one window are split greedily into batches that fit
+// one CTA (kCapCl clusters, kCapP particles, cap_m3 markers, max_rows row-table
+// entries), so that small clusters share a CTA.
+__global__ void k_batch_plan(const int *cnt_in, const int *cum, const int *order, const int *cl_np,
+                             const int *cl_nm, const int *cl_box, int cap_m3, int max_rows, int2 *batches,
+                             int *cnt) {
+    const int n_items = cnt_in[C_NITEMS];
+    const int nw = (cum[n_items] + kWindow - 1) / kWindow;
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+        const int c0 = lower_bound_int(cum, n_items, w * kWindow);
+        const int c1 = lower_bound_int(cum, n_items, (w + 1) * kWindow);
+        int c = c0;
+        while (c < c1) {
+            const int start = c;
+            int nb = 0, np = 0, nm = 0, R = 0;
+            while (c < c1 && nb < kCapCl) {
+                const int id = order[c];
+                const int *box = cl_box + 12 * id;
+                const int W = (box[3] - box[0] + 1 + 31) >> 5;
+                const int cR = (box[4] - box[1] + 1) * (box[5] - box[2] + 1) * W;
+                const int cnp = cl_np[id], cnm = cl_nm[id];
+                if (nb > 0 && (np + cnp > kCapP || nm + cnm > cap_m3 || R + cR > max_rows)) break;
+                np += cnp; nm += cnm; R += cR; ++nb; ++c;
+            }
+            batches[atomicAdd(cnt + C_NBATCH, 1)] = make_int2(start, c);
+        }
+    }
+}
+
 // Single-block exclusive scan (same as the set-up scan), local copy.
 __global__ void k_scan1(const int *in, int *out, int n, long long *total) {
     __shared__ long long part[1024];
@@ -405,9 +453,6 @@ __global__ void k_scan1(const int *in, int *out, int n, long long *total) {
 // capacity), so that small clusters (a single D = 12h sphere has 452 markers)
 // share a CTA instead of leaving most of its threads idle.
 
-constexpr int kCapCl = 32;      // clusters per batch
-constexpr int kWindow = 2048;   // markers per packing window
-
 struct PS {          // particle record in shared memory
     PInfo P;
     int off[3];      // absolute base cell + off = cell relative to its cluster's box
@@ -434,7 +479,8 @@ struct KParams {
     const int32_t *dims;
     float *const *uf;
     float *const *ff;
-    const int *order, *cum, *cl_first, *cl_np, *cl_nm, *cl_box, *cl_plist, *poff;
+    const int *order, *cl_first, *cl_np, *cl_nm, *cl_box, *cl_plist, *cl_scene, *poff;
+    const int2 *batches;
     int *cnt, *fb_list, *err;
     double *FD, *TD;
     int n_forcing, smem_bytes, max_rows;
@@ -488,16 +534,6 @@ __device__ __forceinline__ int upper_index(const CS *cs, int n, int v, bool by_s
         const int mid = (lo + hi + 1) >> 1;
         if ((by_slot ? cs[mid].slot0 : cs[mid].row0) <= v) lo = mid;
         else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int lower_bound_int(const int *a, int n, int v) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] < v) lo = mid + 1;
-        else hi = mid;
     }
     return lo;
 }
@@ -772,47 +808,53 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
     float *s_part = reinterpret_cast<float *>(s_acc + 6 * kCapP);        // [NCH][6]
     uint2 *s_row = reinterpret_cast<uint2 *>(s_part + NCH * 6);          // [R] then the cells
     unsigned char *dyn_end = smem + prm.smem_bytes;
-    __shared__ int s_w, s_c0, s_c1, s_nb, s_np, s_nm, s_R, s_flag, s_scan[32], s_total;
+    __shared__ int s_w, s_np, s_nm, s_R, s_flag, s_scan[32], s_total;
     const int tid = threadIdx.x;
-    const int n_items = prm.cnt[C_NITEMS];
-    const int n_windows = (prm.cum[n_items] + kWindow - 1) / kWindow;
+    const int n_batches = prm.cnt[C_NBATCH];
 
     for (;;) {
         if (tid == 0) s_w = atomicAdd(prm.cnt + C_WORK, 1);
         __syncthreads();
         const int w = s_w;
-        if (w >= n_windows) break;
-        if (tid == 0) {
-            s_c0 = lower_bound_int(prm.cum, n_items, w * kWindow);
-            s_c1 = lower_bound_int(prm.cum, n_items, (w + 1) * kWindow);
-        }
-        __syncthreads();
-        int c0 = s_c0;
-        const int c1 = s_c1;
-        while (c0 < c1) {
-            // greedy batch of consecutive clusters [c0, c) within the capacities
-            if (tid == 0) {
-                int nb = 0, np = 0, nm = 0, R = 0, c = c0;
-                while (c < c1 && nb < kCapCl) {
-                    const int id = prm.order[c];
-                    const int cnp = prm.cl_np[id], cnm = prm.cl_nm[id];
+        if (w >= n_batches) break;
+        {
+            const int2 be = prm.batches[w];
+            const int nbl = be.y - be.x;
+            // cluster records, loaded in parallel; prefix sums over the batch in warp 0
+            if (tid < 32) {
+                int cnp = 0, cR = 0;
+                if (tid < nbl) {
+                    const int id = prm.order[be.x + tid];
                     const int *box = prm.cl_box + 12 * id;
-                    const int Bx = box[3] - box[0] + 1, By = box[4] - box[1] + 1, Bz = box[5] - box[2] + 1;
-                    const int W = (Bx + 31) >> 5, cR = By * Bz * W;
-                    if (nb > 0 && (np + cnp > kCapP || nm + cnm > TPB * (KM / 3) || R + cR > prm.max_rows)) break;
-                    CS &cs = s_cs[nb];
+                    CS &cs = s_cs[tid];
                     cs.x0 = box[0]; cs.y0 = box[1]; cs.z0 = box[2];
-                    cs.Bx = Bx; cs.By = By; cs.Bz = Bz; cs.W = W; cs.R = cR; cs.row0 = R;
-                    cs.first = prm.cl_first[id]; cs.np = cnp; cs.pstart = np;
-                    np += cnp; nm += cnm; R += cR; ++nb; ++c;
+                    cs.Bx = box[3] - box[0] + 1; cs.By = box[4] - box[1] + 1; cs.Bz = box[5] - box[2] + 1;
+                    cs.W = (cs.Bx + 31) >> 5;
+                    cs.R = cs.By * cs.Bz * cs.W;
+                    cs.first = prm.cl_first[id];
+                    cs.np = prm.cl_np[id];
+                    cs.scene = prm.cl_scene[id];
+                    cnp = cs.np;
+                    cR = cs.R;
                 }
-                s_nb = nb; s_np = np; s_R = R; s_c0 = c;
-                s_flag = 0;
+                int sp = cnp, sr = cR;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int a1 = __shfl_up_sync(0xffffffffu, sp, o), a2 = __shfl_up_sync(0xffffffffu, sr, o);
+                    if (tid >= o) { sp += a1; sr += a2; }
+                }
+                if (tid < nbl) {
+                    s_cs[tid].pstart = sp - cnp;
+                    s_cs[tid].row0 = sr - cR;
+                }
+                if (tid == 31) { s_np = sp; s_R = sr; }
+                if (tid == 0) s_flag = 0;
             }
             __syncthreads();
             Batch bt;
-            bt.nb = s_nb; bt.np = s_np; bt.R = s_R;
-            c0 = s_c0;
+            bt.nb = nbl;
+            bt.np = s_np;
+            bt.R = s_R;
             const int np = bt.np;
             // particle table, sorted by global index (fixed marker numbering)
             if (tid < np) {
@@ -849,13 +891,9 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
                 int m = 0;
                 for (int i = 0; i < np; ++i) { s_ps[i].mstart = m; m += (s_ps[i].P.nl + 31) & ~31; }
                 s_nm = m;
-                for (int j = 0; j < bt.nb; ++j) {
-                    s_cs[j].scene = s_ps[0].P.scene;
-                    s_cs[j].dmax = 0.f;
-                }
+                for (int j = 0; j < bt.nb; ++j) s_cs[j].dmax = 0.f;
                 for (int i = 0; i < np; ++i) {
                     CS &cs = s_cs[s_ps[i].cl];
-                    cs.scene = s_ps[i].P.scene;
                     cs.dmax = fmaxf(cs.dmax, s_ps[i].P.D);
                 }
             }
@@ -979,9 +1017,10 @@ void cluster_free(ibm_ctx *ctx) {
     int *ptrs[] = {S->scene_bin_off, S->scene_nb, S->bin_cnt, S->bin_start, S->bin_cur, S->bin_items,
                    S->parent, S->cand, S->cnt, S->root_flag, S->cid, S->pcl, S->poff, S->cl_np, S->cl_nm,
                    S->cl_first, S->cl_cur, S->cl_box, S->cl_plist, S->cl_bkt, S->bkt_cnt, S->bkt_start,
-                   S->order, S->fb_list, S->nm_ord, S->cum};
+                   S->order, S->fb_list, S->nm_ord, S->cum, S->cl_scene};
     for (int *p : ptrs)
         if (p) cudaFree(p);
+    if (S->batches) cudaFree(S->batches);
     if (S->tot) cudaFree(S->tot);
     delete S;
     ctx->cl = nullptr;
@@ -1035,13 +1074,15 @@ static ibm_status cluster_alloc(ibm_ctx *ctx) {
         const int cp = std::max(ctx->cap_p, np);
         int **arrs[] = {&S->bin_items, &S->parent, &S->root_flag, &S->cid, &S->pcl, &S->cl_np, &S->cl_nm,
                         &S->cl_first, &S->cl_cur, &S->cl_plist, &S->cl_bkt, &S->order, &S->fb_list,
-                        &S->nm_ord, &S->cum};
+                        &S->nm_ord, &S->cum, &S->cl_scene};
         for (int **p : arrs) {
             if (*p) cudaFree(*p);
             CK(cudaMalloc(p, (size_t)(cp + 1) * sizeof(int)), "alloc cluster scratch");
         }
         if (S->poff) cudaFree(S->poff);
         if (S->cl_box) cudaFree(S->cl_box);
+        if (S->batches) cudaFree(S->batches);
+        CK(cudaMalloc(&S->batches, (size_t)(cp + 1) * sizeof(int2)), "alloc batch list");
         CK(cudaMalloc(&S->poff, 3 * (size_t)cp * sizeof(int)), "alloc cluster scratch");
         CK(cudaMalloc(&S->cl_box, 12 * (size_t)cp * sizeof(int)), "alloc cluster scratch");
         S->cap_cand = std::max(1 << 16, 16 * cp);
@@ -1118,12 +1159,16 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     k_cluster_fill<<<gb, 256, 0, sm>>>(n, S->pcl, S->cl_first, S->cl_cur, S->cl_plist);
     k_cluster_route<<<gb, 256, 0, sm>>>(S->tot + 1, ctx->pinfo, ctx->dims_d, S->cl_np, S->cl_nm, S->cl_first,
                                         S->cl_plist, S->cl_box, cap_m, max_rows, S->cl_bkt, S->bkt_cnt,
-                                        S->fb_list, S->cnt);
+                                        S->fb_list, S->cl_scene, S->cnt);
     k_scan1<<<1, 1024, 0, sm>>>(S->bkt_cnt, S->bkt_start, kBuckets, S->tot + 3);
     k_order_fill<<<gb, 256, 0, sm>>>(S->tot + 1, S->cl_bkt, S->bkt_start, S->bkt_start + kBuckets + 1, S->order);
     k_gather_nm<<<gb, 256, 0, sm>>>(n, S->cnt, S->order, S->cl_nm, S->nm_ord);
     k_scan1<<<1, 1024, 0, sm>>>(S->nm_ord, S->cum, n, S->tot + 3);
-    ctx->launches += 15;
+    const long long max_windows = (ctx->n_markers + 32ll * n) / kWindow + 2;
+    k_batch_plan<<<grid_for(max_windows, 128), 128, 0, sm>>>(S->cnt, S->cum, S->order, S->cl_np, S->cl_nm,
+                                                            S->cl_box, tpb * (markers_per_thread(tpb) / 3),
+                                                            max_rows, S->batches, S->cnt);
+    ctx->launches += 16;
 
     KParams prm;
     prm.P = ctx->pinfo;
@@ -1133,7 +1178,8 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prm.uf = reinterpret_cast<float *const *>(ctx->uptr_d);
     prm.ff = f_out ? reinterpret_cast<float *const *>(ctx->fptr_d) : nullptr;
     prm.order = S->order;
-    prm.cum = S->cum;
+    prm.batches = S->batches;
+    prm.cl_scene = S->cl_scene;
     prm.max_rows = max_rows;
     prm.cl_first = S->cl_first;
     prm.cl_np = S->cl_np;
