@@ -382,7 +382,7 @@ __device__ __forceinline__ int lower_bound_int(const int *a, int n, int v) {
 }
 
 constexpr int kCapCl = 32;      // clusters per batch
-constexpr int kWindow = 2048;   // markers per packing window
+constexpr int kWindow = 1024;   // markers per packing window
 
 // Work items of the shared-memory kernel.  The padded marker prefix of the
 // size-ordered cluster list is cut into windows of kWindow markers; the
@@ -464,7 +464,9 @@ struct PS {          // particle record in shared memory
 struct CS {          // cluster record in shared memory
     int x0, y0, z0, Bx, By, Bz, W, R;
     int row0;        // first row-table entry
-    int slot0;       // first cell slot
+    int slot0;       // first cell slot (a multiple of 4)
+    int ncell;       // touched cells of the cluster
+    int shift;       // padding added to the prefix slots of its rows
     int pstart;      // first particle of the cluster in the batch (before sorting)
     int first, np;   // particles in cl_plist
     int scene;
@@ -551,6 +553,15 @@ __device__ __forceinline__ void rel_stencil(const PS &s, const float *t32, const
     }
 }
 
+// Box-relative base cell and fractional position of a marker (FP32 path).
+__device__ __forceinline__ void rel_base(const PS &s, const float *t32, const double *t64, int l, int b[3],
+                                         float f[3]) {
+    const float *t = t32 + 3ll * (s.P.toff + l);
+    const double *t6 = t64 + 3ll * (s.P.toff + l);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) b[c] = marker_split32(s.P, t, t6, c, &f[c]) + s.off[c];
+}
+
 __device__ __forceinline__ void row_slots(const uint2 *rt, int W, int By, const int b[3], int slot[9]) {
     const int x = b[0] - 1;
     const int wx = x >> 5;
@@ -573,9 +584,11 @@ __device__ __forceinline__ void cp_async4(void *smem_ptr, const void *gmem_ptr) 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <int TPB, int KM>
-constexpr int fixed_smem_bytes() {
-    return (int)(sizeof(PS) * kCapP + sizeof(CS) * kCapCl + sizeof(double) * 6 * kCapP +
-                 sizeof(float) * (TPB * KM / 32) * 6);
+__host__ __device__ constexpr int fixed_smem_bytes() {
+    // particle and cluster tables, overflow accumulators, chunk sums, chunk -> particle;
+    // the row table that follows starts 16-byte aligned
+    return (int)(((sizeof(PS) * kCapP + sizeof(CS) * kCapCl + sizeof(double) * 6 * kCapP +
+                   sizeof(float) * (TPB * KM / 32) * 6 + ((TPB * KM / 32 + 15) & ~15)) + 15) & ~15);
 }
 
 struct Batch {
@@ -583,13 +596,18 @@ struct Batch {
 };
 
 // Gather (LOAD) or write back the touched cells of components q0..q0+NC-1 of
-// every cluster of the batch.  Slots of one x-row run are consecutive.
+// every cluster of the batch: one warp per (row, 32-cell word) of a cluster's
+// bitmask, one lane per cell, so the accesses of a row run are coalesced.
+// Slots of one x-row run are consecutive.
 template <int TPB, int NC, bool LOAD>
 __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, const CS *s_cs, const uint2 *s_row,
                                            float *s_u, int q0) {
-    for (int i = threadIdx.x; i < bt.R; i += TPB) {
-        unsigned mask = s_row[i].x;
-        if (!mask) continue;
+    constexpr int NW = TPB / 32;
+    const int lane = threadIdx.x & 31;
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    for (int i = threadIdx.x >> 5; i < bt.R; i += NW) {
+        const uint2 rw = s_row[i];
+        if (!rw.x) continue;
         const CS &cs = s_cs[upper_index(s_cs, bt.nb, i, false)];
         const int sc = cs.scene;
         const int nx = prm.dims[3 * sc], ny = prm.dims[3 * sc + 1], nz = prm.dims[3 * sc + 2];
@@ -598,28 +616,273 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
         const int row = li / cs.W, wx = li - row * cs.W;
         const int ry = row % cs.By, rz = row / cs.By;
         const int gy = wrapi(cs.y0 + ry, ny), gz = wrapi(cs.z0 + rz, nz);
-        const long long rowbase = ((long long)gz * ny + gy) * nx;
+        if (!(rw.x & (1u << lane))) continue;
+        const long long g = ((long long)gz * ny + gy) * nx + wrapi(cs.x0 + 32 * wx + lane, nx);
+        const int slot = (int)rw.y + __popc(rw.x & lanemask_lt);
         float *u = prm.uf[sc];
         float *f = prm.ff ? prm.ff[sc] : nullptr;
-        int slot = (int)s_row[i].y;
-        while (mask) {
-            const int bit = __ffs(mask) - 1;
-            mask &= mask - 1u;
-            const long long g = rowbase + wrapi(cs.x0 + 32 * wx + bit, nx);
 #pragma unroll
-            for (int q = 0; q < NC; ++q) {
-                const long long gq = (long long)(q0 + q) * ncell + g;
-                if (LOAD) {
-                    cp_async4(s_u + q * bt.C + slot, u + gq);
-                } else {
-                    if (f) f[gq] = (s_u[q * bt.C + slot] - u[gq]) * prm.finv;
-                    u[gq] = s_u[q * bt.C + slot];
-                }
+        for (int q = 0; q < NC; ++q) {
+            const long long gq = (long long)(q0 + q) * ncell + g;
+            if (LOAD) {
+                cp_async4(s_u + q * bt.C + slot, u + gq);
+            } else {
+                if (f) f[gq] = (s_u[q * bt.C + slot] - u[gq]) * prm.finv;
+                u[gq] = s_u[q * bt.C + slot];
             }
-            ++slot;
         }
     }
     if (LOAD) cp_async_wait_all();
+}
+
+// Marks the 3x3x3 stencil of a marker (box-relative base cell b) in its
+// cluster's row bitmask; false if the stencil leaves the box (never expected:
+// the box bounds every stencil of the cluster).
+__device__ __forceinline__ bool mark_stencil(uint2 *rt, const CS &cs, const int b[3]) {
+    if (b[0] < 1 || b[0] > cs.Bx - 2 || b[1] < 1 || b[1] > cs.By - 2 || b[2] < 1 || b[2] > cs.Bz - 2) return false;
+    const int x = b[0] - 1, wx = x >> 5, bit = x & 31;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int row = (b[2] + dz) * cs.By + (b[1] + dy);
+            atomicOr(&rt[row * cs.W + wx].x, 7u << bit);
+            if (bit > 29) atomicOr(&rt[row * cs.W + wx + 1].x, 7u >> (32 - bit));
+        }
+    return true;
+}
+
+__device__ __forceinline__ int unpack_slot(const unsigned (&sp)[5], int i) {
+    return i == 8 ? (int)sp[4] : (int)((sp[i >> 1] >> ((i & 1) * 16)) & 0xffffu);
+}
+
+// Fixed-point scale of every cluster of the batch (deterministic mode): 2^k
+// with (max|u| + 64 Dmax max|e|) 2^k < 2^30, so that every cell value and every
+// partial sum of spread contributions fits in int32; then u -> int.  The
+// per-cluster slot ranges start at multiples of 4 and their padding is zero,
+// so the passes use 16-byte accesses.
+template <int TPB, int NC>
+__device__ __forceinline__ void det_to_fixed(const Batch &bt, CS *s_cs, float *s_u) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int C = bt.C;
+    for (int j = 0; j < bt.nb; ++j) {
+        const int n4 = (s_cs[j].ncell + 3) >> 2;
+        float um = 0.f;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            const float4 *p = reinterpret_cast<const float4 *>(s_u + q * C + s_cs[j].slot0);
+            for (int i = tid; i < n4; i += TPB) {
+                const float4 v = p[i];
+                um = fmaxf(um, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            }
+        }
+        um = warp_max(um);
+        if (lane == 0 && um > 0.f) atomicMax(&s_cs[j].umax, __float_as_uint(um));
+    }
+    __syncthreads();
+    for (int j = tid; j < bt.nb; j += TPB) {
+        const float range = __uint_as_float(s_cs[j].umax) + 64.f * s_cs[j].dmax * __uint_as_float(s_cs[j].emax);
+        int ex = 100;
+        if (range > 0.f) ex = min(100, max(-100, 29 - (int)ceilf(log2f(range))));
+        s_cs[j].S = ldexpf(1.f, ex);
+        s_cs[j].invS = ldexpf(1.f, -ex);
+    }
+    __syncthreads();
+    for (int j = 0; j < bt.nb; ++j) {
+        const int n4 = (s_cs[j].ncell + 3) >> 2;
+        const float S = s_cs[j].S;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            float4 *p = reinterpret_cast<float4 *>(s_u + q * C + s_cs[j].slot0);
+            for (int i = tid; i < n4; i += TPB) {
+                const float4 v = p[i];
+                int4 r;
+                r.x = __float2int_rn(v.x * S); r.y = __float2int_rn(v.y * S);
+                r.z = __float2int_rn(v.z * S); r.w = __float2int_rn(v.w * S);
+                reinterpret_cast<int4 *>(p)[i] = r;
+            }
+        }
+    }
+}
+
+template <int TPB, int NC>
+__device__ __forceinline__ void det_from_fixed(const Batch &bt, const CS *s_cs, float *s_u) {
+    const int tid = threadIdx.x;
+    const int C = bt.C;
+    for (int j = 0; j < bt.nb; ++j) {
+        const int n4 = (s_cs[j].ncell + 3) >> 2;
+        const float invS = s_cs[j].invS;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            float4 *p = reinterpret_cast<float4 *>(s_u + q * C + s_cs[j].slot0);
+            for (int i = tid; i < n4; i += TPB) {
+                const int4 r = reinterpret_cast<const int4 *>(p)[i];
+                p[i] = make_float4((float)r.x * invS, (float)r.y * invS, (float)r.z * invS, (float)r.w * invS);
+            }
+        }
+    }
+}
+
+// Zero the padding slots of every cluster (components 0..NC-1).
+template <int TPB, int NC>
+__device__ __forceinline__ void zero_padding(const Batch &bt, const CS *s_cs, float *s_u) {
+    for (int j = threadIdx.x; j < bt.nb; j += TPB) {
+        const int s0 = s_cs[j].slot0 + s_cs[j].ncell, s1 = s_cs[j].slot0 + ((s_cs[j].ncell + 3) & ~3);
+        for (int q = 0; q < NC; ++q)
+            for (int i = s0; i < s1; ++i) s_u[q * bt.C + i] = 0.f;
+    }
+}
+
+// The outer forcing loop of a batch of at most TPB*KC markers with each
+// thread's markers (weights, packed row slots, U^d, the summed slip) held in
+// registers for the whole step.
+template <int TPB, int KC, bool DET>
+__device__ __forceinline__ void forcing_cached(const KParams &prm, const Batch &bt, const PS *s_ps, CS *s_cs,
+                                               float *s_part, const unsigned char *s_chunk, const uint2 *s_row,
+                                               float *s_u, unsigned cvalid, const int (&cb)[KC][3],
+                                               const float (&cf)[KC][3]) {
+    int *s_ui = reinterpret_cast<int *>(s_u);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int C = bt.C, nm = bt.nm;
+    unsigned sp[KC][5];
+    float *s_E = s_u + 3 * C;   // per-marker sum of e over the iterations, [nm][3]
+    for (int i = tid; i < 3 * nm; i += TPB) s_E[i] = 0.f;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) sp[k][i] = 0u;
+        if (cvalid & (1u << k)) {
+            const int m = tid + k * TPB;
+            const PS &s = s_ps[s_chunk[m >> 5]];
+            const CS &cs = s_cs[s.cl];
+            int sl[9];
+            row_slots(s_row + cs.row0, cs.W, cs.By, cb[k], sl);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) sp[k][i] = (unsigned)sl[2 * i] | ((unsigned)sl[2 * i + 1] << 16);
+            sp[k][4] = (unsigned)sl[8];
+        }
+    }
+    move_cells<TPB, 3, true>(prm, bt, s_cs, s_row, s_u, 0);
+    __syncthreads();
+    zero_padding<TPB, 3>(bt, s_cs, s_u);
+    __syncthreads();
+    for (int iter = 0; iter < prm.n_forcing; ++iter) {
+        float e[KC][3];
+        if (DET) {
+            for (int j = tid; j < bt.nb; j += TPB) { s_cs[j].umax = 0u; s_cs[j].emax = 0u; }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            float em = 0.f;
+            e[k][0] = e[k][1] = e[k][2] = 0.f;
+            if (cvalid & (1u << k)) {
+                float w[3][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) phi3_weights(cf[k][c], w[c]);
+                float U0 = 0.f, U1 = 0.f, U2 = 0.f;
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz) {
+                    // keep one z-plane of loads in flight (register budget of the cached path)
+                    asm volatile("" ::: "memory");
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const int sl = unpack_slot(sp[k], dz * 3 + dy);
+                        const float wyz = w[2][dz] * w[1][dy];
+                        const float a0 = wyz * w[0][0], a1 = wyz * w[0][1], a2 = wyz * w[0][2];
+                        U0 += a0 * s_u[sl] + a1 * s_u[sl + 1] + a2 * s_u[sl + 2];
+                        U1 += a0 * s_u[C + sl] + a1 * s_u[C + sl + 1] + a2 * s_u[C + sl + 2];
+                        U2 += a0 * s_u[2 * C + sl] + a1 * s_u[2 * C + sl + 1] + a2 * s_u[2 * C + sl + 2];
+                    }
+                }
+                // desired velocity U^d = u_p + w_p x r_l (Sec. 2.1), from the particle record
+                const int m = tid + k * TPB;
+                const PS &s = s_ps[s_chunk[m >> 5]];
+                const float *t = prm.t32 + 3ll * (s.P.toff + (m - s.mstart));
+                const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
+                e[k][0] = s.P.ud[0] + (s.P.om[1] * r2 - s.P.om[2] * r1) - U0;
+                e[k][1] = s.P.ud[1] + (s.P.om[2] * r0 - s.P.om[0] * r2) - U1;
+                e[k][2] = s.P.ud[2] + (s.P.om[0] * r1 - s.P.om[1] * r0) - U2;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) s_E[3 * m + q] += e[k][q];
+                em = fmaxf(fabsf(e[k][0]), fmaxf(fabsf(e[k][1]), fabsf(e[k][2])));
+            }
+            if (DET && (tid - lane) + k * TPB < nm) {
+                const float wm = warp_max(em);
+                if (lane == 0)
+                    atomicMax(&s_cs[s_ps[s_chunk[(tid + k * TPB) >> 5]].cl].emax, __float_as_uint(wm));
+            }
+        }
+        if (DET) {
+            __syncthreads();
+            det_to_fixed<TPB, 3>(bt, s_cs, s_u);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            if (cvalid & (1u << k)) {
+                const int m = tid + k * TPB;
+                const PS &s = s_ps[s_chunk[m >> 5]];
+                const float D = s.P.D * (DET ? s_cs[s.cl].S : 1.f);
+                const float g0 = e[k][0] * D, g1 = e[k][1] * D, g2 = e[k][2] * D;
+                float w[3][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) phi3_weights(cf[k][c], w[c]);
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz) {
+                    asm volatile("" ::: "memory");   // one z-plane of atomics at a time
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const int sl = unpack_slot(sp[k], dz * 3 + dy);
+                        const float wyz = w[2][dz] * w[1][dy];
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const float a = wyz * w[0][dx];
+                            if (DET) {
+                                atomicAdd(&s_ui[sl + dx], __float2int_rn(a * g0));
+                                atomicAdd(&s_ui[C + sl + dx], __float2int_rn(a * g1));
+                                atomicAdd(&s_ui[2 * C + sl + dx], __float2int_rn(a * g2));
+                            } else {
+                                atomicAdd(&s_u[sl + dx], a * g0);
+                                atomicAdd(&s_u[C + sl + dx], a * g1);
+                                atomicAdd(&s_u[2 * C + sl + dx], a * g2);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (DET) {
+            det_from_fixed<TPB, 3>(bt, s_cs, s_u);
+            __syncthreads();
+        }
+    }
+    // particle loads once per step: sum_m e^m = E per marker, warp sums of E D
+    // and r x E D per 32-marker chunk (one particle per chunk)
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int m = tid + k * TPB;
+        if ((tid - lane) + k * TPB < nm) {
+            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (cvalid & (1u << k)) {
+                const PS &s = s_ps[s_chunk[m >> 5]];
+                const float *t = prm.t32 + 3ll * (s.P.toff + (m - s.mstart));
+                const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
+                const float D = s.P.D;
+                v[0] = s_E[3 * m] * D; v[1] = s_E[3 * m + 1] * D; v[2] = s_E[3 * m + 2] * D;
+                v[3] = r1 * v[2] - r2 * v[1];
+                v[4] = r2 * v[0] - r0 * v[2];
+                v[5] = r0 * v[1] - r1 * v[0];
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float x = warp_sum(v[q]);
+                if (lane == 0) s_part[(m >> 5) * 6 + q] = x;
+            }
+        }
+    }
+    move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_u, 0);
 }
 
 // The outer forcing loop (Sec. 2.2.2) for components q0..q0+NC-1 of a batch,
@@ -630,7 +893,8 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
 // per-particle load sums are plain warp sums.
 template <int TPB, int KM, bool DET, int NC>
 __device__ __forceinline__ void forcing_loop(const KParams &prm, const Batch &bt, const PS *s_ps, CS *s_cs,
-                                             float *s_part, const uint2 *s_row, float *s_u, int q0) {
+                                             float *s_part, const unsigned char *s_chunk, const uint2 *s_row,
+                                             float *s_u, int q0) {
     constexpr int KK = KM / NC;   // marker slots per thread in this pass
     int *s_ui = reinterpret_cast<int *>(s_u);
     const int tid = threadIdx.x, lane = tid & 31;
@@ -649,7 +913,7 @@ __device__ __forceinline__ void forcing_loop(const KParams &prm, const Batch &bt
 #pragma unroll
             for (int q = 0; q < NC; ++q) ereg[k][q] = 0.f;
             if (m < nm) {
-                pi = locate(s_ps, np, m);
+                pi = s_chunk[m >> 5];
                 const PS &s = s_ps[pi];
                 const int l = m - s.mstart;
                 if (l < s.P.nl) {
@@ -719,38 +983,15 @@ __device__ __forceinline__ void forcing_loop(const KParams &prm, const Batch &bt
             }
         }
         if (DET) {
-            // per cluster: fixed-point scale 2^k with (max|u| + 64 Dmax max|e|) 2^k < 2^30,
-            // so every cell value and every partial sum of spread contributions fits in int32
-            for (int j = 0; j < bt.nb; ++j) {
-                const int s0 = s_cs[j].slot0, s1 = (j + 1 < bt.nb) ? s_cs[j + 1].slot0 : C;
-                float um = 0.f;
-                for (int q = 0; q < NC; ++q)
-                    for (int i = s0 + tid; i < s1; i += TPB) um = fmaxf(um, fabsf(s_u[q * C + i]));
-                um = warp_max(um);
-                if (lane == 0 && um > 0.f) atomicMax(&s_cs[j].umax, __float_as_uint(um));
-            }
             __syncthreads();
-            for (int j = tid; j < bt.nb; j += TPB) {
-                const float range = __uint_as_float(s_cs[j].umax) + 64.f * s_cs[j].dmax * __uint_as_float(s_cs[j].emax);
-                int ex = 100;
-                if (range > 0.f) ex = min(100, max(-100, 29 - (int)ceilf(log2f(range))));
-                s_cs[j].S = ldexpf(1.f, ex);
-                s_cs[j].invS = ldexpf(1.f, -ex);
-            }
-            __syncthreads();
-            for (int j = 0; j < bt.nb; ++j) {
-                const int s0 = s_cs[j].slot0, s1 = (j + 1 < bt.nb) ? s_cs[j + 1].slot0 : C;
-                const float S = s_cs[j].S;
-                for (int q = 0; q < NC; ++q)
-                    for (int i = s0 + tid; i < s1; i += TPB) s_ui[q * C + i] = __float2int_rn(s_u[q * C + i] * S);
-            }
+            det_to_fixed<TPB, NC>(bt, s_cs, s_u);
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < KK; ++k) {
             const int m = tid + k * TPB;
             if (m < nm) {
-                const int pi = locate(s_ps, np, m);
+                const int pi = s_chunk[m >> 5];
                 const PS &s = s_ps[pi];
                 const int l = m - s.mstart;
                 if (l < s.P.nl) {
@@ -785,20 +1026,17 @@ __device__ __forceinline__ void forcing_loop(const KParams &prm, const Batch &bt
         }
         __syncthreads();
         if (DET) {
-            for (int j = 0; j < bt.nb; ++j) {
-                const int s0 = s_cs[j].slot0, s1 = (j + 1 < bt.nb) ? s_cs[j + 1].slot0 : C;
-                const float invS = s_cs[j].invS;
-                for (int q = 0; q < NC; ++q)
-                    for (int i = s0 + tid; i < s1; i += TPB) s_u[q * C + i] = (float)s_ui[q * C + i] * invS;
-            }
+            det_from_fixed<TPB, NC>(bt, s_cs, s_u);
             __syncthreads();
         }
     }
 }
 
-// One persistent CTA per SM.  DET = fixed-point spreading (int32 shared-memory
-// atomics, bit-reproducible and independent of how clusters are batched).
-template <int TPB, int KM, bool DET>
+// One persistent CTA per SM.  KM: marker slots per thread of the general path;
+// KC: markers per thread held in registers by the cached path.  DET =
+// fixed-point spreading (int32 shared-memory atomics, bit-reproducible and
+// independent of how clusters are batched).
+template <int TPB, int KM, int KC, bool DET>
 __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
     constexpr int NCH = TPB * KM / 32;   // 32-marker chunks
     extern __shared__ __align__(16) unsigned char smem[];
@@ -806,7 +1044,8 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
     CS *s_cs = reinterpret_cast<CS *>(s_ps + kCapP);
     double *s_acc = reinterpret_cast<double *>(s_cs + kCapCl);           // [kCapP][6]
     float *s_part = reinterpret_cast<float *>(s_acc + 6 * kCapP);        // [NCH][6]
-    uint2 *s_row = reinterpret_cast<uint2 *>(s_part + NCH * 6);          // [R] then the cells
+    unsigned char *s_chunk = reinterpret_cast<unsigned char *>(s_part + NCH * 6);   // [NCH] chunk -> particle
+    uint2 *s_row = reinterpret_cast<uint2 *>(smem + fixed_smem_bytes<TPB, KM>());   // [R] then the cells
     unsigned char *dyn_end = smem + prm.smem_bytes;
     __shared__ int s_w, s_np, s_nm, s_R, s_flag, s_scan[32], s_total;
     const int tid = threadIdx.x;
@@ -901,32 +1140,57 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
             bt.nm = s_nm;
             const int nm = bt.nm;
             for (int i = tid; i < (nm >> 5) * 6; i += TPB) s_part[i] = 0.f;
+            for (int i = tid; i < np; i += TPB)
+                for (int ch = s_ps[i].mstart >> 5; ch < (s_ps[i].mstart + s_ps[i].P.nl + 31) >> 5; ++ch)
+                    s_chunk[ch] = (unsigned char)i;
+            __syncthreads();
 
-            // 1. touched-cell bitmask of every cluster (bounds-checked)
-            for (int m = tid; m < nm; m += TPB) {
-                const int pi = locate(s_ps, np, m);
-                const PS &s = s_ps[pi];
-                const int l = m - s.mstart;
-                if (l >= s.P.nl) continue;
-                const CS &cs = s_cs[s.cl];
-                int b[3];
-                float wt[3][3];
-                rel_stencil(s, prm.t32, prm.t64, l, b, wt);
-                if (b[0] < 1 || b[0] > cs.Bx - 2 || b[1] < 1 || b[1] > cs.By - 2 || b[2] < 1 || b[2] > cs.Bz - 2) {
-                    s_flag = 1;
-                    continue;
-                }
-                const int x = b[0] - 1, wx = x >> 5, bit = x & 31;
-                uint2 *rt = s_row + cs.row0;
-                for (int dz = -1; dz <= 1; ++dz)
-                    for (int dy = -1; dy <= 1; ++dy) {
-                        const int row = (b[2] + dz) * cs.By + (b[1] + dy);
-                        atomicOr(&rt[row * cs.W + wx].x, 7u << bit);
-                        if (bit > 29) atomicOr(&rt[row * cs.W + wx + 1].x, 7u >> (32 - bit));
+            // 1. touched-cell bitmask of every cluster (bounds-checked).  A batch of
+            // at most TPB*KC markers keeps each thread's markers' stencils in
+            // registers for the whole step (computed once instead of twice per
+            // iteration).
+            const bool cached = nm <= TPB * KC;
+            int cb[KC][3];          // box-relative base cells (until the slots are known)
+            float cf[KC][3];        // fractional marker positions (weights are recomputed)
+            unsigned cvalid = 0u;   // bit k: slot k holds a marker
+            if (cached) {
+#pragma unroll
+                for (int k = 0; k < KC; ++k) {
+                    const int m = tid + k * TPB;
+                    cb[k][0] = cb[k][1] = cb[k][2] = 0;
+                    cf[k][0] = cf[k][1] = cf[k][2] = 0.f;
+                    if (m < nm) {
+                        const PS &s = s_ps[s_chunk[m >> 5]];
+                        const int l = m - s.mstart;
+                        if (l < s.P.nl) {
+                            int b[3];
+                            rel_base(s, prm.t32, prm.t64, l, b, cf[k]);
+                            const CS &cs = s_cs[s.cl];
+                            if (mark_stencil(s_row + cs.row0, cs, b)) {
+                                cb[k][0] = b[0]; cb[k][1] = b[1]; cb[k][2] = b[2];
+                                cvalid |= 1u << k;
+                            } else {
+                                s_flag = 1;
+                            }
+                        }
                     }
+                }
+            } else {
+                for (int m = tid; m < nm; m += TPB) {
+                    const PS &s = s_ps[s_chunk[m >> 5]];
+                    const int l = m - s.mstart;
+                    if (l >= s.P.nl) continue;
+                    int b[3];
+                    float wt[3][3];
+                    rel_stencil(s, prm.t32, prm.t64, l, b, wt);
+                    const CS &cs = s_cs[s.cl];
+                    if (!mark_stencil(s_row + cs.row0, cs, b)) s_flag = 1;
+                }
             }
             __syncthreads();
-            // 2. compact slots: exclusive prefix of the popcounts over all rows
+            // 2. compact slots: exclusive prefix of the popcounts over all rows, then
+            // each cluster's slots shifted to start at a multiple of 4 (so that the
+            // per-cluster passes over the cells can use 16-byte accesses)
             {
                 const int per = (bt.R + TPB - 1) / TPB;
                 const int lo = min(bt.R, tid * per), hi = min(bt.R, lo + per);
@@ -938,11 +1202,37 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
                     s_row[i].y = (unsigned)run;
                     run += __popc(s_row[i].x);
                 }
-                if (tid == 0) s_total = total;
+                __syncthreads();
+                if (tid < 32) {
+                    // warp 0: per-cluster padded slot offsets
+                    int c0 = 0, cnt = 0;
+                    if (tid < bt.nb) {
+                        c0 = (int)s_row[s_cs[tid].row0].y;
+                        const int c1 = tid + 1 < bt.nb ? (int)s_row[s_cs[tid + 1].row0].y : total;
+                        cnt = c1 - c0;
+                    }
+                    const int padded = (cnt + 3) & ~3;
+                    int inc = padded;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int a1 = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (tid >= o) inc += a1;
+                    }
+                    if (tid < bt.nb) {
+                        s_cs[tid].slot0 = inc - padded;
+                        s_cs[tid].ncell = cnt;
+                        s_cs[tid].shift = (inc - padded) - c0;
+                    }
+                    if (tid == 31) s_total = inc;
+                }
+                __syncthreads();
+                for (int i = tid; i < bt.R; i += TPB) {
+                    if (!s_row[i].x) continue;
+                    s_row[i].y += (unsigned)s_cs[upper_index(s_cs, bt.nb, i, false)].shift;
+                }
             }
             __syncthreads();
             bt.C = s_total;
-            for (int j = tid; j < bt.nb; j += TPB) s_cs[j].slot0 = (int)s_row[s_cs[j].row0].y;
             float *s_u = reinterpret_cast<float *>(s_row + ((bt.R + 3) & ~3));
             const int cap_cells = (int)((dyn_end - reinterpret_cast<unsigned char *>(s_u)) / 4);
             const bool three = 3 * bt.C <= cap_cells && nm <= TPB * (KM / 3);
@@ -965,16 +1255,22 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
                 if (!three) atomicAdd(prm.cnt + C_ONECOMP, bt.nb);
             }
             __syncthreads();
-            if (three) {
+            if (cached && three && 3 * bt.C + 3 * nm <= cap_cells) {
+                forcing_cached<TPB, KC, DET>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_u, cvalid, cb, cf);
+            } else if (three) {
                 move_cells<TPB, 3, true>(prm, bt, s_cs, s_row, s_u, 0);
                 __syncthreads();
-                forcing_loop<TPB, KM, DET, 3>(prm, bt, s_ps, s_cs, s_part, s_row, s_u, 0);
+                zero_padding<TPB, 3>(bt, s_cs, s_u);
+                __syncthreads();
+                forcing_loop<TPB, KM, DET, 3>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_u, 0);
                 move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_u, 0);
             } else {
                 for (int q = 0; q < 3; ++q) {
                     move_cells<TPB, 1, true>(prm, bt, s_cs, s_row, s_u, q);
                     __syncthreads();
-                    forcing_loop<TPB, KM, DET, 1>(prm, bt, s_ps, s_cs, s_part, s_row, s_u, q);
+                    zero_padding<TPB, 1>(bt, s_cs, s_u);
+                    __syncthreads();
+                    forcing_loop<TPB, KM, DET, 1>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_u, q);
                     move_cells<TPB, 1, false>(prm, bt, s_cs, s_row, s_u, q);
                     __syncthreads();
                 }
@@ -1097,9 +1393,9 @@ static ibm_status cluster_alloc(ibm_ctx *ctx) {
     return IBM_OK;
 }
 
-template <int TPB, int KM, bool DET>
+template <int TPB, int KM, int KC, bool DET>
 static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams &prm) {
-    auto kern = k_cluster_forcing<TPB, KM, DET>;
+    auto kern = k_cluster_forcing<TPB, KM, KC, DET>;
     if (S->smem_bytes == 0 || S->tpb != TPB || S->det != (int)DET) {
         S->smem_bytes = max_dyn_smem() & ~15;
         S->cap_c = (S->smem_bytes - fixed_smem_bytes<TPB, KM>()) / 4;   // FP32 cell slots (all components)
@@ -1119,8 +1415,10 @@ static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams
     return ibm_cuda_check(ctx, cudaGetLastError(), "cluster kernel");
 }
 
-// markers per thread of the cluster kernel for a block size
-static int markers_per_thread(int tpb) { return tpb == 1024 ? 12 : (tpb == 512 ? 24 : 48); }
+// marker slots per thread of the cluster kernel's general path, and markers per
+// thread held in registers by its cached path, for a block size
+static int markers_per_thread(int tpb) { return tpb == 1024 ? 12 : (tpb == 512 ? 24 : (tpb == 448 ? 27 : 48)); }
+static int cached_per_thread(int tpb) { return tpb == 1024 ? 1 : (tpb == 512 ? 4 : (tpb == 448 ? 5 : 8)); }
 
 ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
     ibm_status st = ensure_field_ptrs(ctx, u_ptrs, f_out);
@@ -1130,10 +1428,10 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     ClusterScratch *S = reinterpret_cast<ClusterScratch *>(ctx->cl);
     const int n = ctx->n_p;
     cudaStream_t sm = ctx->stream;
-    const int tpb = ctx->cfg.threads_per_block ? ctx->cfg.threads_per_block : 1024;
+    const int tpb = ctx->cfg.threads_per_block ? ctx->cfg.threads_per_block : 512;
     const int cap_m = tpb * markers_per_thread(tpb);
     // row table may take at most half of the dynamic shared memory
-    const int max_rows = (max_dyn_smem() - fixed_smem_bytes<1024, 12>()) / 16;
+    const int max_rows = (max_dyn_smem() - fixed_smem_bytes<256, 48>()) / 16;
 
     CK(cudaMemsetAsync(S->cnt, 0, C_COUNT * sizeof(int), sm), "zero counters");
     CK(cudaMemsetAsync(S->bin_cnt, 0, (S->nbins + 1) * sizeof(int), sm), "zero bins");
@@ -1166,7 +1464,7 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     k_scan1<<<1, 1024, 0, sm>>>(S->nm_ord, S->cum, n, S->tot + 3);
     const long long max_windows = (ctx->n_markers + 32ll * n) / kWindow + 2;
     k_batch_plan<<<grid_for(max_windows, 128), 128, 0, sm>>>(S->cnt, S->cum, S->order, S->cl_np, S->cl_nm,
-                                                            S->cl_box, tpb * (markers_per_thread(tpb) / 3),
+                                                            S->cl_box, tpb * cached_per_thread(tpb),
                                                             max_rows, S->batches, S->cnt);
     ctx->launches += 16;
 
@@ -1197,11 +1495,17 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prof_begin(ctx);
     const bool det = ctx->cfg.spread_mode == IBM_SPREAD_DETERMINISTIC;
     if (tpb == 1024)
-        st = det ? launch_cluster_kernel<1024, 12, true>(ctx, S, prm) : launch_cluster_kernel<1024, 12, false>(ctx, S, prm);
+        st = det ? launch_cluster_kernel<1024, 12, 1, true>(ctx, S, prm)
+                 : launch_cluster_kernel<1024, 12, 1, false>(ctx, S, prm);
     else if (tpb == 512)
-        st = det ? launch_cluster_kernel<512, 24, true>(ctx, S, prm) : launch_cluster_kernel<512, 24, false>(ctx, S, prm);
+        st = det ? launch_cluster_kernel<512, 24, 4, true>(ctx, S, prm)
+                 : launch_cluster_kernel<512, 24, 4, false>(ctx, S, prm);
+    else if (tpb == 448)
+        st = det ? launch_cluster_kernel<448, 27, 5, true>(ctx, S, prm)
+                 : launch_cluster_kernel<448, 27, 5, false>(ctx, S, prm);
     else
-        st = det ? launch_cluster_kernel<256, 48, true>(ctx, S, prm) : launch_cluster_kernel<256, 48, false>(ctx, S, prm);
+        st = det ? launch_cluster_kernel<256, 48, 8, true>(ctx, S, prm)
+                 : launch_cluster_kernel<256, 48, 8, false>(ctx, S, prm);
     prof_end(ctx);
     if (st != IBM_OK) return st;
     ctx->launches += 1;
