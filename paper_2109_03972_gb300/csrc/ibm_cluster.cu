@@ -340,6 +340,9 @@ __global__ void k_cluster_route(const long long *n_clust_d, const PInfo *P, cons
             R *= (k == 0) ? (ext + 31) / 32 : ext;
         }
         ok = ok && R <= max_rows;
+        // bitmask entry decode words hold y, z < 1024 and 16 words (512 cells) per row
+        ok = ok && (cl_box[12 * c + 4] - cl_box[12 * c + 1]) < 1023 && (cl_box[12 * c + 5] - cl_box[12 * c + 2]) < 1023 &&
+             (cl_box[12 * c + 3] - cl_box[12 * c]) < 511;
         if (ok) {
             const int b = min(kBuckets - 1, nm / 8);
             cl_bkt[c] = kBuckets - 1 - b;   // larger clusters first
@@ -595,40 +598,43 @@ struct Batch {
     int nb, np, nm, R, C;
 };
 
+// Per (row, 32-cell word) entry of a cluster's bitmask: cluster (5 bits), word
+// within the row (4), row y (10) and row z (10) in the cluster's box.
+__device__ __forceinline__ unsigned pack_dec(int j, int wx, int ry, int rz) {
+    return (unsigned)j | ((unsigned)wx << 5) | ((unsigned)ry << 9) | ((unsigned)rz << 19);
+}
+
 // Gather (LOAD) or write back the touched cells of components q0..q0+NC-1 of
-// every cluster of the batch: one warp per (row, 32-cell word) of a cluster's
-// bitmask, one lane per cell, so the accesses of a row run are coalesced.
-// Slots of one x-row run are consecutive.
+// every cluster of the batch, one thread per cell slot: consecutive threads
+// take consecutive slots, i.e. consecutive cells of a row run, so the global
+// accesses coalesce.  s_inv maps a slot to its bitmask entry (0xffff for the
+// padding slots), s_dec gives the entry's place in its cluster's box.
 template <int TPB, int NC, bool LOAD>
 __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, const CS *s_cs, const uint2 *s_row,
-                                           float *s_u, int q0) {
-    constexpr int NW = TPB / 32;
-    const int lane = threadIdx.x & 31;
-    const unsigned lanemask_lt = (1u << lane) - 1u;
-    for (int i = threadIdx.x >> 5; i < bt.R; i += NW) {
+                                           const unsigned *s_dec, const unsigned short *s_inv, float *s_u, int q0) {
+    for (int sl = threadIdx.x; sl < bt.C; sl += TPB) {
+        const unsigned i = s_inv[sl];
+        if (i == 0xffffu) continue;
         const uint2 rw = s_row[i];
-        if (!rw.x) continue;
-        const CS &cs = s_cs[upper_index(s_cs, bt.nb, i, false)];
+        const unsigned d = s_dec[i];
+        const CS &cs = s_cs[d & 31u];
+        const int wx = (d >> 5) & 15u, ry = (d >> 9) & 1023u, rz = d >> 19;
+        const int bit = (int)__fns(rw.x, 0u, sl - (int)rw.y + 1);
         const int sc = cs.scene;
         const int nx = prm.dims[3 * sc], ny = prm.dims[3 * sc + 1], nz = prm.dims[3 * sc + 2];
         const long long ncell = (long long)nx * ny * nz;
-        const int li = i - cs.row0;
-        const int row = li / cs.W, wx = li - row * cs.W;
-        const int ry = row % cs.By, rz = row / cs.By;
-        const int gy = wrapi(cs.y0 + ry, ny), gz = wrapi(cs.z0 + rz, nz);
-        if (!(rw.x & (1u << lane))) continue;
-        const long long g = ((long long)gz * ny + gy) * nx + wrapi(cs.x0 + 32 * wx + lane, nx);
-        const int slot = (int)rw.y + __popc(rw.x & lanemask_lt);
+        const long long g = ((long long)wrapi(cs.z0 + rz, nz) * ny + wrapi(cs.y0 + ry, ny)) * nx +
+                            wrapi(cs.x0 + 32 * wx + bit, nx);
         float *u = prm.uf[sc];
         float *f = prm.ff ? prm.ff[sc] : nullptr;
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
             const long long gq = (long long)(q0 + q) * ncell + g;
             if (LOAD) {
-                cp_async4(s_u + q * bt.C + slot, u + gq);
+                cp_async4(s_u + q * bt.C + sl, u + gq);
             } else {
-                if (f) f[gq] = (s_u[q * bt.C + slot] - u[gq]) * prm.finv;
-                u[gq] = s_u[q * bt.C + slot];
+                if (f) f[gq] = (s_u[q * bt.C + sl] - u[gq]) * prm.finv;
+                u[gq] = s_u[q * bt.C + sl];
             }
         }
     }
@@ -739,6 +745,7 @@ __device__ __forceinline__ void zero_padding(const Batch &bt, const CS *s_cs, fl
 template <int TPB, int KC, bool DET>
 __device__ __forceinline__ void forcing_cached(const KParams &prm, const Batch &bt, const PS *s_ps, CS *s_cs,
                                                float *s_part, const unsigned char *s_chunk, const uint2 *s_row,
+                                               const unsigned *s_dec, const unsigned short *s_inv,
                                                float *s_u, unsigned cvalid, const int (&cb)[KC][3],
                                                const float (&cf)[KC][3]) {
     int *s_ui = reinterpret_cast<int *>(s_u);
@@ -762,7 +769,7 @@ __device__ __forceinline__ void forcing_cached(const KParams &prm, const Batch &
             sp[k][4] = (unsigned)sl[8];
         }
     }
-    move_cells<TPB, 3, true>(prm, bt, s_cs, s_row, s_u, 0);
+    move_cells<TPB, 3, true>(prm, bt, s_cs, s_row, s_dec, s_inv, s_u, 0);
     __syncthreads();
     zero_padding<TPB, 3>(bt, s_cs, s_u);
     __syncthreads();
@@ -882,7 +889,7 @@ __device__ __forceinline__ void forcing_cached(const KParams &prm, const Batch &
             }
         }
     }
-    move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_u, 0);
+    move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_dec, s_inv, s_u, 0);
 }
 
 // The outer forcing loop (Sec. 2.2.2) for components q0..q0+NC-1 of a batch,
@@ -1124,7 +1131,15 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
                 s_ps[tid].off[1] = prm.poff[3 * p + 1] - cs.y0;
                 s_ps[tid].off[2] = prm.poff[3 * p + 2] - cs.z0;
             }
-            for (int i = tid; i < bt.R; i += TPB) s_row[i].x = 0u;
+            unsigned *s_dec = reinterpret_cast<unsigned *>(s_row + bt.R);
+            for (int i = tid; i < bt.R; i += TPB) {
+                s_row[i].x = 0u;
+                const int j = upper_index(s_cs, bt.nb, i, false);
+                const CS &cs = s_cs[j];
+                const int li = i - cs.row0;
+                const int row = li / cs.W, wx = li - row * cs.W;
+                s_dec[i] = pack_dec(j, wx, row % cs.By, row / cs.By);
+            }
             __syncthreads();
             if (tid == 0) {
                 int m = 0;
@@ -1233,7 +1248,22 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
             }
             __syncthreads();
             bt.C = s_total;
-            float *s_u = reinterpret_cast<float *>(s_row + ((bt.R + 3) & ~3));
+            unsigned short *s_inv = reinterpret_cast<unsigned short *>(s_dec + bt.R);
+            float *s_u = reinterpret_cast<float *>(
+                (reinterpret_cast<uintptr_t>(s_inv) + 2 * (uintptr_t)bt.C + 15) & ~(uintptr_t)15);
+            if (reinterpret_cast<unsigned char *>(s_u) <= dyn_end) {
+                for (int i = tid; i < bt.C; i += TPB) s_inv[i] = 0xffffu;
+                __syncthreads();
+                for (int i = tid; i < bt.R; i += TPB) {
+                    unsigned mask = s_row[i].x;
+                    int sl = (int)s_row[i].y;
+                    while (mask) {
+                        mask &= mask - 1u;
+                        s_inv[sl++] = (unsigned short)i;
+                    }
+                }
+            }
+            __syncthreads();
             const int cap_cells = (int)((dyn_end - reinterpret_cast<unsigned char *>(s_u)) / 4);
             const bool three = 3 * bt.C <= cap_cells && nm <= TPB * (KM / 3);
             if (s_flag || bt.C > cap_cells || nm > TPB * KM) {
@@ -1250,28 +1280,30 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
                 continue;
             }
             if (tid == 0) {
-                atomicMax(prm.cnt + C_MAXCELLS, bt.C);
-                atomicAdd(prm.cnt + C_TOUCHED, bt.C);
+                int touched = 0;
+                for (int j = 0; j < bt.nb; ++j) touched += s_cs[j].ncell;
+                atomicMax(prm.cnt + C_MAXCELLS, touched);
+                atomicAdd(prm.cnt + C_TOUCHED, touched);
                 if (!three) atomicAdd(prm.cnt + C_ONECOMP, bt.nb);
             }
             __syncthreads();
             if (cached && three && 3 * bt.C + 3 * nm <= cap_cells) {
-                forcing_cached<TPB, KC, DET>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_u, cvalid, cb, cf);
+                forcing_cached<TPB, KC, DET>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_dec, s_inv, s_u, cvalid, cb, cf);
             } else if (three) {
-                move_cells<TPB, 3, true>(prm, bt, s_cs, s_row, s_u, 0);
+                move_cells<TPB, 3, true>(prm, bt, s_cs, s_row, s_dec, s_inv, s_u, 0);
                 __syncthreads();
                 zero_padding<TPB, 3>(bt, s_cs, s_u);
                 __syncthreads();
                 forcing_loop<TPB, KM, DET, 3>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_u, 0);
-                move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_u, 0);
+                move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_dec, s_inv, s_u, 0);
             } else {
                 for (int q = 0; q < 3; ++q) {
-                    move_cells<TPB, 1, true>(prm, bt, s_cs, s_row, s_u, q);
+                    move_cells<TPB, 1, true>(prm, bt, s_cs, s_row, s_dec, s_inv, s_u, q);
                     __syncthreads();
                     zero_padding<TPB, 1>(bt, s_cs, s_u);
                     __syncthreads();
                     forcing_loop<TPB, KM, DET, 1>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_u, q);
-                    move_cells<TPB, 1, false>(prm, bt, s_cs, s_row, s_u, q);
+                    move_cells<TPB, 1, false>(prm, bt, s_cs, s_row, s_dec, s_inv, s_u, q);
                     __syncthreads();
                 }
             }
