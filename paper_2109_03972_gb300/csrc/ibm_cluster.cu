@@ -521,17 +521,6 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
     return pre;
 }
 
-// Particle of batch marker m (markers of particle i occupy [mstart_i, mstart_i + nl_i)).
-__device__ __forceinline__ int locate(const PS *ps, int np, int m) {
-    int lo = 0, hi = np - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (ps[mid].mstart <= m) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 // Largest j with key[j] <= v among n entries (key[0] <= v).
 __device__ __forceinline__ int upper_index(const CS *cs, int n, int v, bool by_slot) {
     int lo = 0, hi = n - 1;
@@ -607,6 +596,44 @@ struct Batch {
 template <int TPB, int NC, bool LOAD>
 __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, const CS *s_cs, const uint2 *s_row,
                                            const unsigned short *s_inv, float *s_u, int q0) {
+    if (!s_inv) {
+        // no slot table: one thread per bitmask entry, walking its set bits
+        for (int i = threadIdx.x; i < bt.R; i += TPB) {
+            unsigned mask = s_row[i].x;
+            if (!mask) continue;
+            const CS &cs = s_cs[upper_index(s_cs, bt.nb, i, false)];
+            const int li = i - cs.row0;
+            const int row = (int)(((float)li + 0.5f) * __frcp_rn((float)cs.W));
+            const int wx = li - row * cs.W;
+            const int rz = (int)(((float)row + 0.5f) * __frcp_rn((float)cs.By));
+            const int ry = row - rz * cs.By;
+            const int sc = cs.scene;
+            const int nx = prm.dims[3 * sc], ny = prm.dims[3 * sc + 1], nz = prm.dims[3 * sc + 2];
+            const long long ncell = (long long)nx * ny * nz;
+            const long long rowbase = ((long long)wrapi(cs.z0 + rz, nz) * ny + wrapi(cs.y0 + ry, ny)) * nx;
+            float *u = prm.uf[sc];
+            float *f = prm.ff ? prm.ff[sc] : nullptr;
+            int sl = (int)s_row[i].y;
+            while (mask) {
+                const int bit = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const long long g = rowbase + wrapi(cs.x0 + 32 * wx + bit, nx);
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    const long long gq = (long long)(q0 + q) * ncell + g;
+                    if (LOAD) {
+                        cp_async4(s_u + q * bt.C + sl, u + gq);
+                    } else {
+                        if (f) f[gq] = (s_u[q * bt.C + sl] - u[gq]) * prm.finv;
+                        u[gq] = s_u[q * bt.C + sl];
+                    }
+                }
+                ++sl;
+            }
+        }
+        if (LOAD) cp_async_wait_all();
+        return;
+    }
     for (int sl = threadIdx.x; sl < bt.C; sl += TPB) {
         const unsigned i = s_inv[sl];
         if (i == 0xffffu) continue;
@@ -738,13 +765,9 @@ __device__ __forceinline__ void zero_padding(const Batch &bt, const CS *s_cs, fl
     }
 }
 
-// The outer forcing loop of a batch of at most TPB*KC markers.  Each thread's
-// markers keep their fractional positions and packed row slots in registers
-// for the whole step (stencils are located once per step, not twice per
-// iteration).  The three velocity components are run one after the other
-// (they are independent in the loop: F = (U^d - W u)/tau and the spreading
-// act per component), so the batch holds one component of its touched cells
-// in shared memory at a time.
+// The outer forcing loop of a batch of at most TPB*KC markers with each
+// thread's markers (weights, packed row slots, U^d, the summed slip) held in
+// registers for the whole step.
 template <int TPB, int KC, bool DET>
 __device__ __forceinline__ void forcing_cached(const KParams &prm, const Batch &bt, const PS *s_ps, CS *s_cs,
                                                float *s_part, const unsigned char *s_chunk, const uint2 *s_row,
@@ -752,8 +775,10 @@ __device__ __forceinline__ void forcing_cached(const KParams &prm, const Batch &
                                                const float (&cf)[KC][3]) {
     int *s_ui = reinterpret_cast<int *>(s_u);
     const int tid = threadIdx.x, lane = tid & 31;
-    const int nm = bt.nm;
+    const int C = bt.C, nm = bt.nm;
     unsigned sp[KC][5];
+    float *s_E = s_u + 3 * C;   // per-marker sum of e over the iterations, [nm][3]
+    for (int i = tid; i < 3 * nm; i += TPB) s_E[i] = 0.f;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
 #pragma unroll
@@ -769,116 +794,127 @@ __device__ __forceinline__ void forcing_cached(const KParams &prm, const Batch &
             sp[k][4] = (unsigned)sl[8];
         }
     }
-    for (int q = 0; q < 3; ++q) {
-        move_cells<TPB, 1, true>(prm, bt, s_cs, s_row, s_inv, s_u, q);
-        __syncthreads();
-        zero_padding<TPB, 1>(bt, s_cs, s_u);
-        __syncthreads();
-        float Eq[KC];
-#pragma unroll
-        for (int k = 0; k < KC; ++k) Eq[k] = 0.f;
-        for (int iter = 0; iter < prm.n_forcing; ++iter) {
-            float e[KC];
-            if (DET) {
-                for (int j = tid; j < bt.nb; j += TPB) { s_cs[j].umax = 0u; s_cs[j].emax = 0u; }
-                __syncthreads();
-            }
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                float em = 0.f;
-                e[k] = 0.f;
-                if (cvalid & (1u << k)) {
-                    float w[3][3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) phi3_weights(cf[k][c], w[c]);
-                    float U = 0.f;
-#pragma unroll
-                    for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-                        for (int dy = 0; dy < 3; ++dy) {
-                            const int sl = unpack_slot(sp[k], dz * 3 + dy);
-                            const float wyz = w[2][dz] * w[1][dy];
-                            U += wyz * (w[0][0] * s_u[sl] + w[0][1] * s_u[sl + 1] + w[0][2] * s_u[sl + 2]);
-                        }
-                    // component q of the desired velocity U^d = u_p + w_p x r_l (Sec. 2.1)
-                    const int m = tid + k * TPB;
-                    const PS &s = s_ps[s_chunk[m >> 5]];
-                    const float *t = prm.t32 + 3ll * (s.P.toff + (m - s.mstart));
-                    const int qa = q == 2 ? 0 : q + 1, qb = q == 0 ? 2 : q - 1;   // (q, qa, qb) cyclic
-                    const float udq = s.P.ud[q] + s.P.rphys * (s.P.om[qa] * t[qb] - s.P.om[qb] * t[qa]);
-                    e[k] = udq - U;
-                    Eq[k] += e[k];
-                    em = fabsf(e[k]);
-                }
-                if (DET && (tid - lane) + k * TPB < nm) {
-                    const float wm = warp_max(em);
-                    if (lane == 0)
-                        atomicMax(&s_cs[s_ps[s_chunk[(tid + k * TPB) >> 5]].cl].emax, __float_as_uint(wm));
-                }
-            }
-            if (DET) {
-                __syncthreads();
-                det_to_fixed<TPB, 1>(bt, s_cs, s_u);
-            }
+    move_cells<TPB, 3, true>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
+    __syncthreads();
+    zero_padding<TPB, 3>(bt, s_cs, s_u);
+    __syncthreads();
+    for (int iter = 0; iter < prm.n_forcing; ++iter) {
+        float e[KC][3];
+        if (DET) {
+            for (int j = tid; j < bt.nb; j += TPB) { s_cs[j].umax = 0u; s_cs[j].emax = 0u; }
             __syncthreads();
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                if (cvalid & (1u << k)) {
-                    const int m = tid + k * TPB;
-                    const PS &s = s_ps[s_chunk[m >> 5]];
-                    const float g = e[k] * s.P.D * (DET ? s_cs[s.cl].S : 1.f);
-                    float w[3][3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) phi3_weights(cf[k][c], w[c]);
-#pragma unroll
-                    for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-                        for (int dy = 0; dy < 3; ++dy) {
-                            const int sl = unpack_slot(sp[k], dz * 3 + dy);
-                            const float gyz = w[2][dz] * w[1][dy] * g;
-#pragma unroll
-                            for (int dx = 0; dx < 3; ++dx) {
-                                if (DET) atomicAdd(&s_ui[sl + dx], __float2int_rn(w[0][dx] * gyz));
-                                else atomicAdd(&s_u[sl + dx], w[0][dx] * gyz);
-                            }
-                        }
-                }
-            }
-            __syncthreads();
-            if (DET) {
-                det_from_fixed<TPB, 1>(bt, s_cs, s_u);
-                __syncthreads();
-            }
         }
-        // particle loads of component q: force F_q = sum_m e_q D and its torque
-        // r x F, warp sums per 32-marker chunk (one particle per chunk)
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
-            const int m = tid + k * TPB;
-            if ((tid - lane) + k * TPB < nm) {
-                float f = 0.f, ta = 0.f, tb = 0.f;
-                if (cvalid & (1u << k)) {
-                    const PS &s = s_ps[s_chunk[m >> 5]];
-                    const float *t = prm.t32 + 3ll * (s.P.toff + (m - s.mstart));
-                    const int qa = q == 2 ? 0 : q + 1, qb = q == 0 ? 2 : q - 1;
-                    f = Eq[k] * s.P.D;
-                    // (r x F)_qa = r_qb F_q, (r x F)_qb = -r_qa F_q
-                    ta = s.P.rphys * t[qb] * f;
-                    tb = -s.P.rphys * t[qa] * f;
+            float em = 0.f;
+            e[k][0] = e[k][1] = e[k][2] = 0.f;
+            if (cvalid & (1u << k)) {
+                float w[3][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) phi3_weights(cf[k][c], w[c]);
+                float U0 = 0.f, U1 = 0.f, U2 = 0.f;
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz) {
+                    // keep one z-plane of loads in flight (register budget of the cached path)
+                    asm volatile("" ::: "memory");
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const int sl = unpack_slot(sp[k], dz * 3 + dy);
+                        const float wyz = w[2][dz] * w[1][dy];
+                        const float a0 = wyz * w[0][0], a1 = wyz * w[0][1], a2 = wyz * w[0][2];
+                        U0 += a0 * s_u[sl] + a1 * s_u[sl + 1] + a2 * s_u[sl + 2];
+                        U1 += a0 * s_u[C + sl] + a1 * s_u[C + sl + 1] + a2 * s_u[C + sl + 2];
+                        U2 += a0 * s_u[2 * C + sl] + a1 * s_u[2 * C + sl + 1] + a2 * s_u[2 * C + sl + 2];
+                    }
                 }
-                const float xf = warp_sum(f), xa = warp_sum(ta), xb = warp_sum(tb);
-                if (lane == 0) {
-                    const int qa = q == 2 ? 0 : q + 1, qb = q == 0 ? 2 : q - 1;
-                    float *pp = s_part + (m >> 5) * 6;
-                    pp[q] += xf;
-                    pp[3 + qa] += xa;
-                    pp[3 + qb] += xb;
+                // desired velocity U^d = u_p + w_p x r_l (Sec. 2.1), from the particle record
+                const int m = tid + k * TPB;
+                const PS &s = s_ps[s_chunk[m >> 5]];
+                const float *t = prm.t32 + 3ll * (s.P.toff + (m - s.mstart));
+                const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
+                e[k][0] = s.P.ud[0] + (s.P.om[1] * r2 - s.P.om[2] * r1) - U0;
+                e[k][1] = s.P.ud[1] + (s.P.om[2] * r0 - s.P.om[0] * r2) - U1;
+                e[k][2] = s.P.ud[2] + (s.P.om[0] * r1 - s.P.om[1] * r0) - U2;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) s_E[3 * m + q] += e[k][q];
+                em = fmaxf(fabsf(e[k][0]), fmaxf(fabsf(e[k][1]), fabsf(e[k][2])));
+            }
+            if (DET && (tid - lane) + k * TPB < nm) {
+                const float wm = warp_max(em);
+                if (lane == 0)
+                    atomicMax(&s_cs[s_ps[s_chunk[(tid + k * TPB) >> 5]].cl].emax, __float_as_uint(wm));
+            }
+        }
+        if (DET) {
+            __syncthreads();
+            det_to_fixed<TPB, 3>(bt, s_cs, s_u);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            if (cvalid & (1u << k)) {
+                const int m = tid + k * TPB;
+                const PS &s = s_ps[s_chunk[m >> 5]];
+                const float D = s.P.D * (DET ? s_cs[s.cl].S : 1.f);
+                const float g0 = e[k][0] * D, g1 = e[k][1] * D, g2 = e[k][2] * D;
+                float w[3][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) phi3_weights(cf[k][c], w[c]);
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz) {
+                    asm volatile("" ::: "memory");   // one z-plane of atomics at a time
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const int sl = unpack_slot(sp[k], dz * 3 + dy);
+                        const float wyz = w[2][dz] * w[1][dy];
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const float a = wyz * w[0][dx];
+                            if (DET) {
+                                atomicAdd(&s_ui[sl + dx], __float2int_rn(a * g0));
+                                atomicAdd(&s_ui[C + sl + dx], __float2int_rn(a * g1));
+                                atomicAdd(&s_ui[2 * C + sl + dx], __float2int_rn(a * g2));
+                            } else {
+                                atomicAdd(&s_u[sl + dx], a * g0);
+                                atomicAdd(&s_u[C + sl + dx], a * g1);
+                                atomicAdd(&s_u[2 * C + sl + dx], a * g2);
+                            }
+                        }
+                    }
                 }
             }
         }
-        move_cells<TPB, 1, false>(prm, bt, s_cs, s_row, s_inv, s_u, q);
         __syncthreads();
+        if (DET) {
+            det_from_fixed<TPB, 3>(bt, s_cs, s_u);
+            __syncthreads();
+        }
     }
+    // particle loads once per step: sum_m e^m = E per marker, warp sums of E D
+    // and r x E D per 32-marker chunk (one particle per chunk)
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int m = tid + k * TPB;
+        if ((tid - lane) + k * TPB < nm) {
+            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (cvalid & (1u << k)) {
+                const PS &s = s_ps[s_chunk[m >> 5]];
+                const float *t = prm.t32 + 3ll * (s.P.toff + (m - s.mstart));
+                const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
+                const float D = s.P.D;
+                v[0] = s_E[3 * m] * D; v[1] = s_E[3 * m + 1] * D; v[2] = s_E[3 * m + 2] * D;
+                v[3] = r1 * v[2] - r2 * v[1];
+                v[4] = r2 * v[0] - r0 * v[2];
+                v[5] = r0 * v[1] - r1 * v[0];
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float x = warp_sum(v[q]);
+                if (lane == 0) s_part[(m >> 5) * 6 + q] = x;
+            }
+        }
+    }
+    move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
 }
 
 // The outer forcing loop (Sec. 2.2.2) for components q0..q0+NC-1 of a batch,
@@ -894,7 +930,7 @@ __device__ __forceinline__ void forcing_loop(const KParams &prm, const Batch &bt
     constexpr int KK = KM / NC;   // marker slots per thread in this pass
     int *s_ui = reinterpret_cast<int *>(s_u);
     const int tid = threadIdx.x, lane = tid & 31;
-    const int C = bt.C, nm = bt.nm, np = bt.np;
+    const int C = bt.C, nm = bt.nm;
     for (int iter = 0; iter < prm.n_forcing; ++iter) {
         float ereg[KK][NC];
         if (DET)
@@ -1229,10 +1265,21 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
             }
             __syncthreads();
             bt.C = s_total;
+            // cells go right after the row table, or after a slot -> entry table when
+            // that fits too (it lets the gather/writeback run one thread per cell)
+            auto align16 = [](const void *q) {
+                return reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(q) + 15) & ~(uintptr_t)15);
+            };
+            float *const u_plain = align16(s_row + bt.R);
+            const int cap_cells = (int)((dyn_end - reinterpret_cast<unsigned char *>(u_plain)) / 4);
+            const bool three = 3 * bt.C <= cap_cells && nm <= TPB * (KM / 3);
+            const bool use_cached = cached && three && 3 * bt.C + 3 * nm <= cap_cells;
+            const int need = use_cached ? 3 * bt.C + 3 * nm : (three ? 3 * bt.C : bt.C);
             unsigned short *s_inv = reinterpret_cast<unsigned short *>(s_row + bt.R);
-            float *s_u = reinterpret_cast<float *>(
-                (reinterpret_cast<uintptr_t>(s_inv) + 2 * (uintptr_t)bt.C + 15) & ~(uintptr_t)15);
-            if (reinterpret_cast<unsigned char *>(s_u) <= dyn_end) {
+            float *const u_inv = align16(s_inv + bt.C);
+            const bool use_inv = (int)((dyn_end - reinterpret_cast<unsigned char *>(u_inv)) / 4) >= need;
+            float *s_u = use_inv ? u_inv : u_plain;
+            if (use_inv) {
                 for (int i = tid; i < bt.C; i += TPB) s_inv[i] = 0xffffu;
                 __syncthreads();
                 for (int i = tid; i < bt.R; i += TPB) {
@@ -1243,10 +1290,10 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
                         s_inv[sl++] = (unsigned short)i;
                     }
                 }
+            } else {
+                s_inv = nullptr;
             }
             __syncthreads();
-            const int cap_cells = (int)((dyn_end - reinterpret_cast<unsigned char *>(s_u)) / 4);
-            const bool three = 3 * bt.C <= cap_cells && nm <= TPB * (KM / 3);
             if (s_flag || bt.C > cap_cells || nm > TPB * KM) {
                 // does not fit even one component at a time: hand it to the plain path
                 if (tid == 0) {
@@ -1268,7 +1315,7 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
                 if (!three) atomicAdd(prm.cnt + C_ONECOMP, bt.nb);
             }
             __syncthreads();
-            if (cached && bt.C <= cap_cells) {
+            if (use_cached) {
                 forcing_cached<TPB, KC, DET>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_inv, s_u, cvalid, cb, cf);
             } else if (three) {
                 move_cells<TPB, 3, true>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
@@ -1431,7 +1478,7 @@ static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams
 // marker slots per thread of the cluster kernel's general path, and markers per
 // thread held in registers by its cached path, for a block size
 static int markers_per_thread(int tpb) { return tpb == 1024 ? 12 : (tpb == 512 ? 24 : 48); }
-static int cached_per_thread(int tpb) { return tpb == 1024 ? 1 : (tpb == 512 ? 6 : 8); }
+static int cached_per_thread(int tpb) { return tpb == 1024 ? 1 : (tpb == 512 ? 4 : 8); }
 
 ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
     ibm_status st = ensure_field_ptrs(ctx, u_ptrs, f_out);
@@ -1511,8 +1558,8 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
         st = det ? launch_cluster_kernel<1024, 12, 1, true>(ctx, S, prm)
                  : launch_cluster_kernel<1024, 12, 1, false>(ctx, S, prm);
     else if (tpb == 512)
-        st = det ? launch_cluster_kernel<512, 24, 6, true>(ctx, S, prm)
-                 : launch_cluster_kernel<512, 24, 6, false>(ctx, S, prm);
+        st = det ? launch_cluster_kernel<512, 24, 4, true>(ctx, S, prm)
+                 : launch_cluster_kernel<512, 24, 4, false>(ctx, S, prm);
     else
         st = det ? launch_cluster_kernel<256, 48, 8, true>(ctx, S, prm)
                  : launch_cluster_kernel<256, 48, 8, false>(ctx, S, prm);
