@@ -176,6 +176,34 @@ ibm_status ibm_step_stats(ibm_ctx *ctx, int64_t *stats);
  * reading.  Synchronises.  Errors: STATE (profile off), CUDA. */
 ibm_status ibm_kernel_timing(ibm_ctx *ctx, double *total_ms, int64_t *count, int reset);
 
+/* One FP64 forcing step that allocates nothing (no context, no cudaMalloc or
+ * cudaFree, no host allocation).  For callers that cannot allocate device
+ * memory: work being captured into or replayed from a CUDA graph, hosts that
+ * give the library a fixed memory budget up front, applications whose own
+ * allocator owns the device.  The paper has no counterpart; it is the plain
+ * FP64 form of ibm_forcing_step (one thread per marker, global atomics) for a
+ * single periodic nx*ny*nz grid, with the same results up to the order of
+ * floating-point additions.
+ * Inputs (DEVICE, double): x_p, u_p, omega_p [n_p][3], d_p [n_p].
+ * In/out (DEVICE, double): u [3][nz][ny][nx], updated in place.
+ * Outputs (DEVICE, double): F_out, T_out [n_p][3], the fluid-side loads summed
+ *   over the n_forcing iterations (as ibm_particle_loads).
+ * Scratch: one 16 MiB array inside the library that every GPU loading the
+ * library holds until exit.  Limits: n_p <= 65536 and at most 688,106 markers
+ * in total (N_l = round(pi (d_p/h)^2) per particle); larger inputs return
+ * IBM_ERR_CAPACITY and leave u unchanged.  Every call reuses the same array,
+ * so calls whose work overlaps on the GPU (other streams, other host threads
+ * on the same device) race and corrupt each other.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call outside any stream capture.  The call synchronises cuda_stream to read
+ * its error word.
+ * Errors: INVALID_ARG (bad sizes, NULL pointers, non-finite or oversized
+ * particles: d_p/h + 4 > smallest grid edge), CAPACITY, CUDA. */
+ibm_status ibm_forcing_step_static(int nx, int ny, int nz, double h, int n_forcing, double tau, int n_p,
+                                   const double *x_p, const double *u_p, const double *omega_p,
+                                   const double *d_p, double *u, double *F_out, double *T_out,
+                                   void *cuda_stream);
+
 /* Human-readable status name; never NULL. */
 const char *ibm_status_string(ibm_status s);
 
