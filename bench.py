@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bidisperse", choices=sorted(WORKLOAD_DESC))
-    ap.add_argument("--mode", default="cluster", choices=["cluster", "deterministic", "plain"])
+    ap.add_argument("--mode", default="deterministic", choices=["cluster", "deterministic", "plain"])
     ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = default)")
     ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
     ap.add_argument("--e2e-steps", type=int, default=5)

@@ -1488,7 +1488,7 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     ClusterScratch *S = reinterpret_cast<ClusterScratch *>(ctx->cl);
     const int n = ctx->n_p;
     cudaStream_t sm = ctx->stream;
-    const int tpb = ctx->cfg.threads_per_block ? ctx->cfg.threads_per_block : 512;
+    const int tpb = ctx->cfg.threads_per_block ? ctx->cfg.threads_per_block : 1024;
     const int cap_m = tpb * markers_per_thread(tpb);
     // row table may take at most half of the dynamic shared memory
     const int max_rows = (max_dyn_smem() - fixed_smem_bytes<256, 48>()) / 16;
