@@ -385,21 +385,21 @@ __device__ __forceinline__ int lower_bound_int(const int *a, int n, int v) {
 }
 
 constexpr int kCapCl = 32;      // clusters per batch
-constexpr int kWindow = 1024;   // markers per packing window
 
 // Work items of the shared-memory kernel.  The padded marker prefix of the
-// size-ordered cluster list is cut into windows of kWindow markers; the
+// size-ordered cluster list is cut into windows of `window` markers; the
 // clusters that start in one window are split greedily into batches that fit
-// one CTA (kCapCl clusters, kCapP particles, cap_m3 markers, max_rows row-table
-// entries), so that small clusters share a CTA.
+// one CTA (kCapCl clusters, kCapP particles, `window` markers, max_rows
+// row-table entries), so that small clusters share a CTA.
 __global__ void k_batch_plan(const int *cnt_in, const int *cum, const int *order, const int *cl_np,
-                             const int *cl_nm, const int *cl_box, int cap_m3, int max_rows, int2 *batches,
+                             const int *cl_nm, const int *cl_box, int window, int max_rows, int2 *batches,
                              int *cnt) {
     const int n_items = cnt_in[C_NITEMS];
-    const int nw = (cum[n_items] + kWindow - 1) / kWindow;
+    const int nw = (cum[n_items] + window - 1) / window;
+    const int cap_m3 = window;
     for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
-        const int c0 = lower_bound_int(cum, n_items, w * kWindow);
-        const int c1 = lower_bound_int(cum, n_items, (w + 1) * kWindow);
+        const int c0 = lower_bound_int(cum, n_items, w * window);
+        const int c1 = lower_bound_int(cum, n_items, (w + 1) * window);
         int c = c0;
         while (c < c1) {
             const int start = c;
@@ -450,11 +450,12 @@ __global__ void k_scan1(const int *in, int *out, int n, long long *total) {
 // Work items.  Clusters on the shared-memory path are ordered by size
 // (largest first) and their marker counts, each particle's padded to a whole
 // number of 32-marker chunks, are prefix-summed.  The prefix is cut into
-// windows of kWindow markers; a CTA takes one window at a time and packs the
-// clusters that start in it into batches that fit its shared memory (up to
-// kCapCl clusters, kCapP particles, a row-table budget and the marker
-// capacity), so that small clusters (a single D = 12h sphere has 452 markers)
-// share a CTA instead of leaving most of its threads idle.
+// windows of the record path's marker capacity (2048 markers for 1024
+// threads); the clusters that start in one window are packed into batches
+// that fit one CTA's shared memory (up to kCapCl clusters, kCapP particles, a
+// row-table budget and the window), so that small clusters (a single D = 12h
+// sphere has 452 markers) share a CTA instead of leaving most of its threads
+// idle.  A CTA takes one batch at a time from the list.
 
 struct PS {          // particle record in shared memory
     PInfo P;
@@ -577,10 +578,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 template <int TPB, int KM>
 __host__ __device__ constexpr int fixed_smem_bytes() {
-    // particle and cluster tables, overflow accumulators, chunk sums, chunk -> particle;
-    // the row table that follows starts 16-byte aligned
-    return (int)(((sizeof(PS) * kCapP + sizeof(CS) * kCapCl + sizeof(double) * 6 * kCapP +
-                   sizeof(float) * (TPB * KM / 32) * 6 + ((TPB * KM / 32 + 15) & ~15)) + 15) & ~15);
+    // particle and cluster tables, chunk sums, chunk -> particle; the row table
+    // that follows starts 16-byte aligned
+    return (int)(((sizeof(PS) * kCapP + sizeof(CS) * kCapCl + sizeof(float) * (TPB * KM / 32) * 6 +
+                   ((TPB * KM / 32 + 15) & ~15)) + 15) & ~15);
 }
 
 struct Batch {
@@ -684,25 +685,30 @@ __device__ __forceinline__ bool mark_stencil(uint2 *rt, const CS &cs, const int 
     return true;
 }
 
-__device__ __forceinline__ int unpack_slot(const unsigned (&sp)[5], int i) {
-    return i == 8 ? (int)sp[4] : (int)((sp[i >> 1] >> ((i & 1) * 16)) & 0xffffu);
-}
+// Deterministic mode keeps the touched cells in fixed point while markers
+// spread into them: value = round(u 2^k) in int32, with one power-of-two
+// scale per cluster and iteration.  The scale comes from a running bound B on
+// |u| over the cluster's cells: B_0 = max |u^0| (one scan after the gather),
+// and before the spreading of iteration m, B_m = B_{m-1} + 64 Dmax max|e^m|,
+// which bounds |u^m| because no cell collects more than 64 unit weights
+// (Sec. 2.2.2: u^m = u^{m-1} + W^T D e^m).  2^k is the largest power of two
+// with B_m 2^k < 2^30, so every cell value and every partial sum fits.  The
+// scale depends only on the cluster, never on how clusters are batched or on
+// the order of the atomic additions, so the result is bit-reproducible.
+// The per-cluster slot ranges start at multiples of 4 and their padding is
+// zero, so the passes use 16-byte accesses.
 
-// Fixed-point scale of every cluster of the batch (deterministic mode): 2^k
-// with (max|u| + 64 Dmax max|e|) 2^k < 2^30, so that every cell value and every
-// partial sum of spread contributions fits in int32; then u -> int.  The
-// per-cluster slot ranges start at multiples of 4 and their padding is zero,
-// so the passes use 16-byte accesses.
+// B_0: max |u| over components 0..NC-1 of each cluster's cells (umax must be
+// zero on entry).
 template <int TPB, int NC>
-__device__ __forceinline__ void det_to_fixed(const Batch &bt, CS *s_cs, float *s_u) {
+__device__ __forceinline__ void det_scan(const Batch &bt, CS *s_cs, const float *s_u) {
     const int tid = threadIdx.x, lane = tid & 31;
-    const int C = bt.C;
     for (int j = 0; j < bt.nb; ++j) {
         const int n4 = (s_cs[j].ncell + 3) >> 2;
         float um = 0.f;
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-            const float4 *p = reinterpret_cast<const float4 *>(s_u + q * C + s_cs[j].slot0);
+            const float4 *p = reinterpret_cast<const float4 *>(s_u + q * bt.C + s_cs[j].slot0);
             for (int i = tid; i < n4; i += TPB) {
                 const float4 v = p[i];
                 um = fmaxf(um, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
@@ -711,45 +717,45 @@ __device__ __forceinline__ void det_to_fixed(const Batch &bt, CS *s_cs, float *s
         um = warp_max(um);
         if (lane == 0 && um > 0.f) atomicMax(&s_cs[j].umax, __float_as_uint(um));
     }
-    __syncthreads();
-    for (int j = tid; j < bt.nb; j += TPB) {
+}
+
+// Scale of this iteration from the bound and the iteration's max |e| (one
+// thread per cluster); advances the bound and clears max |e| for the next
+// iteration.
+template <int TPB>
+__device__ __forceinline__ void det_scale(const Batch &bt, CS *s_cs) {
+    for (int j = threadIdx.x; j < bt.nb; j += TPB) {
         const float range = __uint_as_float(s_cs[j].umax) + 64.f * s_cs[j].dmax * __uint_as_float(s_cs[j].emax);
         int ex = 100;
         if (range > 0.f) ex = min(100, max(-100, 29 - (int)ceilf(log2f(range))));
         s_cs[j].S = ldexpf(1.f, ex);
         s_cs[j].invS = ldexpf(1.f, -ex);
-    }
-    __syncthreads();
-    for (int j = 0; j < bt.nb; ++j) {
-        const int n4 = (s_cs[j].ncell + 3) >> 2;
-        const float S = s_cs[j].S;
-#pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            float4 *p = reinterpret_cast<float4 *>(s_u + q * C + s_cs[j].slot0);
-            for (int i = tid; i < n4; i += TPB) {
-                const float4 v = p[i];
-                int4 r;
-                r.x = __float2int_rn(v.x * S); r.y = __float2int_rn(v.y * S);
-                r.z = __float2int_rn(v.z * S); r.w = __float2int_rn(v.w * S);
-                reinterpret_cast<int4 *>(p)[i] = r;
-            }
-        }
+        s_cs[j].umax = __float_as_uint(range);
+        s_cs[j].emax = 0u;
     }
 }
 
-template <int TPB, int NC>
-__device__ __forceinline__ void det_from_fixed(const Batch &bt, const CS *s_cs, float *s_u) {
+// u -> round(u S) (TO) or back, components 0..NC-1 of every cluster.
+template <int TPB, int NC, bool TO>
+__device__ __forceinline__ void det_convert(const Batch &bt, const CS *s_cs, float *s_u) {
     const int tid = threadIdx.x;
-    const int C = bt.C;
     for (int j = 0; j < bt.nb; ++j) {
         const int n4 = (s_cs[j].ncell + 3) >> 2;
-        const float invS = s_cs[j].invS;
+        const float S = TO ? s_cs[j].S : s_cs[j].invS;
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-            float4 *p = reinterpret_cast<float4 *>(s_u + q * C + s_cs[j].slot0);
+            float4 *p = reinterpret_cast<float4 *>(s_u + q * bt.C + s_cs[j].slot0);
             for (int i = tid; i < n4; i += TPB) {
-                const int4 r = reinterpret_cast<const int4 *>(p)[i];
-                p[i] = make_float4((float)r.x * invS, (float)r.y * invS, (float)r.z * invS, (float)r.w * invS);
+                if (TO) {
+                    const float4 v = p[i];
+                    int4 r;
+                    r.x = __float2int_rn(v.x * S); r.y = __float2int_rn(v.y * S);
+                    r.z = __float2int_rn(v.z * S); r.w = __float2int_rn(v.w * S);
+                    reinterpret_cast<int4 *>(p)[i] = r;
+                } else {
+                    const int4 r = reinterpret_cast<const int4 *>(p)[i];
+                    p[i] = make_float4((float)r.x * S, (float)r.y * S, (float)r.z * S, (float)r.w * S);
+                }
             }
         }
     }
@@ -765,153 +771,146 @@ __device__ __forceinline__ void zero_padding(const Batch &bt, const CS *s_cs, fl
     }
 }
 
-// The outer forcing loop of a batch of at most TPB*KC markers with each
-// thread's markers (weights, packed row slots, U^d, the summed slip) held in
-// registers for the whole step.
-template <int TPB, int KC, bool DET>
-__device__ __forceinline__ void forcing_cached(const KParams &prm, const Batch &bt, const PS *s_ps, CS *s_cs,
-                                               float *s_part, const unsigned char *s_chunk, const uint2 *s_row,
-                                               const unsigned short *s_inv, float *s_u, unsigned cvalid, const int (&cb)[KC][3],
-                                               const float (&cf)[KC][3]) {
+// Gather components q0..q0+NC-1 of the touched cells, zero the padding and,
+// in deterministic mode, start the bound of the fixed-point scale.
+template <int TPB, int NC, bool DET>
+__device__ __forceinline__ void load_cells(const KParams &prm, const Batch &bt, CS *s_cs, const uint2 *s_row,
+                                           const unsigned short *s_inv, float *s_u, int q0) {
+    for (int j = threadIdx.x; j < bt.nb; j += TPB) { s_cs[j].umax = 0u; s_cs[j].emax = 0u; }
+    move_cells<TPB, NC, true>(prm, bt, s_cs, s_row, s_inv, s_u, q0);
+    __syncthreads();
+    zero_padding<TPB, NC>(bt, s_cs, s_u);
+    __syncthreads();
+    if (DET) det_scan<TPB, NC>(bt, s_cs, s_u);
+}
+
+constexpr unsigned kNoMarker = 0xffffffffu;   // record of a padding marker
+
+// Slot i (0..8, row dz*3+dy) of a marker record: rows 0..7 packed two per
+// word in rb, row 8 in the low bits of ra.w.
+__device__ __forceinline__ int rec_slot(const uint4 &rb, unsigned s8, int i) {
+    const unsigned wd = i < 2 ? rb.x : (i < 4 ? rb.y : (i < 6 ? rb.z : rb.w));
+    return i == 8 ? (int)s8 : (int)((wd >> ((i & 1) * 16)) & 0xffffu);
+}
+
+// The outer forcing loop (Sec. 2.2.2) of a batch whose markers' stencils are
+// held as records in shared memory: ra[m] = (fractional position, slot of
+// row 8) and rb[m] = slots of rows 0..7, built once per step, so that each
+// iteration only recomputes the nine phi_3 weights.  Markers m = tid + k TPB,
+// k < KR; e^m stays in registers between interpolation and spreading.  The
+// per-chunk load sums are taken every iteration, in the same order as the
+// recomputing path, so that both give identical results.
+template <int TPB, int KR, bool DET>
+__device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt, const PS *s_ps, CS *s_cs,
+                                            float *s_part, const unsigned char *s_chunk, const uint2 *s_row,
+                                            const unsigned short *s_inv, float *s_u, const float4 *s_ra,
+                                            const uint4 *s_rb) {
     int *s_ui = reinterpret_cast<int *>(s_u);
     const int tid = threadIdx.x, lane = tid & 31;
     const int C = bt.C, nm = bt.nm;
-    unsigned sp[KC][5];
-    float *s_E = s_u + 3 * C;   // per-marker sum of e over the iterations, [nm][3]
-    for (int i = tid; i < 3 * nm; i += TPB) s_E[i] = 0.f;
-#pragma unroll
-    for (int k = 0; k < KC; ++k) {
-#pragma unroll
-        for (int i = 0; i < 5; ++i) sp[k][i] = 0u;
-        if (cvalid & (1u << k)) {
-            const int m = tid + k * TPB;
-            const PS &s = s_ps[s_chunk[m >> 5]];
-            const CS &cs = s_cs[s.cl];
-            int sl[9];
-            row_slots(s_row + cs.row0, cs.W, cs.By, cb[k], sl);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) sp[k][i] = (unsigned)sl[2 * i] | ((unsigned)sl[2 * i + 1] << 16);
-            sp[k][4] = (unsigned)sl[8];
-        }
-    }
-    move_cells<TPB, 3, true>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
-    __syncthreads();
-    zero_padding<TPB, 3>(bt, s_cs, s_u);
-    __syncthreads();
+    load_cells<TPB, 3, DET>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
     for (int iter = 0; iter < prm.n_forcing; ++iter) {
-        float e[KC][3];
-        if (DET) {
-            for (int j = tid; j < bt.nb; j += TPB) { s_cs[j].umax = 0u; s_cs[j].emax = 0u; }
-            __syncthreads();
-        }
+        float e[KR][3];
 #pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            float em = 0.f;
+        for (int k = 0; k < KR; ++k) {
+            const int m = tid + k * TPB;
             e[k][0] = e[k][1] = e[k][2] = 0.f;
-            if (cvalid & (1u << k)) {
+            if (m - lane >= nm) continue;   // whole warp past the end
+            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float em = 0.f;
+            const float4 a = s_ra[m];
+            const PS &s = s_ps[s_chunk[m >> 5]];
+            if (__float_as_uint(a.w) != kNoMarker) {
+                const uint4 rb = s_rb[m];
+                const unsigned s8 = __float_as_uint(a.w);
                 float w[3][3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) phi3_weights(cf[k][c], w[c]);
+                phi3_weights(a.x, w[0]);
+                phi3_weights(a.y, w[1]);
+                phi3_weights(a.z, w[2]);
                 float U0 = 0.f, U1 = 0.f, U2 = 0.f;
 #pragma unroll
-                for (int dz = 0; dz < 3; ++dz) {
-                    // keep one z-plane of loads in flight (register budget of the cached path)
-                    asm volatile("" ::: "memory");
+                for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
                     for (int dy = 0; dy < 3; ++dy) {
-                        const int sl = unpack_slot(sp[k], dz * 3 + dy);
+                        const int sl = rec_slot(rb, s8, dz * 3 + dy);
                         const float wyz = w[2][dz] * w[1][dy];
                         const float a0 = wyz * w[0][0], a1 = wyz * w[0][1], a2 = wyz * w[0][2];
                         U0 += a0 * s_u[sl] + a1 * s_u[sl + 1] + a2 * s_u[sl + 2];
                         U1 += a0 * s_u[C + sl] + a1 * s_u[C + sl + 1] + a2 * s_u[C + sl + 2];
                         U2 += a0 * s_u[2 * C + sl] + a1 * s_u[2 * C + sl + 1] + a2 * s_u[2 * C + sl + 2];
                     }
-                }
                 // desired velocity U^d = u_p + w_p x r_l (Sec. 2.1), from the particle record
-                const int m = tid + k * TPB;
-                const PS &s = s_ps[s_chunk[m >> 5]];
                 const float *t = prm.t32 + 3ll * (s.P.toff + (m - s.mstart));
                 const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
                 e[k][0] = s.P.ud[0] + (s.P.om[1] * r2 - s.P.om[2] * r1) - U0;
                 e[k][1] = s.P.ud[1] + (s.P.om[2] * r0 - s.P.om[0] * r2) - U1;
                 e[k][2] = s.P.ud[2] + (s.P.om[0] * r1 - s.P.om[1] * r0) - U2;
-#pragma unroll
-                for (int q = 0; q < 3; ++q) s_E[3 * m + q] += e[k][q];
                 em = fmaxf(fabsf(e[k][0]), fmaxf(fabsf(e[k][1]), fabsf(e[k][2])));
-            }
-            if (DET && (tid - lane) + k * TPB < nm) {
-                const float wm = warp_max(em);
-                if (lane == 0)
-                    atomicMax(&s_cs[s_ps[s_chunk[(tid + k * TPB) >> 5]].cl].emax, __float_as_uint(wm));
-            }
-        }
-        if (DET) {
-            __syncthreads();
-            det_to_fixed<TPB, 3>(bt, s_cs, s_u);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            if (cvalid & (1u << k)) {
-                const int m = tid + k * TPB;
-                const PS &s = s_ps[s_chunk[m >> 5]];
-                const float D = s.P.D * (DET ? s_cs[s.cl].S : 1.f);
-                const float g0 = e[k][0] * D, g1 = e[k][1] * D, g2 = e[k][2] * D;
-                float w[3][3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) phi3_weights(cf[k][c], w[c]);
-#pragma unroll
-                for (int dz = 0; dz < 3; ++dz) {
-                    asm volatile("" ::: "memory");   // one z-plane of atomics at a time
-#pragma unroll
-                    for (int dy = 0; dy < 3; ++dy) {
-                        const int sl = unpack_slot(sp[k], dz * 3 + dy);
-                        const float wyz = w[2][dz] * w[1][dy];
-#pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) {
-                            const float a = wyz * w[0][dx];
-                            if (DET) {
-                                atomicAdd(&s_ui[sl + dx], __float2int_rn(a * g0));
-                                atomicAdd(&s_ui[C + sl + dx], __float2int_rn(a * g1));
-                                atomicAdd(&s_ui[2 * C + sl + dx], __float2int_rn(a * g2));
-                            } else {
-                                atomicAdd(&s_u[sl + dx], a * g0);
-                                atomicAdd(&s_u[C + sl + dx], a * g1);
-                                atomicAdd(&s_u[2 * C + sl + dx], a * g2);
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        if (DET) {
-            det_from_fixed<TPB, 3>(bt, s_cs, s_u);
-            __syncthreads();
-        }
-    }
-    // particle loads once per step: sum_m e^m = E per marker, warp sums of E D
-    // and r x E D per 32-marker chunk (one particle per chunk)
-#pragma unroll
-    for (int k = 0; k < KC; ++k) {
-        const int m = tid + k * TPB;
-        if ((tid - lane) + k * TPB < nm) {
-            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (cvalid & (1u << k)) {
-                const PS &s = s_ps[s_chunk[m >> 5]];
-                const float *t = prm.t32 + 3ll * (s.P.toff + (m - s.mstart));
-                const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
                 const float D = s.P.D;
-                v[0] = s_E[3 * m] * D; v[1] = s_E[3 * m + 1] * D; v[2] = s_E[3 * m + 2] * D;
+                v[0] = e[k][0] * D; v[1] = e[k][1] * D; v[2] = e[k][2] * D;
                 v[3] = r1 * v[2] - r2 * v[1];
                 v[4] = r2 * v[0] - r0 * v[2];
                 v[5] = r0 * v[1] - r1 * v[0];
             }
+            // the 32 lanes of a warp hold markers of one particle: warp sums into
+            // the chunk table (FP32 over 32 terms; FP64 across chunks at the end)
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
                 const float x = warp_sum(v[q]);
-                if (lane == 0) s_part[(m >> 5) * 6 + q] = x;
+                if (lane == 0) s_part[(m >> 5) * 6 + q] += x;
             }
+            if (DET) {
+                const float wm = warp_max(em);
+                if (lane == 0) atomicMax(&s_cs[s.cl].emax, __float_as_uint(wm));
+            }
+        }
+        __syncthreads();
+        if (DET) {
+            det_scale<TPB>(bt, s_cs);
+            __syncthreads();
+            det_convert<TPB, 3, true>(bt, s_cs, s_u);
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            const int m = tid + k * TPB;
+            if (m >= nm) continue;
+            const float4 a = s_ra[m];
+            if (__float_as_uint(a.w) == kNoMarker) continue;
+            const uint4 rb = s_rb[m];
+            const unsigned s8 = __float_as_uint(a.w);
+            const PS &s = s_ps[s_chunk[m >> 5]];
+            const float D = s.P.D * (DET ? s_cs[s.cl].S : 1.f);
+            const float g0 = e[k][0] * D, g1 = e[k][1] * D, g2 = e[k][2] * D;
+            float w[3][3];
+            phi3_weights(a.x, w[0]);
+            phi3_weights(a.y, w[1]);
+            phi3_weights(a.z, w[2]);
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+                    const int sl = rec_slot(rb, s8, dz * 3 + dy);
+                    const float wyz = w[2][dz] * w[1][dy];
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const float c = wyz * w[0][dx];
+                        if (DET) {
+                            atomicAdd(&s_ui[sl + dx], __float2int_rn(c * g0));
+                            atomicAdd(&s_ui[C + sl + dx], __float2int_rn(c * g1));
+                            atomicAdd(&s_ui[2 * C + sl + dx], __float2int_rn(c * g2));
+                        } else {
+                            atomicAdd(&s_u[sl + dx], c * g0);
+                            atomicAdd(&s_u[C + sl + dx], c * g1);
+                            atomicAdd(&s_u[2 * C + sl + dx], c * g2);
+                        }
+                    }
+                }
+        }
+        __syncthreads();
+        if (DET) {
+            det_convert<TPB, 3, false>(bt, s_cs, s_u);
+            __syncthreads();
         }
     }
     move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
@@ -933,9 +932,6 @@ __device__ __forceinline__ void forcing_loop(const KParams &prm, const Batch &bt
     const int C = bt.C, nm = bt.nm;
     for (int iter = 0; iter < prm.n_forcing; ++iter) {
         float ereg[KK][NC];
-        if (DET)
-            for (int j = tid; j < bt.nb; j += TPB) { s_cs[j].umax = 0u; s_cs[j].emax = 0u; }
-        if (DET) __syncthreads();
 #pragma unroll
         for (int k = 0; k < KK; ++k) {
             const int m = tid + k * TPB;
@@ -1014,11 +1010,13 @@ __device__ __forceinline__ void forcing_loop(const KParams &prm, const Batch &bt
                 }
             }
         }
-        if (DET) {
-            __syncthreads();
-            det_to_fixed<TPB, NC>(bt, s_cs, s_u);
-        }
         __syncthreads();
+        if (DET) {
+            det_scale<TPB>(bt, s_cs);
+            __syncthreads();
+            det_convert<TPB, NC, true>(bt, s_cs, s_u);
+            __syncthreads();
+        }
 #pragma unroll
         for (int k = 0; k < KK; ++k) {
             const int m = tid + k * TPB;
@@ -1058,24 +1056,23 @@ __device__ __forceinline__ void forcing_loop(const KParams &prm, const Batch &bt
         }
         __syncthreads();
         if (DET) {
-            det_from_fixed<TPB, NC>(bt, s_cs, s_u);
+            det_convert<TPB, NC, false>(bt, s_cs, s_u);
             __syncthreads();
         }
     }
 }
 
-// One persistent CTA per SM.  KM: marker slots per thread of the general path;
-// KC: markers per thread held in registers by the cached path.  DET =
+// Persistent CTAs (MINB per SM).  KM: marker slots per thread of the
+// recomputing path; KR: markers per thread of the record path.  DET =
 // fixed-point spreading (int32 shared-memory atomics, bit-reproducible and
 // independent of how clusters are batched).
-template <int TPB, int KM, int KC, bool DET>
-__global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
+template <int TPB, int KM, int KR, bool DET, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
     constexpr int NCH = TPB * KM / 32;   // 32-marker chunks
     extern __shared__ __align__(16) unsigned char smem[];
     PS *s_ps = reinterpret_cast<PS *>(smem);
     CS *s_cs = reinterpret_cast<CS *>(s_ps + kCapP);
-    double *s_acc = reinterpret_cast<double *>(s_cs + kCapCl);           // [kCapP][6]
-    float *s_part = reinterpret_cast<float *>(s_acc + 6 * kCapP);        // [NCH][6]
+    float *s_part = reinterpret_cast<float *>(s_cs + kCapCl);            // [NCH][6]
     unsigned char *s_chunk = reinterpret_cast<unsigned char *>(s_part + NCH * 6);   // [NCH] chunk -> particle
     uint2 *s_row = reinterpret_cast<uint2 *>(smem + fixed_smem_bytes<TPB, KM>());   // [R] then the cells
     unsigned char *dyn_end = smem + prm.smem_bytes;
@@ -1177,47 +1174,30 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
                     s_chunk[ch] = (unsigned char)i;
             __syncthreads();
 
-            // 1. touched-cell bitmask of every cluster (bounds-checked).  A batch of
-            // at most TPB*KC markers keeps each thread's markers' stencils in
-            // registers for the whole step (computed once instead of twice per
-            // iteration).
-            const bool cached = nm <= TPB * KC;
-            int cb[KC][3];          // box-relative base cells (until the slots are known)
-            float cf[KC][3];        // fractional marker positions (weights are recomputed)
-            unsigned cvalid = 0u;   // bit k: slot k holds a marker
-            if (cached) {
-#pragma unroll
-                for (int k = 0; k < KC; ++k) {
-                    const int m = tid + k * TPB;
-                    cb[k][0] = cb[k][1] = cb[k][2] = 0;
-                    cf[k][0] = cf[k][1] = cf[k][2] = 0.f;
-                    if (m < nm) {
-                        const PS &s = s_ps[s_chunk[m >> 5]];
-                        const int l = m - s.mstart;
-                        if (l < s.P.nl) {
-                            int b[3];
-                            rel_base(s, prm.t32, prm.t64, l, b, cf[k]);
-                            const CS &cs = s_cs[s.cl];
-                            if (mark_stencil(s_row + cs.row0, cs, b)) {
-                                cb[k][0] = b[0]; cb[k][1] = b[1]; cb[k][2] = b[2];
-                                cvalid |= 1u << k;
-                            } else {
-                                s_flag = 1;
-                            }
-                        }
-                    }
+            // 1. touched-cell bitmask of every cluster (bounds-checked).  When the
+            // batch's marker records fit in the top of shared memory beside the row
+            // table, each marker's fractional position and packed box-relative base
+            // cell are kept there (the base becomes the row slots after step 2).
+            const int rec_bytes = 32 * nm;
+            float4 *const s_ra = reinterpret_cast<float4 *>(dyn_end - rec_bytes);
+            uint4 *const s_rb = reinterpret_cast<uint4 *>(dyn_end - rec_bytes / 2);
+            const bool rec_ok = nm <= TPB * KR &&
+                                reinterpret_cast<unsigned char *>(s_row + bt.R) + 16 <= dyn_end - rec_bytes;
+            for (int m = tid; m < nm; m += TPB) {
+                const PS &s = s_ps[s_chunk[m >> 5]];
+                const int l = m - s.mstart;
+                if (l >= s.P.nl) {
+                    if (rec_ok) s_ra[m] = make_float4(0.f, 0.f, 0.f, __uint_as_float(kNoMarker));
+                    continue;
                 }
-            } else {
-                for (int m = tid; m < nm; m += TPB) {
-                    const PS &s = s_ps[s_chunk[m >> 5]];
-                    const int l = m - s.mstart;
-                    if (l >= s.P.nl) continue;
-                    int b[3];
-                    float wt[3][3];
-                    rel_stencil(s, prm.t32, prm.t64, l, b, wt);
-                    const CS &cs = s_cs[s.cl];
-                    if (!mark_stencil(s_row + cs.row0, cs, b)) s_flag = 1;
-                }
+                int b[3];
+                float f[3];
+                rel_base(s, prm.t32, prm.t64, l, b, f);
+                const CS &cs = s_cs[s.cl];
+                if (!mark_stencil(s_row + cs.row0, cs, b)) s_flag = 1;
+                if (rec_ok)
+                    s_ra[m] = make_float4(f[0], f[1], f[2],
+                                          __uint_as_float((unsigned)b[0] | ((unsigned)b[1] << 10) | ((unsigned)b[2] << 20)));
             }
             __syncthreads();
             // 2. compact slots: exclusive prefix of the popcounts over all rows, then
@@ -1273,8 +1253,9 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
             float *const u_plain = align16(s_row + bt.R);
             const int cap_cells = (int)((dyn_end - reinterpret_cast<unsigned char *>(u_plain)) / 4);
             const bool three = 3 * bt.C <= cap_cells && nm <= TPB * (KM / 3);
-            const bool use_cached = cached && three && 3 * bt.C + 3 * nm <= cap_cells;
-            const int need = use_cached ? 3 * bt.C + 3 * nm : (three ? 3 * bt.C : bt.C);
+            // record path: cells below the records
+            const bool use_rec = rec_ok && three && 3 * bt.C + rec_bytes / 4 <= cap_cells;
+            const int need = use_rec ? 3 * bt.C + rec_bytes / 4 : (three ? 3 * bt.C : bt.C);
             unsigned short *s_inv = reinterpret_cast<unsigned short *>(s_row + bt.R);
             float *const u_inv = align16(s_inv + bt.C);
             const bool use_inv = (int)((dyn_end - reinterpret_cast<unsigned char *>(u_inv)) / 4) >= need;
@@ -1292,6 +1273,20 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
                 }
             } else {
                 s_inv = nullptr;
+            }
+            if (use_rec) {
+                // base cell -> the nine row slots of the marker's stencil
+                for (int m = tid; m < nm; m += TPB) {
+                    const unsigned bp = __float_as_uint(s_ra[m].w);
+                    if (bp == kNoMarker) continue;
+                    const CS &cs = s_cs[s_ps[s_chunk[m >> 5]].cl];
+                    const int b[3] = {(int)(bp & 1023u), (int)((bp >> 10) & 1023u), (int)(bp >> 20)};
+                    int sl[9];
+                    row_slots(s_row + cs.row0, cs.W, cs.By, b, sl);
+                    s_rb[m] = make_uint4((unsigned)sl[0] | ((unsigned)sl[1] << 16), (unsigned)sl[2] | ((unsigned)sl[3] << 16),
+                                         (unsigned)sl[4] | ((unsigned)sl[5] << 16), (unsigned)sl[6] | ((unsigned)sl[7] << 16));
+                    s_ra[m].w = __uint_as_float((unsigned)sl[8]);
+                }
             }
             __syncthreads();
             if (s_flag || bt.C > cap_cells || nm > TPB * KM) {
@@ -1315,21 +1310,15 @@ __global__ void __launch_bounds__(TPB, 1) k_cluster_forcing(KParams prm) {
                 if (!three) atomicAdd(prm.cnt + C_ONECOMP, bt.nb);
             }
             __syncthreads();
-            if (use_cached) {
-                forcing_cached<TPB, KC, DET>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_inv, s_u, cvalid, cb, cf);
+            if (use_rec) {
+                forcing_rec<TPB, KR, DET>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_inv, s_u, s_ra, s_rb);
             } else if (three) {
-                move_cells<TPB, 3, true>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
-                __syncthreads();
-                zero_padding<TPB, 3>(bt, s_cs, s_u);
-                __syncthreads();
+                load_cells<TPB, 3, DET>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
                 forcing_loop<TPB, KM, DET, 3>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_u, 0);
                 move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
             } else {
                 for (int q = 0; q < 3; ++q) {
-                    move_cells<TPB, 1, true>(prm, bt, s_cs, s_row, s_inv, s_u, q);
-                    __syncthreads();
-                    zero_padding<TPB, 1>(bt, s_cs, s_u);
-                    __syncthreads();
+                    load_cells<TPB, 1, DET>(prm, bt, s_cs, s_row, s_inv, s_u, q);
                     forcing_loop<TPB, KM, DET, 1>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_u, q);
                     move_cells<TPB, 1, false>(prm, bt, s_cs, s_row, s_inv, s_u, q);
                     __syncthreads();
@@ -1355,12 +1344,15 @@ int grid_for(long long n, int block) {
     return (int)std::max(1ll, std::min(g, 65535ll * 8));
 }
 
-static int max_dyn_smem() {
-    int dev = 0, optin = 0;
+// Dynamic shared memory per CTA when minb CTAs share an SM.
+static int max_dyn_smem(int minb = 1) {
+    int dev = 0, optin = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     const int statics = 64 * 4 + 64;   // s_item, s_flag, s_scan, s_total, s_red
-    return optin - statics - 256;
+    const int per_block = minb <= 1 ? optin : std::min(optin, per_sm / minb - 1024);
+    return per_block - statics - 256;
 }
 
 }  // namespace
@@ -1453,11 +1445,11 @@ static ibm_status cluster_alloc(ibm_ctx *ctx) {
     return IBM_OK;
 }
 
-template <int TPB, int KM, int KC, bool DET>
+template <int TPB, int KM, int KR, bool DET, int MINB>
 static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams &prm) {
-    auto kern = k_cluster_forcing<TPB, KM, KC, DET>;
+    auto kern = k_cluster_forcing<TPB, KM, KR, DET, MINB>;
     if (S->smem_bytes == 0 || S->tpb != TPB || S->det != (int)DET) {
-        S->smem_bytes = max_dyn_smem() & ~15;
+        S->smem_bytes = max_dyn_smem(MINB) & ~15;
         S->cap_c = (S->smem_bytes - fixed_smem_bytes<TPB, KM>()) / 4;   // FP32 cell slots (all components)
         S->tpb = TPB;
         S->kmax = KM;
@@ -1475,10 +1467,11 @@ static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams
     return ibm_cuda_check(ctx, cudaGetLastError(), "cluster kernel");
 }
 
-// marker slots per thread of the cluster kernel's general path, and markers per
-// thread held in registers by its cached path, for a block size
-static int markers_per_thread(int tpb) { return tpb == 1024 ? 12 : (tpb == 512 ? 24 : 48); }
-static int cached_per_thread(int tpb) { return tpb == 1024 ? 1 : (tpb == 512 ? 4 : 8); }
+// marker slots per thread of the cluster kernel's recomputing path, and
+// markers per thread of its record path, for a block size
+static int markers_per_thread(int tpb) { return tpb == 1024 ? 12 : (tpb == 512 ? 12 : 48); }
+static int records_per_thread(int tpb) { return tpb == 1024 ? 2 : (tpb == 512 ? 2 : 8); }
+static int ctas_per_sm(int tpb) { return tpb == 512 ? 2 : 1; }
 
 ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
     ibm_status st = ensure_field_ptrs(ctx, u_ptrs, f_out);
@@ -1491,7 +1484,7 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     const int tpb = ctx->cfg.threads_per_block ? ctx->cfg.threads_per_block : 1024;
     const int cap_m = tpb * markers_per_thread(tpb);
     // row table may take at most half of the dynamic shared memory
-    const int max_rows = (max_dyn_smem() - fixed_smem_bytes<256, 48>()) / 16;
+    const int max_rows = (max_dyn_smem(ctas_per_sm(tpb)) - fixed_smem_bytes<256, 48>()) / 16;
 
     CK(cudaMemsetAsync(S->cnt, 0, C_COUNT * sizeof(int), sm), "zero counters");
     CK(cudaMemsetAsync(S->bin_cnt, 0, (S->nbins + 1) * sizeof(int), sm), "zero bins");
@@ -1522,10 +1515,11 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     k_order_fill<<<gb, 256, 0, sm>>>(S->tot + 1, S->cl_bkt, S->bkt_start, S->bkt_start + kBuckets + 1, S->order);
     k_gather_nm<<<gb, 256, 0, sm>>>(n, S->cnt, S->order, S->cl_nm, S->nm_ord);
     k_scan1<<<1, 1024, 0, sm>>>(S->nm_ord, S->cum, n, S->tot + 3);
-    const long long max_windows = (ctx->n_markers + 32ll * n) / kWindow + 2;
+    // packing window = the record path's marker capacity
+    const int window = tpb * records_per_thread(tpb);
+    const long long max_windows = (ctx->n_markers + 32ll * n) / window + 2;
     k_batch_plan<<<grid_for(max_windows, 128), 128, 0, sm>>>(S->cnt, S->cum, S->order, S->cl_np, S->cl_nm,
-                                                            S->cl_box, tpb * cached_per_thread(tpb),
-                                                            max_rows, S->batches, S->cnt);
+                                                            S->cl_box, window, max_rows, S->batches, S->cnt);
     ctx->launches += 16;
 
     KParams prm;
@@ -1555,14 +1549,14 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prof_begin(ctx);
     const bool det = ctx->cfg.spread_mode == IBM_SPREAD_DETERMINISTIC;
     if (tpb == 1024)
-        st = det ? launch_cluster_kernel<1024, 12, 1, true>(ctx, S, prm)
-                 : launch_cluster_kernel<1024, 12, 1, false>(ctx, S, prm);
+        st = det ? launch_cluster_kernel<1024, 12, 2, true, 1>(ctx, S, prm)
+                 : launch_cluster_kernel<1024, 12, 2, false, 1>(ctx, S, prm);
     else if (tpb == 512)
-        st = det ? launch_cluster_kernel<512, 24, 4, true>(ctx, S, prm)
-                 : launch_cluster_kernel<512, 24, 4, false>(ctx, S, prm);
+        st = det ? launch_cluster_kernel<512, 12, 2, true, 2>(ctx, S, prm)
+                 : launch_cluster_kernel<512, 12, 2, false, 2>(ctx, S, prm);
     else
-        st = det ? launch_cluster_kernel<256, 48, 8, true>(ctx, S, prm)
-                 : launch_cluster_kernel<256, 48, 8, false>(ctx, S, prm);
+        st = det ? launch_cluster_kernel<256, 48, 8, true, 1>(ctx, S, prm)
+                 : launch_cluster_kernel<256, 48, 8, false, 1>(ctx, S, prm);
     prof_end(ctx);
     if (st != IBM_OK) return st;
     ctx->launches += 1;
