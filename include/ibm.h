@@ -80,7 +80,7 @@ typedef struct {
     double g[3];             /* gravity vector (Newton-Euler only)             */
     int max_particles;       /* capacity of the context                        */
     int requires_grad;       /* 1: keep what ibm_backward needs                */
-    int threads_per_block;   /* 0 = autotune; else 256, 512 or 1024 (CLUSTER)  */
+    int threads_per_block;   /* 0 = default (1024); else 512 or 1024 (CLUSTER)  */
     int profile;             /* 1: time the main forcing kernel with CUDA events */
 } ibm_config;
 

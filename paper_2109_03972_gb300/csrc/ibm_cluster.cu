@@ -522,17 +522,6 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
     return pre;
 }
 
-// Largest j with key[j] <= v among n entries (key[0] <= v).
-__device__ __forceinline__ int upper_index(const CS *cs, int n, int v, bool by_slot) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if ((by_slot ? cs[mid].slot0 : cs[mid].row0) <= v) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 // Box-relative base cell and weights of a marker (FP32 path).
 __device__ __forceinline__ void rel_stencil(const PS &s, const float *t32, const double *t64, int l, int b[3],
                                             float w[3][3]) {
@@ -571,7 +560,8 @@ __device__ __forceinline__ void row_slots(const uint2 *rt, int W, int By, const 
 
 __device__ __forceinline__ void cp_async4(void *smem_ptr, const void *gmem_ptr) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_ptr);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_ptr) : "memory");
+    // no memory clobber: nothing reads the target before cp_async_wait_all
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_ptr));
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -590,78 +580,68 @@ struct Batch {
 
 
 // Gather (LOAD) or write back the touched cells of components q0..q0+NC-1 of
-// every cluster of the batch, one thread per cell slot: consecutive threads
-// take consecutive slots, i.e. consecutive cells of a row run, so the global
-// accesses coalesce.  s_inv maps a slot to its bitmask entry (0xffff for the
-// padding slots).
+// every cluster of the batch, cluster by cluster (its box and scene are
+// uniform in the loop).  With the slot table s_inv (slot -> bitmask entry)
+// consecutive threads take consecutive slots, i.e. consecutive cells of a row
+// run, so the global accesses coalesce; without it one thread walks the set
+// bits of one bitmask entry.
 template <int TPB, int NC, bool LOAD>
 __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, const CS *s_cs, const uint2 *s_row,
                                            const unsigned short *s_inv, float *s_u, int q0) {
-    if (!s_inv) {
-        // no slot table: one thread per bitmask entry, walking its set bits
-        for (int i = threadIdx.x; i < bt.R; i += TPB) {
-            unsigned mask = s_row[i].x;
-            if (!mask) continue;
-            const CS &cs = s_cs[upper_index(s_cs, bt.nb, i, false)];
-            const int li = i - cs.row0;
-            const int row = (int)(((float)li + 0.5f) * __frcp_rn((float)cs.W));
-            const int wx = li - row * cs.W;
-            const int rz = (int)(((float)row + 0.5f) * __frcp_rn((float)cs.By));
-            const int ry = row - rz * cs.By;
-            const int sc = cs.scene;
-            const int nx = prm.dims[3 * sc], ny = prm.dims[3 * sc + 1], nz = prm.dims[3 * sc + 2];
-            const long long ncell = (long long)nx * ny * nz;
-            const long long rowbase = ((long long)wrapi(cs.z0 + rz, nz) * ny + wrapi(cs.y0 + ry, ny)) * nx;
-            float *u = prm.uf[sc];
-            float *f = prm.ff ? prm.ff[sc] : nullptr;
-            int sl = (int)s_row[i].y;
-            while (mask) {
-                const int bit = __ffs(mask) - 1;
-                mask &= mask - 1u;
-                const long long g = rowbase + wrapi(cs.x0 + 32 * wx + bit, nx);
-#pragma unroll
-                for (int q = 0; q < NC; ++q) {
-                    const long long gq = (long long)(q0 + q) * ncell + g;
-                    if (LOAD) {
-                        cp_async4(s_u + q * bt.C + sl, u + gq);
-                    } else {
-                        if (f) f[gq] = (s_u[q * bt.C + sl] - u[gq]) * prm.finv;
-                        u[gq] = s_u[q * bt.C + sl];
-                    }
-                }
-                ++sl;
-            }
-        }
-        if (LOAD) cp_async_wait_all();
-        return;
-    }
-    for (int sl = threadIdx.x; sl < bt.C; sl += TPB) {
-        const unsigned i = s_inv[sl];
-        if (i == 0xffffu) continue;
-        const uint2 rw = s_row[i];
-        const CS &cs = s_cs[upper_index(s_cs, bt.nb, (int)i, false)];
-        // entry -> (row, word) -> (ry, rz); exact small-integer divisions in FP32
-        const int li = (int)i - cs.row0;
-        const int row = (int)(((float)li + 0.5f) * __frcp_rn((float)cs.W));
-        const int wx = li - row * cs.W;
-        const int rz = (int)(((float)row + 0.5f) * __frcp_rn((float)cs.By));
-        const int ry = row - rz * cs.By;
-        const int bit = (int)__fns(rw.x, 0u, sl - (int)rw.y + 1);
-        const int sc = cs.scene;
+    const int tid = threadIdx.x;
+    for (int j = 0; j < bt.nb; ++j) {
+        const int x0 = s_cs[j].x0, y0 = s_cs[j].y0, z0 = s_cs[j].z0;
+        const int W = s_cs[j].W, By = s_cs[j].By, row0 = s_cs[j].row0;
+        const int sc = s_cs[j].scene;
         const int nx = prm.dims[3 * sc], ny = prm.dims[3 * sc + 1], nz = prm.dims[3 * sc + 2];
         const long long ncell = (long long)nx * ny * nz;
-        const long long g = ((long long)wrapi(cs.z0 + rz, nz) * ny + wrapi(cs.y0 + ry, ny)) * nx +
-                            wrapi(cs.x0 + 32 * wx + bit, nx);
-        float *u = prm.uf[sc];
-        float *f = prm.ff ? prm.ff[sc] : nullptr;
+        float *u = prm.uf[sc] + (long long)q0 * ncell;
+        float *f = prm.ff ? prm.ff[sc] + (long long)q0 * ncell : nullptr;
+        float *su = s_u + s_cs[j].slot0;   // this cluster's slots, component q0
+        // entry -> (row, word) -> (ry, rz): exact small-integer divisions in FP32
+        const float rW = __frcp_rn((float)W), rBy = __frcp_rn((float)By);
+        auto row_base = [&](int li, int &wx) {
+            const int row = (int)(((float)li + 0.5f) * rW);
+            wx = li - row * W;
+            const int rz = (int)(((float)row + 0.5f) * rBy);
+            const int ry = row - rz * By;
+            return ((long long)wrapi(z0 + rz, nz) * ny + wrapi(y0 + ry, ny)) * nx;
+        };
+        auto move = [&](long long g, int sl) {
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            const long long gq = (long long)(q0 + q) * ncell + g;
-            if (LOAD) {
-                cp_async4(s_u + q * bt.C + sl, u + gq);
-            } else {
-                if (f) f[gq] = (s_u[q * bt.C + sl] - u[gq]) * prm.finv;
-                u[gq] = s_u[q * bt.C + sl];
+            for (int q = 0; q < NC; ++q) {
+                if (LOAD) {
+                    cp_async4(su + q * bt.C + sl, u + q * ncell + g);
+                } else {
+                    const float v = su[q * bt.C + sl];
+                    if (f) f[q * ncell + g] = (v - u[q * ncell + g]) * prm.finv;
+                    u[q * ncell + g] = v;
+                }
+            }
+        };
+        if (s_inv) {
+            const int base = s_cs[j].slot0;
+            for (int sl = tid; sl < s_cs[j].ncell; sl += TPB) {
+                const unsigned i = s_inv[base + sl];
+                const uint2 rw = s_row[i];
+                int wx;
+                const long long rb = row_base((int)i - row0, wx);
+                const int bit = (int)__fns(rw.x, 0u, base + sl - (int)rw.y + 1);
+                move(rb + wrapi(x0 + 32 * wx + bit, nx), sl);
+            }
+        } else {
+            for (int li = tid; li < s_cs[j].R; li += TPB) {
+                unsigned mask = s_row[row0 + li].x;
+                if (!mask) continue;
+                int wx;
+                const long long rb = row_base(li, wx);
+                int sl = (int)s_row[row0 + li].y - s_cs[j].slot0;
+                while (mask) {
+                    const int bit = __ffs(mask) - 1;
+                    mask &= mask - 1u;
+                    move(rb + wrapi(x0 + 32 * wx + bit, nx), sl);
+                    ++sl;
+                }
             }
         }
     }
@@ -793,28 +773,31 @@ __device__ __forceinline__ int rec_slot(const uint4 &rb, unsigned s8, int i) {
     return i == 8 ? (int)s8 : (int)((wd >> ((i & 1) * 16)) & 0xffffu);
 }
 
-// The outer forcing loop (Sec. 2.2.2) of a batch whose markers' stencils are
-// held as records in shared memory: ra[m] = (fractional position, slot of
-// row 8) and rb[m] = slots of rows 0..7, built once per step, so that each
-// iteration only recomputes the nine phi_3 weights.  Markers m = tid + k TPB,
-// k < KR; e^m stays in registers between interpolation and spreading.  The
-// per-chunk load sums are taken every iteration, in the same order as the
-// recomputing path, so that both give identical results.
-template <int TPB, int KR, bool DET>
+// The outer forcing loop (Sec. 2.2.2) for components q0..q0+NC-1 of a batch
+// whose markers' stencils are held as records in shared memory: ra[m] =
+// (fractional position, slot of row 8) and rb[m] = slots of rows 0..7, built
+// once per step, so that each iteration only recomputes the nine phi_3
+// weights.  Components are independent in the loop, so a batch too large for
+// all three runs them one at a time (NC = 1).  Markers m = tid + k TPB, k < KR;
+// e^m stays in registers between interpolation and spreading.  The per-chunk
+// load sums are taken every iteration, in the same order as the recomputing
+// path, so that both give identical results.
+template <int TPB, int KR, bool DET, int NC>
 __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt, const PS *s_ps, CS *s_cs,
                                             float *s_part, const unsigned char *s_chunk, const uint2 *s_row,
                                             const unsigned short *s_inv, float *s_u, const float4 *s_ra,
-                                            const uint4 *s_rb) {
+                                            const uint4 *s_rb, int q0) {
     int *s_ui = reinterpret_cast<int *>(s_u);
     const int tid = threadIdx.x, lane = tid & 31;
     const int C = bt.C, nm = bt.nm;
-    load_cells<TPB, 3, DET>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
+    load_cells<TPB, NC, DET>(prm, bt, s_cs, s_row, s_inv, s_u, q0);
     for (int iter = 0; iter < prm.n_forcing; ++iter) {
-        float e[KR][3];
+        float e[KR][NC];
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
             const int m = tid + k * TPB;
-            e[k][0] = e[k][1] = e[k][2] = 0.f;
+#pragma unroll
+            for (int q = 0; q < NC; ++q) e[k][q] = 0.f;
             if (m - lane >= nm) continue;   // whole warp past the end
             float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float em = 0.f;
@@ -827,7 +810,9 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
                 phi3_weights(a.x, w[0]);
                 phi3_weights(a.y, w[1]);
                 phi3_weights(a.z, w[2]);
-                float U0 = 0.f, U1 = 0.f, U2 = 0.f;
+                float U[NC];
+#pragma unroll
+                for (int q = 0; q < NC; ++q) U[q] = 0.f;
 #pragma unroll
                 for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
@@ -835,27 +820,42 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
                         const int sl = rec_slot(rb, s8, dz * 3 + dy);
                         const float wyz = w[2][dz] * w[1][dy];
                         const float a0 = wyz * w[0][0], a1 = wyz * w[0][1], a2 = wyz * w[0][2];
-                        U0 += a0 * s_u[sl] + a1 * s_u[sl + 1] + a2 * s_u[sl + 2];
-                        U1 += a0 * s_u[C + sl] + a1 * s_u[C + sl + 1] + a2 * s_u[C + sl + 2];
-                        U2 += a0 * s_u[2 * C + sl] + a1 * s_u[2 * C + sl + 1] + a2 * s_u[2 * C + sl + 2];
+#pragma unroll
+                        for (int q = 0; q < NC; ++q)
+                            U[q] += a0 * s_u[q * C + sl] + a1 * s_u[q * C + sl + 1] + a2 * s_u[q * C + sl + 2];
                     }
                 // desired velocity U^d = u_p + w_p x r_l (Sec. 2.1), from the particle record
                 const float *t = prm.t32 + 3ll * (s.P.toff + (m - s.mstart));
                 const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
-                e[k][0] = s.P.ud[0] + (s.P.om[1] * r2 - s.P.om[2] * r1) - U0;
-                e[k][1] = s.P.ud[1] + (s.P.om[2] * r0 - s.P.om[0] * r2) - U1;
-                e[k][2] = s.P.ud[2] + (s.P.om[0] * r1 - s.P.om[1] * r0) - U2;
-                em = fmaxf(fabsf(e[k][0]), fmaxf(fabsf(e[k][1]), fabsf(e[k][2])));
+                const float ud0 = s.P.ud[0] + (s.P.om[1] * r2 - s.P.om[2] * r1);
+                const float ud1 = s.P.ud[1] + (s.P.om[2] * r0 - s.P.om[0] * r2);
+                const float ud2 = s.P.ud[2] + (s.P.om[0] * r1 - s.P.om[1] * r0);
                 const float D = s.P.D;
-                v[0] = e[k][0] * D; v[1] = e[k][1] * D; v[2] = e[k][2] * D;
-                v[3] = r1 * v[2] - r2 * v[1];
-                v[4] = r2 * v[0] - r0 * v[2];
-                v[5] = r0 * v[1] - r1 * v[0];
+                float ed[3];
+                if (NC == 3) {
+                    e[k][0] = ud0 - U[0];
+                    e[k][NC > 1 ? 1 : 0] = ud1 - U[NC > 1 ? 1 : 0];
+                    e[k][NC > 2 ? 2 : 0] = ud2 - U[NC > 2 ? 2 : 0];
+                    em = fmaxf(fabsf(e[k][0]), fmaxf(fabsf(e[k][NC > 1 ? 1 : 0]), fabsf(e[k][NC > 2 ? 2 : 0])));
+                    ed[0] = e[k][0] * D; ed[1] = e[k][NC > 1 ? 1 : 0] * D; ed[2] = e[k][NC > 2 ? 2 : 0] * D;
+                } else {
+                    const float x = (q0 == 0 ? ud0 : (q0 == 1 ? ud1 : ud2)) - U[0];
+                    e[k][0] = x;
+                    em = fabsf(x);
+                    ed[0] = q0 == 0 ? x * D : 0.f;
+                    ed[1] = q0 == 1 ? x * D : 0.f;
+                    ed[2] = q0 == 2 ? x * D : 0.f;
+                }
+                v[0] = ed[0]; v[1] = ed[1]; v[2] = ed[2];
+                v[3] = r1 * ed[2] - r2 * ed[1];
+                v[4] = r2 * ed[0] - r0 * ed[2];
+                v[5] = r0 * ed[1] - r1 * ed[0];
             }
             // the 32 lanes of a warp hold markers of one particle: warp sums into
             // the chunk table (FP32 over 32 terms; FP64 across chunks at the end)
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
+                if (NC == 1 && ((q < 3 && q != q0) || q == 3 + q0)) continue;   // zero in this pass
                 const float x = warp_sum(v[q]);
                 if (lane == 0) s_part[(m >> 5) * 6 + q] += x;
             }
@@ -868,7 +868,7 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
         if (DET) {
             det_scale<TPB>(bt, s_cs);
             __syncthreads();
-            det_convert<TPB, 3, true>(bt, s_cs, s_u);
+            det_convert<TPB, NC, true>(bt, s_cs, s_u);
             __syncthreads();
         }
 #pragma unroll
@@ -881,7 +881,9 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
             const unsigned s8 = __float_as_uint(a.w);
             const PS &s = s_ps[s_chunk[m >> 5]];
             const float D = s.P.D * (DET ? s_cs[s.cl].S : 1.f);
-            const float g0 = e[k][0] * D, g1 = e[k][1] * D, g2 = e[k][2] * D;
+            float g[NC];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) g[q] = e[k][q] * D;
             float w[3][3];
             phi3_weights(a.x, w[0]);
             phi3_weights(a.y, w[1]);
@@ -895,25 +897,21 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
                         const float c = wyz * w[0][dx];
-                        if (DET) {
-                            atomicAdd(&s_ui[sl + dx], __float2int_rn(c * g0));
-                            atomicAdd(&s_ui[C + sl + dx], __float2int_rn(c * g1));
-                            atomicAdd(&s_ui[2 * C + sl + dx], __float2int_rn(c * g2));
-                        } else {
-                            atomicAdd(&s_u[sl + dx], c * g0);
-                            atomicAdd(&s_u[C + sl + dx], c * g1);
-                            atomicAdd(&s_u[2 * C + sl + dx], c * g2);
+#pragma unroll
+                        for (int q = 0; q < NC; ++q) {
+                            if (DET) atomicAdd(&s_ui[q * C + sl + dx], __float2int_rn(c * g[q]));
+                            else atomicAdd(&s_u[q * C + sl + dx], c * g[q]);
                         }
                     }
                 }
         }
         __syncthreads();
         if (DET) {
-            det_convert<TPB, 3, false>(bt, s_cs, s_u);
+            det_convert<TPB, NC, false>(bt, s_cs, s_u);
             __syncthreads();
         }
     }
-    move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
+    move_cells<TPB, NC, false>(prm, bt, s_cs, s_row, s_inv, s_u, q0);
 }
 
 // The outer forcing loop (Sec. 2.2.2) for components q0..q0+NC-1 of a batch,
@@ -1063,10 +1061,11 @@ __device__ __forceinline__ void forcing_loop(const KParams &prm, const Batch &bt
 }
 
 // Persistent CTAs (MINB per SM).  KM: marker slots per thread of the
-// recomputing path; KR: markers per thread of the record path.  DET =
+// recomputing path; KR, KR1: markers per thread of the record path with all
+// three components or one at a time.  DET =
 // fixed-point spreading (int32 shared-memory atomics, bit-reproducible and
 // independent of how clusters are batched).
-template <int TPB, int KM, int KR, bool DET, int MINB>
+template <int TPB, int KM, int KR, int KR1, bool DET, int MINB>
 __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
     constexpr int NCH = TPB * KM / 32;   // 32-marker chunks
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1181,7 +1180,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
             const int rec_bytes = 32 * nm;
             float4 *const s_ra = reinterpret_cast<float4 *>(dyn_end - rec_bytes);
             uint4 *const s_rb = reinterpret_cast<uint4 *>(dyn_end - rec_bytes / 2);
-            const bool rec_ok = nm <= TPB * KR &&
+            const bool rec_ok = nm <= TPB * KR1 &&
                                 reinterpret_cast<unsigned char *>(s_row + bt.R) + 16 <= dyn_end - rec_bytes;
             for (int m = tid; m < nm; m += TPB) {
                 const PS &s = s_ps[s_chunk[m >> 5]];
@@ -1238,9 +1237,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                     if (tid == 31) s_total = inc;
                 }
                 __syncthreads();
-                for (int i = tid; i < bt.R; i += TPB) {
-                    if (!s_row[i].x) continue;
-                    s_row[i].y += (unsigned)s_cs[upper_index(s_cs, bt.nb, i, false)].shift;
+                for (int j = 0; j < bt.nb; ++j) {
+                    const unsigned sh = (unsigned)s_cs[j].shift;
+                    const int r1 = s_cs[j].row0 + s_cs[j].R;
+                    for (int i = s_cs[j].row0 + tid; i < r1; i += TPB)
+                        if (s_row[i].x) s_row[i].y += sh;
                 }
             }
             __syncthreads();
@@ -1254,8 +1255,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
             const int cap_cells = (int)((dyn_end - reinterpret_cast<unsigned char *>(u_plain)) / 4);
             const bool three = 3 * bt.C <= cap_cells && nm <= TPB * (KM / 3);
             // record path: cells below the records
-            const bool use_rec = rec_ok && three && 3 * bt.C + rec_bytes / 4 <= cap_cells;
-            const int need = use_rec ? 3 * bt.C + rec_bytes / 4 : (three ? 3 * bt.C : bt.C);
+            const bool use_rec = rec_ok && three && nm <= TPB * KR && 3 * bt.C + rec_bytes / 4 <= cap_cells;
+            // one component at a time: with records where the three do not fit
+            const bool use_rec1 = !three && rec_ok && bt.C + rec_bytes / 4 <= cap_cells;
+            const int need = use_rec ? 3 * bt.C + rec_bytes / 4
+                                     : (use_rec1 ? bt.C + rec_bytes / 4 : (three ? 3 * bt.C : bt.C));
             unsigned short *s_inv = reinterpret_cast<unsigned short *>(s_row + bt.R);
             float *const u_inv = align16(s_inv + bt.C);
             const bool use_inv = (int)((dyn_end - reinterpret_cast<unsigned char *>(u_inv)) / 4) >= need;
@@ -1274,7 +1278,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
             } else {
                 s_inv = nullptr;
             }
-            if (use_rec) {
+            if (use_rec || use_rec1) {
                 // base cell -> the nine row slots of the marker's stencil
                 for (int m = tid; m < nm; m += TPB) {
                     const unsigned bp = __float_as_uint(s_ra[m].w);
@@ -1311,7 +1315,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
             }
             __syncthreads();
             if (use_rec) {
-                forcing_rec<TPB, KR, DET>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_inv, s_u, s_ra, s_rb);
+                forcing_rec<TPB, KR, DET, 3>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_inv, s_u, s_ra, s_rb, 0);
+            } else if (use_rec1) {
+                for (int q = 0; q < 3; ++q) {
+                    forcing_rec<TPB, KR1, DET, 1>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_inv, s_u, s_ra, s_rb,
+                                                  q);
+                    __syncthreads();
+                }
             } else if (three) {
                 load_cells<TPB, 3, DET>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
                 forcing_loop<TPB, KM, DET, 3>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_u, 0);
@@ -1445,9 +1455,9 @@ static ibm_status cluster_alloc(ibm_ctx *ctx) {
     return IBM_OK;
 }
 
-template <int TPB, int KM, int KR, bool DET, int MINB>
+template <int TPB, int KM, int KR, int KR1, bool DET, int MINB>
 static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams &prm) {
-    auto kern = k_cluster_forcing<TPB, KM, KR, DET, MINB>;
+    auto kern = k_cluster_forcing<TPB, KM, KR, KR1, DET, MINB>;
     if (S->smem_bytes == 0 || S->tpb != TPB || S->det != (int)DET) {
         S->smem_bytes = max_dyn_smem(MINB) & ~15;
         S->cap_c = (S->smem_bytes - fixed_smem_bytes<TPB, KM>()) / 4;   // FP32 cell slots (all components)
@@ -1469,8 +1479,8 @@ static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams
 
 // marker slots per thread of the cluster kernel's recomputing path, and
 // markers per thread of its record path, for a block size
-static int markers_per_thread(int tpb) { return tpb == 1024 ? 12 : (tpb == 512 ? 12 : 48); }
-static int records_per_thread(int tpb) { return tpb == 1024 ? 2 : (tpb == 512 ? 2 : 8); }
+static int markers_per_thread(int) { return 12; }
+static int records_per_thread(int) { return 2; }
 static int ctas_per_sm(int tpb) { return tpb == 512 ? 2 : 1; }
 
 ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
@@ -1484,7 +1494,7 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     const int tpb = ctx->cfg.threads_per_block ? ctx->cfg.threads_per_block : 1024;
     const int cap_m = tpb * markers_per_thread(tpb);
     // row table may take at most half of the dynamic shared memory
-    const int max_rows = (max_dyn_smem(ctas_per_sm(tpb)) - fixed_smem_bytes<256, 48>()) / 16;
+    const int max_rows = (max_dyn_smem(ctas_per_sm(tpb)) - fixed_smem_bytes<1024, 12>()) / 16;
 
     CK(cudaMemsetAsync(S->cnt, 0, C_COUNT * sizeof(int), sm), "zero counters");
     CK(cudaMemsetAsync(S->bin_cnt, 0, (S->nbins + 1) * sizeof(int), sm), "zero bins");
@@ -1549,14 +1559,11 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prof_begin(ctx);
     const bool det = ctx->cfg.spread_mode == IBM_SPREAD_DETERMINISTIC;
     if (tpb == 1024)
-        st = det ? launch_cluster_kernel<1024, 12, 2, true, 1>(ctx, S, prm)
-                 : launch_cluster_kernel<1024, 12, 2, false, 1>(ctx, S, prm);
-    else if (tpb == 512)
-        st = det ? launch_cluster_kernel<512, 12, 2, true, 2>(ctx, S, prm)
-                 : launch_cluster_kernel<512, 12, 2, false, 2>(ctx, S, prm);
+        st = det ? launch_cluster_kernel<1024, 12, 2, 5, true, 1>(ctx, S, prm)
+                 : launch_cluster_kernel<1024, 12, 2, 5, false, 1>(ctx, S, prm);
     else
-        st = det ? launch_cluster_kernel<256, 48, 8, true, 1>(ctx, S, prm)
-                 : launch_cluster_kernel<256, 48, 8, false, 1>(ctx, S, prm);
+        st = det ? launch_cluster_kernel<512, 12, 2, 5, true, 2>(ctx, S, prm)
+                 : launch_cluster_kernel<512, 12, 2, 5, false, 2>(ctx, S, prm);
     prof_end(ctx);
     if (st != IBM_OK) return st;
     ctx->launches += 1;

@@ -138,8 +138,7 @@ ibm_status ibm_create(const ibm_config *cfg, void *cuda_stream, ibm_ctx **out) {
     if (cfg->newton_euler && (!(cfg->rho_f > 0.0) || !std::isfinite(cfg->g[0]) ||
                               !std::isfinite(cfg->g[1]) || !std::isfinite(cfg->g[2])))
         return IBM_ERR_INVALID_ARG;
-    if (cfg->threads_per_block != 0 && cfg->threads_per_block != 256 &&
-        cfg->threads_per_block != 512 && cfg->threads_per_block != 1024)
+    if (cfg->threads_per_block != 0 && cfg->threads_per_block != 512 && cfg->threads_per_block != 1024)
         return IBM_ERR_INVALID_ARG;
     int min_edge = 1 << 30;
     for (int s = 0; s < cfg->n_scenes; ++s)
