@@ -76,6 +76,8 @@ struct ClusterScratch {
     int *bkt_cnt = nullptr, *bkt_start = nullptr, *order = nullptr, *fb_list = nullptr;
     int *nm_ord = nullptr, *cum = nullptr, *cl_scene = nullptr;
     int2 *batches = nullptr;
+    float4 *grec = nullptr;          // marker records of batches kept in global memory
+    size_t grec_bytes = 0;
     int smem_bytes = 0, cap_c = 0, tpb = 0, kmax = 0, det = -1;
 };
 
@@ -487,6 +489,7 @@ struct KParams {
     float *const *ff;
     const int *order, *cl_first, *cl_np, *cl_nm, *cl_box, *cl_plist, *cl_scene, *poff;
     const int2 *batches;
+    float4 *grec;   // per CTA: 2 * TPB * KM float4 (records a, then b)
     int *cnt, *fb_list, *err;
     double *FD, *TD;
     int n_forcing, smem_bytes, max_rows;
@@ -520,19 +523,6 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
     *total = sh[TPB / 32 - 1];
     __syncthreads();
     return pre;
-}
-
-// Box-relative base cell and weights of a marker (FP32 path).
-__device__ __forceinline__ void rel_stencil(const PS &s, const float *t32, const double *t64, int l, int b[3],
-                                            float w[3][3]) {
-    const float *t = t32 + 3ll * (s.P.toff + l);
-    const double *t6 = t64 + 3ll * (s.P.toff + l);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float fr;
-        b[c] = marker_split32(s.P, t, t6, c, &fr) + s.off[c];
-        phi3_weights(fr, w[c]);
-    }
 }
 
 // Box-relative base cell and fractional position of a marker (FP32 path).
@@ -773,20 +763,21 @@ __device__ __forceinline__ int rec_slot(const uint4 &rb, unsigned s8, int i) {
     return i == 8 ? (int)s8 : (int)((wd >> ((i & 1) * 16)) & 0xffffu);
 }
 
-// The outer forcing loop (Sec. 2.2.2) for components q0..q0+NC-1 of a batch
-// whose markers' stencils are held as records in shared memory: ra[m] =
-// (fractional position, slot of row 8) and rb[m] = slots of rows 0..7, built
-// once per step, so that each iteration only recomputes the nine phi_3
-// weights.  Components are independent in the loop, so a batch too large for
-// all three runs them one at a time (NC = 1).  Markers m = tid + k TPB, k < KR;
-// e^m stays in registers between interpolation and spreading.  The per-chunk
-// load sums are taken every iteration, in the same order as the recomputing
-// path, so that both give identical results.
+// The outer forcing loop (Sec. 2.2.2) for components q0..q0+NC-1 of a batch,
+// on its touched cells in shared memory.  Each marker's stencil is a record
+// built once per step: ra[m] = (fractional position, slot of row 8), rb[m] =
+// slots of rows 0..7, in shared memory when they fit there and in global
+// memory (L2) otherwise, so that each iteration only recomputes the nine
+// phi_3 weights.  Components are independent in the loop, so a batch too
+// large for all three runs them one at a time (NC = 1).  Markers m = tid +
+// k TPB, k < KR; e^m stays in registers between interpolation and spreading.
+// The per-chunk load sums are taken every iteration (FP32 warp sums of 32
+// markers of one particle; FP64 across chunks at the end).
 template <int TPB, int KR, bool DET, int NC>
 __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt, const PS *s_ps, CS *s_cs,
                                             float *s_part, const unsigned char *s_chunk, const uint2 *s_row,
-                                            const unsigned short *s_inv, float *s_u, const float4 *s_ra,
-                                            const uint4 *s_rb, int q0) {
+                                            const unsigned short *s_inv, float *s_u, const float4 *ra,
+                                            const uint4 *rb, int q0) {
     int *s_ui = reinterpret_cast<int *>(s_u);
     const int tid = threadIdx.x, lane = tid & 31;
     const int C = bt.C, nm = bt.nm;
@@ -801,10 +792,10 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
             if (m - lane >= nm) continue;   // whole warp past the end
             float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float em = 0.f;
-            const float4 a = s_ra[m];
+            const float4 a = ra[m];
             const PS &s = s_ps[s_chunk[m >> 5]];
             if (__float_as_uint(a.w) != kNoMarker) {
-                const uint4 rb = s_rb[m];
+                const uint4 r = rb[m];
                 const unsigned s8 = __float_as_uint(a.w);
                 float w[3][3];
                 phi3_weights(a.x, w[0]);
@@ -817,7 +808,7 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
                 for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
                     for (int dy = 0; dy < 3; ++dy) {
-                        const int sl = rec_slot(rb, s8, dz * 3 + dy);
+                        const int sl = rec_slot(r, s8, dz * 3 + dy);
                         const float wyz = w[2][dz] * w[1][dy];
                         const float a0 = wyz * w[0][0], a1 = wyz * w[0][1], a2 = wyz * w[0][2];
 #pragma unroll
@@ -875,9 +866,9 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
         for (int k = 0; k < KR; ++k) {
             const int m = tid + k * TPB;
             if (m >= nm) continue;
-            const float4 a = s_ra[m];
+            const float4 a = ra[m];
             if (__float_as_uint(a.w) == kNoMarker) continue;
-            const uint4 rb = s_rb[m];
+            const uint4 r = rb[m];
             const unsigned s8 = __float_as_uint(a.w);
             const PS &s = s_ps[s_chunk[m >> 5]];
             const float D = s.P.D * (DET ? s_cs[s.cl].S : 1.f);
@@ -892,7 +883,7 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
             for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy) {
-                    const int sl = rec_slot(rb, s8, dz * 3 + dy);
+                    const int sl = rec_slot(r, s8, dz * 3 + dy);
                     const float wyz = w[2][dz] * w[1][dy];
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
@@ -914,158 +905,12 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
     move_cells<TPB, NC, false>(prm, bt, s_cs, s_row, s_inv, s_u, q0);
 }
 
-// The outer forcing loop (Sec. 2.2.2) for components q0..q0+NC-1 of a batch,
-// on its touched cells in shared memory.  Components are independent in the
-// loop (F = (U^d - W u)/tau and the spreading act per component), so a batch
-// too large for all three runs them one at a time.  Each warp handles 32
-// markers of one particle (particles are padded to whole chunks), so the
-// per-particle load sums are plain warp sums.
-template <int TPB, int KM, bool DET, int NC>
-__device__ __forceinline__ void forcing_loop(const KParams &prm, const Batch &bt, const PS *s_ps, CS *s_cs,
-                                             float *s_part, const unsigned char *s_chunk, const uint2 *s_row,
-                                             float *s_u, int q0) {
-    constexpr int KK = KM / NC;   // marker slots per thread in this pass
-    int *s_ui = reinterpret_cast<int *>(s_u);
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int C = bt.C, nm = bt.nm;
-    for (int iter = 0; iter < prm.n_forcing; ++iter) {
-        float ereg[KK][NC];
-#pragma unroll
-        for (int k = 0; k < KK; ++k) {
-            const int m = tid + k * TPB;
-            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float emax = 0.f;
-            int pi = -1;
-#pragma unroll
-            for (int q = 0; q < NC; ++q) ereg[k][q] = 0.f;
-            if (m < nm) {
-                pi = s_chunk[m >> 5];
-                const PS &s = s_ps[pi];
-                const int l = m - s.mstart;
-                if (l < s.P.nl) {
-                    const CS &cs = s_cs[s.cl];
-                    int b[3];
-                    float w[3][3];
-                    rel_stencil(s, prm.t32, prm.t64, l, b, w);
-                    int slot[9];
-                    row_slots(s_row + cs.row0, cs.W, cs.By, b, slot);
-                    float U[NC];
-#pragma unroll
-                    for (int q = 0; q < NC; ++q) U[q] = 0.f;
-#pragma unroll
-                    for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-                        for (int dy = 0; dy < 3; ++dy) {
-                            const int sl = slot[dz * 3 + dy];
-                            const float wyz = w[2][dz] * w[1][dy];
-                            const float a0 = wyz * w[0][0], a1 = wyz * w[0][1], a2 = wyz * w[0][2];
-#pragma unroll
-                            for (int q = 0; q < NC; ++q)
-                                U[q] += a0 * s_u[q * C + sl] + a1 * s_u[q * C + sl + 1] + a2 * s_u[q * C + sl + 2];
-                        }
-                    const float *t = prm.t32 + 3ll * (s.P.toff + l);
-                    const float r0 = s.P.rphys * t[0], r1 = s.P.rphys * t[1], r2 = s.P.rphys * t[2];
-                    const float ud0 = s.P.ud[0] + (s.P.om[1] * r2 - s.P.om[2] * r1);
-                    const float ud1 = s.P.ud[1] + (s.P.om[2] * r0 - s.P.om[0] * r2);
-                    const float ud2 = s.P.ud[2] + (s.P.om[0] * r1 - s.P.om[1] * r0);
-                    const float D = s.P.D;
-                    float ed[3];
-                    if (NC == 3) {
-                        const float e0 = ud0 - U[0], e1 = ud1 - U[NC > 1 ? 1 : 0], e2 = ud2 - U[NC > 2 ? 2 : 0];
-                        ereg[k][0] = e0;
-                        ereg[k][NC > 1 ? 1 : 0] = e1;
-                        ereg[k][NC > 2 ? 2 : 0] = e2;
-                        emax = fmaxf(fabsf(e0), fmaxf(fabsf(e1), fabsf(e2)));
-                        ed[0] = e0 * D; ed[1] = e1 * D; ed[2] = e2 * D;
-                    } else {
-                        const float e = (q0 == 0 ? ud0 : (q0 == 1 ? ud1 : ud2)) - U[0];
-                        ereg[k][0] = e;
-                        emax = fabsf(e);
-                        ed[0] = q0 == 0 ? e * D : 0.f;
-                        ed[1] = q0 == 1 ? e * D : 0.f;
-                        ed[2] = q0 == 2 ? e * D : 0.f;
-                    }
-                    v[0] = ed[0]; v[1] = ed[1]; v[2] = ed[2];
-                    v[3] = r1 * ed[2] - r2 * ed[1];
-                    v[4] = r2 * ed[0] - r0 * ed[2];
-                    v[5] = r0 * ed[1] - r1 * ed[0];
-                }
-            }
-            // the 32 lanes of a warp hold markers of one particle: warp sums into
-            // the chunk table (FP32 over 32 terms; FP64 across chunks at the end)
-            const int chunk = (m - lane) >> 5;
-            const bool any = __any_sync(0xffffffffu, pi >= 0 && m < nm);
-            if (any) {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    if (NC == 1 && ((q < 3 && q != q0) || q == 3 + q0)) continue;   // zero in this pass
-                    const float x = warp_sum(v[q]);
-                    if (lane == 0) s_part[chunk * 6 + q] += x;
-                }
-                if (DET) {
-                    const float wm = warp_max(emax);
-                    if (lane == 0) atomicMax(&s_cs[s_ps[pi].cl].emax, __float_as_uint(wm));
-                }
-            }
-        }
-        __syncthreads();
-        if (DET) {
-            det_scale<TPB>(bt, s_cs);
-            __syncthreads();
-            det_convert<TPB, NC, true>(bt, s_cs, s_u);
-            __syncthreads();
-        }
-#pragma unroll
-        for (int k = 0; k < KK; ++k) {
-            const int m = tid + k * TPB;
-            if (m < nm) {
-                const int pi = s_chunk[m >> 5];
-                const PS &s = s_ps[pi];
-                const int l = m - s.mstart;
-                if (l < s.P.nl) {
-                    const CS &cs = s_cs[s.cl];
-                    int b[3];
-                    float w[3][3];
-                    rel_stencil(s, prm.t32, prm.t64, l, b, w);
-                    int slot[9];
-                    row_slots(s_row + cs.row0, cs.W, cs.By, b, slot);
-                    const float D = s.P.D * (DET ? cs.S : 1.f);
-                    float g[NC];
-#pragma unroll
-                    for (int q = 0; q < NC; ++q) g[q] = ereg[k][q] * D;
-#pragma unroll
-                    for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-                        for (int dy = 0; dy < 3; ++dy) {
-                            const int sl = slot[dz * 3 + dy];
-                            const float wyz = w[2][dz] * w[1][dy];
-#pragma unroll
-                            for (int dx = 0; dx < 3; ++dx) {
-                                const float a = wyz * w[0][dx];
-#pragma unroll
-                                for (int q = 0; q < NC; ++q) {
-                                    if (DET) atomicAdd(&s_ui[q * C + sl + dx], __float2int_rn(a * g[q]));
-                                    else atomicAdd(&s_u[q * C + sl + dx], a * g[q]);
-                                }
-                            }
-                        }
-                }
-            }
-        }
-        __syncthreads();
-        if (DET) {
-            det_convert<TPB, NC, false>(bt, s_cs, s_u);
-            __syncthreads();
-        }
-    }
-}
-
-// Persistent CTAs (MINB per SM).  KM: marker slots per thread of the
-// recomputing path; KR, KR1: markers per thread of the record path with all
-// three components or one at a time.  DET =
+// Persistent CTAs (MINB per SM).  KM: markers per thread of a batch (at most
+// TPB KM markers, one component at a time; TPB KM / 3 with all three); KR:
+// markers per thread when the records stay in shared memory.  DET =
 // fixed-point spreading (int32 shared-memory atomics, bit-reproducible and
 // independent of how clusters are batched).
-template <int TPB, int KM, int KR, int KR1, bool DET, int MINB>
+template <int TPB, int KM, int KR, bool DET, int MINB>
 __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
     constexpr int NCH = TPB * KM / 32;   // 32-marker chunks
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1173,20 +1018,25 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                     s_chunk[ch] = (unsigned char)i;
             __syncthreads();
 
-            // 1. touched-cell bitmask of every cluster (bounds-checked).  When the
-            // batch's marker records fit in the top of shared memory beside the row
-            // table, each marker's fractional position and packed box-relative base
-            // cell are kept there (the base becomes the row slots after step 2).
+            // 1. touched-cell bitmask of every cluster (bounds-checked), and each
+            // marker's record: fractional position and packed box-relative base cell
+            // (the base becomes the nine row slots after step 2).  The records go to
+            // the top of shared memory when they fit there beside the row table,
+            // else to this CTA's slice of a global scratch (a few hundred KB, served
+            // from L2).
             const int rec_bytes = 32 * nm;
             float4 *const s_ra = reinterpret_cast<float4 *>(dyn_end - rec_bytes);
             uint4 *const s_rb = reinterpret_cast<uint4 *>(dyn_end - rec_bytes / 2);
-            const bool rec_ok = nm <= TPB * KR1 &&
-                                reinterpret_cast<unsigned char *>(s_row + bt.R) + 16 <= dyn_end - rec_bytes;
+            float4 *const g_ra = prm.grec + (size_t)blockIdx.x * (2 * TPB * KM);
+            uint4 *const g_rb = reinterpret_cast<uint4 *>(g_ra + TPB * KM);
+            const bool rec_smem = nm <= TPB * KR &&
+                                  reinterpret_cast<unsigned char *>(s_row + bt.R) + 16 <= dyn_end - rec_bytes;
+            float4 *const ra0 = rec_smem ? s_ra : g_ra;
             for (int m = tid; m < nm; m += TPB) {
                 const PS &s = s_ps[s_chunk[m >> 5]];
                 const int l = m - s.mstart;
                 if (l >= s.P.nl) {
-                    if (rec_ok) s_ra[m] = make_float4(0.f, 0.f, 0.f, __uint_as_float(kNoMarker));
+                    ra0[m] = make_float4(0.f, 0.f, 0.f, __uint_as_float(kNoMarker));
                     continue;
                 }
                 int b[3];
@@ -1194,9 +1044,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                 rel_base(s, prm.t32, prm.t64, l, b, f);
                 const CS &cs = s_cs[s.cl];
                 if (!mark_stencil(s_row + cs.row0, cs, b)) s_flag = 1;
-                if (rec_ok)
-                    s_ra[m] = make_float4(f[0], f[1], f[2],
-                                          __uint_as_float((unsigned)b[0] | ((unsigned)b[1] << 10) | ((unsigned)b[2] << 20)));
+                ra0[m] = make_float4(f[0], f[1], f[2],
+                                     __uint_as_float((unsigned)b[0] | ((unsigned)b[1] << 10) | ((unsigned)b[2] << 20)));
             }
             __syncthreads();
             // 2. compact slots: exclusive prefix of the popcounts over all rows, then
@@ -1254,12 +1103,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
             float *const u_plain = align16(s_row + bt.R);
             const int cap_cells = (int)((dyn_end - reinterpret_cast<unsigned char *>(u_plain)) / 4);
             const bool three = 3 * bt.C <= cap_cells && nm <= TPB * (KM / 3);
-            // record path: cells below the records
-            const bool use_rec = rec_ok && three && nm <= TPB * KR && 3 * bt.C + rec_bytes / 4 <= cap_cells;
-            // one component at a time: with records where the three do not fit
-            const bool use_rec1 = !three && rec_ok && bt.C + rec_bytes / 4 <= cap_cells;
-            const int need = use_rec ? 3 * bt.C + rec_bytes / 4
-                                     : (use_rec1 ? bt.C + rec_bytes / 4 : (three ? 3 * bt.C : bt.C));
+            // records stay in shared memory (below them the cells) if all fits
+            const bool use_rec = rec_smem && three && 3 * bt.C + rec_bytes / 4 <= cap_cells;
+            float4 *const ra = use_rec ? s_ra : g_ra;
+            uint4 *const rb = use_rec ? s_rb : g_rb;
+            const int need = use_rec ? 3 * bt.C + rec_bytes / 4 : (three ? 3 * bt.C : bt.C);
             unsigned short *s_inv = reinterpret_cast<unsigned short *>(s_row + bt.R);
             float *const u_inv = align16(s_inv + bt.C);
             const bool use_inv = (int)((dyn_end - reinterpret_cast<unsigned char *>(u_inv)) / 4) >= need;
@@ -1278,19 +1126,21 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
             } else {
                 s_inv = nullptr;
             }
-            if (use_rec || use_rec1) {
-                // base cell -> the nine row slots of the marker's stencil
-                for (int m = tid; m < nm; m += TPB) {
-                    const unsigned bp = __float_as_uint(s_ra[m].w);
-                    if (bp == kNoMarker) continue;
+            // base cell -> the nine row slots of the marker's stencil (records move
+            // to global memory if the cells need their shared memory)
+            for (int m = tid; m < nm; m += TPB) {
+                float4 a = ra0[m];
+                const unsigned bp = __float_as_uint(a.w);
+                if (bp != kNoMarker) {
                     const CS &cs = s_cs[s_ps[s_chunk[m >> 5]].cl];
                     const int b[3] = {(int)(bp & 1023u), (int)((bp >> 10) & 1023u), (int)(bp >> 20)};
                     int sl[9];
                     row_slots(s_row + cs.row0, cs.W, cs.By, b, sl);
-                    s_rb[m] = make_uint4((unsigned)sl[0] | ((unsigned)sl[1] << 16), (unsigned)sl[2] | ((unsigned)sl[3] << 16),
-                                         (unsigned)sl[4] | ((unsigned)sl[5] << 16), (unsigned)sl[6] | ((unsigned)sl[7] << 16));
-                    s_ra[m].w = __uint_as_float((unsigned)sl[8]);
+                    rb[m] = make_uint4((unsigned)sl[0] | ((unsigned)sl[1] << 16), (unsigned)sl[2] | ((unsigned)sl[3] << 16),
+                                       (unsigned)sl[4] | ((unsigned)sl[5] << 16), (unsigned)sl[6] | ((unsigned)sl[7] << 16));
+                    a.w = __uint_as_float((unsigned)sl[8]);
                 }
+                ra[m] = a;
             }
             __syncthreads();
             if (s_flag || bt.C > cap_cells || nm > TPB * KM) {
@@ -1315,22 +1165,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
             }
             __syncthreads();
             if (use_rec) {
-                forcing_rec<TPB, KR, DET, 3>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_inv, s_u, s_ra, s_rb, 0);
-            } else if (use_rec1) {
-                for (int q = 0; q < 3; ++q) {
-                    forcing_rec<TPB, KR1, DET, 1>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_inv, s_u, s_ra, s_rb,
-                                                  q);
-                    __syncthreads();
-                }
+                forcing_rec<TPB, KR, DET, 3>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_inv, s_u, ra, rb, 0);
             } else if (three) {
-                load_cells<TPB, 3, DET>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
-                forcing_loop<TPB, KM, DET, 3>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_u, 0);
-                move_cells<TPB, 3, false>(prm, bt, s_cs, s_row, s_inv, s_u, 0);
+                forcing_rec<TPB, KM / 3, DET, 3>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_inv, s_u, ra, rb, 0);
             } else {
                 for (int q = 0; q < 3; ++q) {
-                    load_cells<TPB, 1, DET>(prm, bt, s_cs, s_row, s_inv, s_u, q);
-                    forcing_loop<TPB, KM, DET, 1>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_u, q);
-                    move_cells<TPB, 1, false>(prm, bt, s_cs, s_row, s_inv, s_u, q);
+                    forcing_rec<TPB, KM, DET, 1>(prm, bt, s_ps, s_cs, s_part, s_chunk, s_row, s_inv, s_u, ra, rb, q);
                     __syncthreads();
                 }
             }
@@ -1379,6 +1219,7 @@ void cluster_free(ibm_ctx *ctx) {
     for (int *p : ptrs)
         if (p) cudaFree(p);
     if (S->batches) cudaFree(S->batches);
+    if (S->grec) cudaFree(S->grec);
     if (S->tot) cudaFree(S->tot);
     delete S;
     ctx->cl = nullptr;
@@ -1455,9 +1296,9 @@ static ibm_status cluster_alloc(ibm_ctx *ctx) {
     return IBM_OK;
 }
 
-template <int TPB, int KM, int KR, int KR1, bool DET, int MINB>
+template <int TPB, int KM, int KR, bool DET, int MINB>
 static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams &prm) {
-    auto kern = k_cluster_forcing<TPB, KM, KR, KR1, DET, MINB>;
+    auto kern = k_cluster_forcing<TPB, KM, KR, DET, MINB>;
     if (S->smem_bytes == 0 || S->tpb != TPB || S->det != (int)DET) {
         S->smem_bytes = max_dyn_smem(MINB) & ~15;
         S->cap_c = (S->smem_bytes - fixed_smem_bytes<TPB, KM>()) / 4;   // FP32 cell slots (all components)
@@ -1473,6 +1314,15 @@ static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, S->smem_bytes), "occupancy");
     const int grid = std::max(1, nsm * std::max(per_sm, 1));
+    const size_t grec = (size_t)grid * 2 * TPB * KM * sizeof(float4);
+    if (S->grec_bytes < grec) {
+        if (S->grec) cudaFree(S->grec);
+        S->grec = nullptr;
+        S->grec_bytes = 0;
+        CK(cudaMalloc(&S->grec, grec), "alloc marker records");
+        S->grec_bytes = grec;
+    }
+    prm.grec = S->grec;
     kern<<<grid, TPB, S->smem_bytes, ctx->stream>>>(prm);
     return ibm_cuda_check(ctx, cudaGetLastError(), "cluster kernel");
 }
@@ -1559,11 +1409,11 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prof_begin(ctx);
     const bool det = ctx->cfg.spread_mode == IBM_SPREAD_DETERMINISTIC;
     if (tpb == 1024)
-        st = det ? launch_cluster_kernel<1024, 12, 2, 5, true, 1>(ctx, S, prm)
-                 : launch_cluster_kernel<1024, 12, 2, 5, false, 1>(ctx, S, prm);
+        st = det ? launch_cluster_kernel<1024, 12, 2, true, 1>(ctx, S, prm)
+                 : launch_cluster_kernel<1024, 12, 2, false, 1>(ctx, S, prm);
     else
-        st = det ? launch_cluster_kernel<512, 12, 2, 5, true, 2>(ctx, S, prm)
-                 : launch_cluster_kernel<512, 12, 2, 5, false, 2>(ctx, S, prm);
+        st = det ? launch_cluster_kernel<512, 12, 2, true, 2>(ctx, S, prm)
+                 : launch_cluster_kernel<512, 12, 2, false, 2>(ctx, S, prm);
     prof_end(ctx);
     if (st != IBM_OK) return st;
     ctx->launches += 1;
