@@ -201,19 +201,29 @@ __global__ void k_candidates(int n_p, const PInfo *P, const int *scene_nb, const
 
 // Exact test of one candidate pair: some markers l of p and l' of q with
 // |b_l - b_l'|_inf <= 2 (then their 3x3x3 stencils share a cell).  Uses the
-// same FP32-path base cells as the forcing kernels.
+// same FP32-path base cells as the forcing kernels.  Only markers within
+// a + 3 sqrt 3 + 1 of the other centre can qualify.  q's qualifying base cells
+// are marked in a 32^3 bit volume around them, which is dilated by 2 along
+// each axis (separable max filter on 32-bit rows), so that each qualifying
+// marker of p needs one bit test.  A volume wider than 32 cells falls back to
+// comparing the two lists pair by pair.
 __global__ void __launch_bounds__(kPairThreads) k_pair_test(const PInfo *P, const float *t32, const double *t64,
                                                             const int32_t *dims, const int *cand, const int *cnt,
                                                             int cap_cand, int *parent, int *err) {
     __shared__ int3 qb[kPairCap];
-    __shared__ int nq, found, over;
+    __shared__ unsigned vol[2][32 * 32];   // [z][y] rows of 32 x-bits
+    __shared__ int nq, found, over, lo[3], hi[3];
     const int ncand = min(cnt[C_NCAND], cap_cand);
     for (int k = blockIdx.x; k < ncand; k += gridDim.x) {
         const int p = cand[2 * k], q = cand[2 * k + 1];
         const PInfo Pp = P[p], Pq = P[q];
         int sh[3];
         min_image_shift(Pp.xi, Pq.xi, dims, Pp.scene, sh);
-        if (threadIdx.x == 0) { nq = 0; found = 0; over = 0; }
+        if (threadIdx.x == 0) {
+            nq = 0; found = 0; over = 0;
+            lo[0] = lo[1] = lo[2] = INT_MAX;
+            hi[0] = hi[1] = hi[2] = INT_MIN;
+        }
         __syncthreads();
         const float rp = (float)(Pp.a + 3.0 * 1.7320508075688772 + 1.0);
         const float rq = (float)(Pq.a + 3.0 * 1.7320508075688772 + 1.0);
@@ -225,22 +235,60 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_test(const PInfo *P, cons
                 dd += v * v;
             }
             if (dd > rp * rp) continue;
-            int3 b;
+            int b[3];
             float fr;
-            b.x = marker_split32(Pq, t, t64 + 3ll * (Pq.toff + l), 0, &fr) + sh[0];
-            b.y = marker_split32(Pq, t, t64 + 3ll * (Pq.toff + l), 1, &fr) + sh[1];
-            b.z = marker_split32(Pq, t, t64 + 3ll * (Pq.toff + l), 2, &fr) + sh[2];
+            for (int c = 0; c < 3; ++c) {
+                b[c] = marker_split32(Pq, t, t64 + 3ll * (Pq.toff + l), c, &fr) + sh[c];
+                atomicMin(&lo[c], b[c]);
+                atomicMax(&hi[c], b[c]);
+            }
             const int i = atomicAdd(&nq, 1);
-            if (i < kPairCap) qb[i] = b;
+            if (i < kPairCap) qb[i] = make_int3(b[0], b[1], b[2]);
             else over = 1;
         }
         __syncthreads();
+        const int n = nq;
         if (over) {
             if (threadIdx.x == 0 && !uf_unite(parent, p, q)) set_err(err, IBM_EBIT_TIMEOUT);
             __syncthreads();
             continue;
         }
-        const int n = nq;
+        if (n == 0) {
+            __syncthreads();
+            continue;
+        }
+        const int o0 = lo[0] - 2, o1 = lo[1] - 2, o2 = lo[2] - 2;
+        const bool use_vol = hi[0] - o0 < 30 && hi[1] - o1 < 30 && hi[2] - o2 < 30;
+        if (use_vol) {
+            for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) vol[0][i] = 0u;
+            __syncthreads();
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                const int3 b = qb[j];
+                atomicOr(&vol[0][(b.z - o2) * 32 + (b.y - o1)], 1u << (b.x - o0));
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+                const unsigned w = vol[0][i];
+                vol[0][i] = w | (w << 1) | (w << 2) | (w >> 1) | (w >> 2);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+                const int z = i >> 5, y = i & 31;
+                unsigned w = 0u;
+                for (int d = -2; d <= 2; ++d)
+                    if (y + d >= 0 && y + d < 32) w |= vol[0][z * 32 + y + d];
+                vol[1][i] = w;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+                const int z = i >> 5, y = i & 31;
+                unsigned w = 0u;
+                for (int d = -2; d <= 2; ++d)
+                    if (z + d >= 0 && z + d < 32) w |= vol[1][(z + d) * 32 + y];
+                vol[0][i] = w;
+            }
+            __syncthreads();
+        }
         for (int l = threadIdx.x; l < Pp.nl && !found; l += blockDim.x) {
             const float *t = t32 + 3ll * (Pp.toff + l);
             float dd = 0.f;
@@ -253,11 +301,18 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_test(const PInfo *P, cons
             const int bx = marker_split32(Pp, t, t64 + 3ll * (Pp.toff + l), 0, &fr);
             const int by = marker_split32(Pp, t, t64 + 3ll * (Pp.toff + l), 1, &fr);
             const int bz = marker_split32(Pp, t, t64 + 3ll * (Pp.toff + l), 2, &fr);
-            for (int j = 0; j < n; ++j) {
-                const int3 b = qb[j];
-                if (abs(b.x - bx) <= 2 && abs(b.y - by) <= 2 && abs(b.z - bz) <= 2) {
+            if (use_vol) {
+                // the dilated volume covers every cell within 2 of a q base
+                const int x = bx - o0, y = by - o1, z = bz - o2;
+                if (x >= 0 && x < 32 && y >= 0 && y < 32 && z >= 0 && z < 32 && ((vol[0][z * 32 + y] >> x) & 1u))
                     found = 1;
-                    break;
+            } else {
+                for (int j = 0; j < n; ++j) {
+                    const int3 b = qb[j];
+                    if (abs(b.x - bx) <= 2 && abs(b.y - by) <= 2 && abs(b.z - bz) <= 2) {
+                        found = 1;
+                        break;
+                    }
                 }
             }
         }
