@@ -41,11 +41,12 @@
 
 namespace {
 
-constexpr int kCapP = 64;        // particles per shared-memory cluster
+constexpr int kCapP = 32;        // particles per shared-memory batch
 constexpr int kBuckets = 1024;   // work-order buckets
 constexpr int kPairThreads = 128;
 constexpr int kPairCap = 1024;   // near-marker list in the exact pair test
 constexpr int kUnionSpin = 1 << 22;
+constexpr int kSparseRows = 32768;   // box rows (y, z) of a cluster with a sparse row table
 
 enum {
     C_NCAND = 0,
@@ -156,46 +157,47 @@ __device__ __forceinline__ void min_image_shift(const double xp[3], const double
     }
 }
 
+// Candidate pairs: one thread per (particle, neighbouring bin) of the 3x3x3
+// bins around the particle's own (fewer where a scene has fewer bins).
 __global__ void k_candidates(int n_p, const PInfo *P, const int *scene_nb, const int *scene_bin_off,
                              const int32_t *dims, const int *bin_start, const int *bin_items, int *cand,
                              int cap_cand, int *cnt) {
     const float lim = 3.0f * 1.7320508f + 1e-3f;   // margin covers the FP32 rounding of the distance
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_p; p += gridDim.x * blockDim.x) {
-        const PInfo Pp = P[p];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 27ll * n_p;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(t / 27), o = (int)(t - 27ll * p);
+        const PInfo &Pp = P[p];
         const int s = Pp.scene;
+        const int nbx = scene_nb[3 * s], nby = scene_nb[3 * s + 1], nbz = scene_nb[3 * s + 2];
+        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+        // with fewer than 3 bins along an axis every bin is visited once
+        if ((nbx < 3 && ox + 1 >= nbx) || (nby < 3 && oy + 1 >= nby) || (nbz < 3 && oz + 1 >= nbz)) continue;
         int bc[3];
         scene_bin(scene_nb, scene_bin_off, dims, s, Pp.xi, bc);
-        const int nbx = scene_nb[3 * s], nby = scene_nb[3 * s + 1], nbz = scene_nb[3 * s + 2];
-        const int lox = nbx >= 3 ? -1 : 0, hix = nbx >= 3 ? 1 : nbx - 1;
-        const int loy = nby >= 3 ? -1 : 0, hiy = nby >= 3 ? 1 : nby - 1;
-        const int loz = nbz >= 3 ? -1 : 0, hiz = nbz >= 3 ? 1 : nbz - 1;
-        for (int oz = loz; oz <= hiz; ++oz)
-            for (int oy = loy; oy <= hiy; ++oy)
-                for (int ox = lox; ox <= hix; ++ox) {
-                    const int bx = (bc[0] + ox + nbx) % nbx, by = (bc[1] + oy + nby) % nby,
-                              bz = (bc[2] + oz + nbz) % nbz;
-                    const int b = scene_bin_off[s] + (bz * nby + by) * nbx + bx;
-                    for (int i = bin_start[b]; i < bin_start[b + 1]; ++i) {
-                        const int q = bin_items[i];
-                        if (q <= p) continue;
-                        const PInfo &Pq = P[q];
-                        int sh[3];
-                        min_image_shift(Pp.xi, Pq.xi, dims, s, sh);
-                        float d2 = 0.f;
-                        for (int c = 0; c < 3; ++c) {
-                            const float dv = (float)(Pq.xi[c] - Pp.xi[c]) + (float)sh[c];
-                            d2 += dv * dv;
-                        }
-                        const float r = Pp.af + Pq.af + lim;
-                        if (d2 < r * r) {
-                            const int k = atomicAdd(cnt + C_NCAND, 1);
-                            if (k < cap_cand) {
-                                cand[2 * k] = p;
-                                cand[2 * k + 1] = q;
-                            }
-                        }
-                    }
+        const int bx = nbx >= 3 ? (bc[0] + ox + nbx) % nbx : ox + 1;
+        const int by = nby >= 3 ? (bc[1] + oy + nby) % nby : oy + 1;
+        const int bz = nbz >= 3 ? (bc[2] + oz + nbz) % nbz : oz + 1;
+        const int b = scene_bin_off[s] + (bz * nby + by) * nbx + bx;
+        for (int i = bin_start[b]; i < bin_start[b + 1]; ++i) {
+            const int q = bin_items[i];
+            if (q <= p) continue;
+            const PInfo &Pq = P[q];
+            int sh[3];
+            min_image_shift(Pp.xi, Pq.xi, dims, s, sh);
+            float d2 = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                const float dv = (float)(Pq.xi[c] - Pp.xi[c]) + (float)sh[c];
+                d2 += dv * dv;
+            }
+            const float r = Pp.af + Pq.af + lim;
+            if (d2 < r * r) {
+                const int k = atomicAdd(cnt + C_NCAND, 1);
+                if (k < cap_cand) {
+                    cand[2 * k] = p;
+                    cand[2 * k + 1] = q;
                 }
+            }
+        }
     }
 }
 
@@ -396,7 +398,10 @@ __global__ void k_cluster_route(const long long *n_clust_d, const PInfo *P, cons
             ok = ok && ext <= n_k && 2 * cext < n_k;
             R *= (k == 0) ? (ext + 31) / 32 : ext;
         }
-        ok = ok && R <= max_rows;
+        // a dense row table over max_rows entries is replaced by a sparse one
+        // (rows numbered in 16 bits) in the kernel
+        const int nyz = (cl_box[12 * c + 4] - cl_box[12 * c + 1] + 1) * (cl_box[12 * c + 5] - cl_box[12 * c + 2] + 1);
+        ok = ok && (R <= max_rows || nyz <= kSparseRows);
         // bitmask entry decode words hold y, z < 1024 and 16 words (512 cells) per row
         ok = ok && (cl_box[12 * c + 4] - cl_box[12 * c + 1]) < 1023 && (cl_box[12 * c + 5] - cl_box[12 * c + 2]) < 1023 &&
              (cl_box[12 * c + 3] - cl_box[12 * c]) < 511;
@@ -589,7 +594,10 @@ __device__ __forceinline__ void rel_base(const PS &s, const float *t32, const do
     for (int c = 0; c < 3; ++c) b[c] = marker_split32(s.P, t, t6, c, &f[c]) + s.off[c];
 }
 
-__device__ __forceinline__ void row_slots(const uint2 *rt, int W, int By, const int b[3], int slot[9]) {
+// Slots of the nine row runs of a marker's stencil.  rix (sparse row table)
+// maps a box row to its compact row, nullptr for the dense table.
+__device__ __forceinline__ void row_slots(const uint2 *rt, const unsigned short *rix, int W, int By, const int b[3],
+                                          int slot[9]) {
     const int x = b[0] - 1;
     const int wx = x >> 5;
     const unsigned lowmask = (1u << (x & 31)) - 1u;
@@ -597,7 +605,8 @@ __device__ __forceinline__ void row_slots(const uint2 *rt, int W, int By, const 
     for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
-            const int row = (b[2] + dz - 1) * By + (b[1] + dy - 1);
+            const int r = (b[2] + dz - 1) * By + (b[1] + dy - 1);
+            const int row = rix ? (int)rix[r] : r;
             const uint2 e = rt[row * W + wx];
             slot[dz * 3 + dy] = (int)e.y + __popc(e.x & lowmask);
         }
@@ -621,6 +630,8 @@ __host__ __device__ constexpr int fixed_smem_bytes() {
 
 struct Batch {
     int nb, np, nm, R, C;
+    const unsigned short *rix;   // sparse row table: box row -> compact row (else nullptr)
+    const unsigned short *rowid; // sparse row table: compact row -> box row
 };
 
 
@@ -646,8 +657,9 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
         // entry -> (row, word) -> (ry, rz): exact small-integer divisions in FP32
         const float rW = __frcp_rn((float)W), rBy = __frcp_rn((float)By);
         auto row_base = [&](int li, int &wx) {
-            const int row = (int)(((float)li + 0.5f) * rW);
-            wx = li - row * W;
+            const int rc = (int)(((float)li + 0.5f) * rW);
+            wx = li - rc * W;
+            const int row = bt.rowid ? (int)bt.rowid[rc] : rc;
             const int rz = (int)(((float)row + 0.5f) * rBy);
             const int ry = row - rz * By;
             return ((long long)wrapi(z0 + rz, nz) * ny + wrapi(y0 + ry, ny)) * nx;
@@ -694,16 +706,22 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
 }
 
 // Marks the 3x3x3 stencil of a marker (box-relative base cell b) in its
-// cluster's row bitmask; false if the stencil leaves the box (never expected:
-// the box bounds every stencil of the cluster).
-__device__ __forceinline__ bool mark_stencil(uint2 *rt, const CS &cs, const int b[3]) {
-    if (b[0] < 1 || b[0] > cs.Bx - 2 || b[1] < 1 || b[1] > cs.By - 2 || b[2] < 1 || b[2] > cs.Bz - 2) return false;
+// cluster's row bitmask (rows through rix for the sparse table); false if the
+// stencil leaves the box (never expected: the box bounds every stencil of the
+// cluster).
+__device__ __forceinline__ bool in_box(const CS &cs, const int b[3]) {
+    return b[0] >= 1 && b[0] <= cs.Bx - 2 && b[1] >= 1 && b[1] <= cs.By - 2 && b[2] >= 1 && b[2] <= cs.Bz - 2;
+}
+
+__device__ __forceinline__ bool mark_stencil(uint2 *rt, const unsigned short *rix, const CS &cs, const int b[3]) {
+    if (!in_box(cs, b)) return false;
     const int x = b[0] - 1, wx = x >> 5, bit = x & 31;
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
-            const int row = (b[2] + dz) * cs.By + (b[1] + dy);
+            const int r = (b[2] + dz) * cs.By + (b[1] + dy);
+            const int row = rix ? (int)rix[r] : r;
             atomicOr(&rt[row * cs.W + wx].x, 7u << bit);
             if (bit > 29) atomicOr(&rt[row * cs.W + wx + 1].x, 7u >> (32 - bit));
         }
@@ -960,6 +978,87 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
     move_cells<TPB, NC, false>(prm, bt, s_cs, s_row, s_inv, s_u, q0);
 }
 
+template <class T>
+__device__ __forceinline__ T *align16_to(const void *q) {
+    return reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(q) + 15) & ~(uintptr_t)15);
+}
+
+// Sparse row table of a batch holding one large cluster, for when the dense
+// table (one entry per 32 cells of every row of the box) does not fit: the
+// box rows that some stencil reaches are numbered in order (rix: box row ->
+// compact row, rowid: the inverse) and only those get bitmask entries.  The
+// markers' base cells come from their records.  On return s_row points to the
+// compact entries and bt holds the tables; *flag is set when they do not fit.
+template <int TPB>
+__device__ __noinline__ void build_sparse_rows(CS *s_cs, const float4 *ra, int nm, uint2 *base, const unsigned char *dyn_end,
+                                  int *s_scan, int *flag, Batch &bt, uint2 *&s_row) {
+    const int tid = threadIdx.x;
+    CS &cs = s_cs[0];
+    const int By = cs.By, W = cs.W, nyz = cs.By * cs.Bz;
+    unsigned short *rix = reinterpret_cast<unsigned short *>(base);
+    unsigned *rbits = align16_to<unsigned>(rix + nyz);
+    const int nw = (nyz + 31) >> 5;
+    uint2 *rows = align16_to<uint2>(rbits + nw);
+    bool ok = !*flag && reinterpret_cast<const unsigned char *>(rows) + 16 <= dyn_end;   // uniform
+    int nrows = 0;
+    if (ok) {
+        for (int i = tid; i < nw; i += TPB) rbits[i] = 0u;
+        __syncthreads();
+        for (int m = tid; m < nm; m += TPB) {
+            const unsigned bp = __float_as_uint(ra[m].w);
+            if (bp == kNoMarker) continue;
+            const int b1 = (int)((bp >> 10) & 1023u), b2 = (int)(bp >> 20);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int r = (b2 + dz) * By + (b1 + dy);
+                    atomicOr(&rbits[r >> 5], 1u << (r & 31));
+                }
+        }
+        __syncthreads();
+        const int per = (nw + TPB - 1) / TPB;
+        const int lo = min(nw, tid * per), hi = min(nw, lo + per);
+        int sum = 0;
+        for (int i = lo; i < hi; ++i) sum += __popc(rbits[i]);
+        int run = block_excl_scan<TPB>(sum, s_scan, &nrows);
+        unsigned short *rowid = align16_to<unsigned short>(rows + nrows * W);
+        ok = reinterpret_cast<const unsigned char *>(rowid + nrows) + 16 <= dyn_end;   // uniform
+        if (ok) {
+            for (int i = lo; i < hi; ++i) {
+                unsigned bits = rbits[i];
+                while (bits) {
+                    const int r = 32 * i + __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    rix[r] = (unsigned short)run;
+                    rowid[run] = (unsigned short)r;
+                    ++run;
+                }
+            }
+            for (int i = tid; i < nrows * W; i += TPB) rows[i] = make_uint2(0u, 0u);
+            __syncthreads();
+            for (int m = tid; m < nm; m += TPB) {
+                const unsigned bp = __float_as_uint(ra[m].w);
+                if (bp == kNoMarker) continue;
+                const int b[3] = {(int)(bp & 1023u), (int)((bp >> 10) & 1023u), (int)(bp >> 20)};
+                mark_stencil(rows, rix, cs, b);
+            }
+            bt.rix = rix;
+            bt.rowid = rowid;
+        }
+    }
+    if (!ok) {
+        nrows = 0;
+        if (tid == 0) *flag = 1;
+    }
+    __syncthreads();
+    bt.R = nrows * W;
+    if (tid == 0) {
+        cs.row0 = 0;
+        cs.R = bt.R;
+    }
+    __syncthreads();
+    s_row = rows;
+}
+
 // Persistent CTAs (MINB per SM).  KM: markers per thread of a batch (at most
 // TPB KM markers, one component at a time; TPB KM / 3 with all three); KR:
 // markers per thread when the records stay in shared memory.  DET =
@@ -973,7 +1072,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
     CS *s_cs = reinterpret_cast<CS *>(s_ps + kCapP);
     float *s_part = reinterpret_cast<float *>(s_cs + kCapCl);            // [NCH][6]
     unsigned char *s_chunk = reinterpret_cast<unsigned char *>(s_part + NCH * 6);   // [NCH] chunk -> particle
-    uint2 *s_row = reinterpret_cast<uint2 *>(smem + fixed_smem_bytes<TPB, KM>());   // [R] then the cells
+    uint2 *const s_row0 = reinterpret_cast<uint2 *>(smem + fixed_smem_bytes<TPB, KM>());   // [R] then the cells
     unsigned char *dyn_end = smem + prm.smem_bytes;
     __shared__ int s_w, s_np, s_nm, s_R, s_flag, s_scan[32], s_total;
     const int tid = threadIdx.x;
@@ -1022,7 +1121,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
             bt.nb = nbl;
             bt.np = s_np;
             bt.R = s_R;
+            bt.rix = nullptr;
+            bt.rowid = nullptr;
             const int np = bt.np;
+            // a single cluster whose dense row table is too large gets a sparse one
+            const bool sparse = bt.nb == 1 && bt.R > prm.max_rows;
+            uint2 *s_row = s_row0;
             // particle table, sorted by global index (fixed marker numbering)
             if (tid < np) {
                 const int j = [&] {
@@ -1052,7 +1156,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                 s_ps[tid].off[1] = prm.poff[3 * p + 1] - cs.y0;
                 s_ps[tid].off[2] = prm.poff[3 * p + 2] - cs.z0;
             }
-            for (int i = tid; i < bt.R; i += TPB) s_row[i].x = 0u;
+            if (!sparse)
+                for (int i = tid; i < bt.R; i += TPB) s_row[i].x = 0u;
             __syncthreads();
             if (tid == 0) {
                 int m = 0;
@@ -1084,7 +1189,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
             uint4 *const s_rb = reinterpret_cast<uint4 *>(dyn_end - rec_bytes / 2);
             float4 *const g_ra = prm.grec + (size_t)blockIdx.x * (2 * TPB * KM);
             uint4 *const g_rb = reinterpret_cast<uint4 *>(g_ra + TPB * KM);
-            const bool rec_smem = nm <= TPB * KR &&
+            const bool rec_smem = !sparse && nm <= TPB * KR &&
                                   reinterpret_cast<unsigned char *>(s_row + bt.R) + 16 <= dyn_end - rec_bytes;
             float4 *const ra0 = rec_smem ? s_ra : g_ra;
             for (int m = tid; m < nm; m += TPB) {
@@ -1098,15 +1203,18 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                 float f[3];
                 rel_base(s, prm.t32, prm.t64, l, b, f);
                 const CS &cs = s_cs[s.cl];
-                if (!mark_stencil(s_row + cs.row0, cs, b)) s_flag = 1;
+                if (!sparse && !mark_stencil(s_row + cs.row0, nullptr, cs, b)) s_flag = 1;
+                if (sparse && !in_box(cs, b)) s_flag = 1;
                 ra0[m] = make_float4(f[0], f[1], f[2],
                                      __uint_as_float((unsigned)b[0] | ((unsigned)b[1] << 10) | ((unsigned)b[2] << 20)));
             }
             __syncthreads();
+            if (sparse)
+                build_sparse_rows<TPB>(s_cs, ra0, nm, s_row0, dyn_end, s_scan, &s_flag, bt, s_row);
             // 2. compact slots: exclusive prefix of the popcounts over all rows, then
             // each cluster's slots shifted to start at a multiple of 4 (so that the
             // per-cluster passes over the cells can use 16-byte accesses)
-            {
+            auto slot_prefix = [&]() {
                 const int per = (bt.R + TPB - 1) / TPB;
                 const int lo = min(bt.R, tid * per), hi = min(bt.R, lo + per);
                 int sum = 0;
@@ -1147,25 +1255,53 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                     for (int i = s_cs[j].row0 + tid; i < r1; i += TPB)
                         if (s_row[i].x) s_row[i].y += sh;
                 }
-            }
-            __syncthreads();
-            bt.C = s_total;
+                __syncthreads();
+                bt.C = s_total;
+            };
+            slot_prefix();
+            // the row structures end before the slot table and the cells
+            auto rows_end = [&]() {
+                return bt.rowid ? reinterpret_cast<const void *>(bt.rowid + bt.R / s_cs[0].W)
+                                : reinterpret_cast<const void *>(s_row + bt.R);
+            };
             // cells go right after the row table, or after a slot -> entry table when
             // that fits too (it lets the gather/writeback run one thread per cell)
             auto align16 = [](const void *q) {
                 return reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(q) + 15) & ~(uintptr_t)15);
             };
-            float *const u_plain = align16(s_row + bt.R);
-            const int cap_cells = (int)((dyn_end - reinterpret_cast<unsigned char *>(u_plain)) / 4);
+            auto cells_cap = [&]() {
+                return (int)((dyn_end - reinterpret_cast<unsigned char *>(align16(rows_end()))) / 4);
+            };
+            if (!sparse && !rec_smem && !s_flag && bt.nb == 1 && bt.C > cells_cap()) {
+                // a single large cluster whose dense row table leaves too little room:
+                // rebuild it sparse from the records (in global memory) and redo the slots
+                build_sparse_rows<TPB>(s_cs, ra0, nm, s_row0, dyn_end, s_scan, &s_flag, bt, s_row);
+                slot_prefix();
+            }
+            float *const u_plain = align16(rows_end());
+            const int cap_cells = cells_cap();
             const bool three = 3 * bt.C <= cap_cells && nm <= TPB * (KM / 3);
             // records stay in shared memory (below them the cells) if all fits
             const bool use_rec = rec_smem && three && 3 * bt.C + rec_bytes / 4 <= cap_cells;
             float4 *const ra = use_rec ? s_ra : g_ra;
             uint4 *const rb = use_rec ? s_rb : g_rb;
             const int need = use_rec ? 3 * bt.C + rec_bytes / 4 : (three ? 3 * bt.C : bt.C);
-            unsigned short *s_inv = reinterpret_cast<unsigned short *>(s_row + bt.R);
+            if (s_flag || bt.C > cap_cells || nm > TPB * KM) {
+                // does not fit even one component at a time: hand it to the plain path
+                if (tid == 0) {
+                    int np_fb = 0;
+                    for (int j = 0; j < bt.nb; ++j) np_fb += s_cs[j].np;
+                    const int k0 = atomicAdd(prm.cnt + C_NFB, np_fb);
+                    atomicAdd(prm.cnt + C_FBMARK, nm);
+                    atomicAdd(prm.cnt + C_OVERFLOW, bt.nb);
+                    for (int i = 0; i < np; ++i) prm.fb_list[k0 + i] = s_ps[i].gid;
+                }
+                __syncthreads();
+                continue;
+            }
+            unsigned short *s_inv = reinterpret_cast<unsigned short *>(align16(rows_end()));
             float *const u_inv = align16(s_inv + bt.C);
-            const bool use_inv = (int)((dyn_end - reinterpret_cast<unsigned char *>(u_inv)) / 4) >= need;
+            const bool use_inv = bt.R < 0xffff && (int)((dyn_end - reinterpret_cast<unsigned char *>(u_inv)) / 4) >= need;
             float *s_u = use_inv ? u_inv : u_plain;
             if (use_inv) {
                 for (int i = tid; i < bt.C; i += TPB) s_inv[i] = 0xffffu;
@@ -1190,7 +1326,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                     const CS &cs = s_cs[s_ps[s_chunk[m >> 5]].cl];
                     const int b[3] = {(int)(bp & 1023u), (int)((bp >> 10) & 1023u), (int)(bp >> 20)};
                     int sl[9];
-                    row_slots(s_row + cs.row0, cs.W, cs.By, b, sl);
+                    row_slots(s_row + cs.row0, bt.rix, cs.W, cs.By, b, sl);
                     rb[m] = make_uint4((unsigned)sl[0] | ((unsigned)sl[1] << 16), (unsigned)sl[2] | ((unsigned)sl[3] << 16),
                                        (unsigned)sl[4] | ((unsigned)sl[5] << 16), (unsigned)sl[6] | ((unsigned)sl[7] << 16));
                     a.w = __uint_as_float((unsigned)sl[8]);
@@ -1198,19 +1334,6 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                 ra[m] = a;
             }
             __syncthreads();
-            if (s_flag || bt.C > cap_cells || nm > TPB * KM) {
-                // does not fit even one component at a time: hand it to the plain path
-                if (tid == 0) {
-                    int np_fb = 0;
-                    for (int j = 0; j < bt.nb; ++j) np_fb += s_cs[j].np;
-                    const int k0 = atomicAdd(prm.cnt + C_NFB, np_fb);
-                    atomicAdd(prm.cnt + C_FBMARK, nm);
-                    atomicAdd(prm.cnt + C_OVERFLOW, bt.nb);
-                    for (int i = 0; i < np; ++i) prm.fb_list[k0 + i] = s_ps[i].gid;
-                }
-                __syncthreads();
-                continue;
-            }
             if (tid == 0) {
                 int touched = 0;
                 for (int j = 0; j < bt.nb; ++j) touched += s_cs[j].ncell;
@@ -1412,8 +1535,8 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     k_scan1<<<1, 1024, 0, sm>>>(S->bin_cnt, S->bin_start, S->nbins, S->tot);
     k_bin_fill<<<gb, 256, 0, sm>>>(n, ctx->pinfo, S->scene_nb, S->scene_bin_off, ctx->dims_d, S->bin_start,
                                    S->bin_cur, S->bin_items);
-    k_candidates<<<gb, 256, 0, sm>>>(n, ctx->pinfo, S->scene_nb, S->scene_bin_off, ctx->dims_d, S->bin_start,
-                                     S->bin_items, S->cand, S->cap_cand, S->cnt);
+    k_candidates<<<grid_for(27ll * n, 256), 256, 0, sm>>>(n, ctx->pinfo, S->scene_nb, S->scene_bin_off, ctx->dims_d,
+                                                         S->bin_start, S->bin_items, S->cand, S->cap_cand, S->cnt);
     k_pair_test<<<std::min(S->cap_cand, 152 * 16), kPairThreads, 0, sm>>>(
         ctx->pinfo, ctx->tmpl32, ctx->tmpl64, ctx->dims_d, S->cand, S->cnt, S->cap_cand, S->parent, ctx->err_d);
     k_roots<<<gb, 256, 0, sm>>>(n, S->parent, S->root_flag, ctx->err_d);

@@ -91,7 +91,7 @@ static void free_all(ibm_ctx *ctx) {
     void *ptrs[] = {ctx->dims_d, ctx->x, ctx->up, ctx->om, ctx->d, ctx->rho, ctx->scene,
                     ctx->nl, ctx->moff, ctx->toff, ctx->pinfo, ctx->tmpl64, ctx->tmpl32,
                     ctx->tmpl_of_nl, ctx->FD, ctx->TD, ctx->Fout, ctx->Tout, ctx->x_new,
-                    ctx->u_new, ctx->om_new, ctx->slip_acc, ctx->ebuf, ctx->e_hist,
+                    ctx->u_new, ctx->om_new, ctx->slip_acc, ctx->ebuf, ctx->e_hist, ctx->cbuf,
                     ctx->gu_hist, ctx->gmk, ctx->err_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -71,6 +71,8 @@ struct ibm_ctx {
 
     // loads / state outputs (device FP64)
     double *FD = nullptr, *TD = nullptr;     // sum e*D, sum r x e*D (per particle)
+    double *cbuf = nullptr;                  // plain path: per-(particle, chunk) load sums
+    size_t cbuf_cap = 0;
     double *Fout = nullptr, *Tout = nullptr; // F_p, T_p in physical units
     double *x_new = nullptr, *u_new = nullptr, *om_new = nullptr;
     double *slip_acc = nullptr;              // [2]

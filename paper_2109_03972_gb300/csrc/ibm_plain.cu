@@ -238,16 +238,16 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
     const PInfo *__restrict__ P, const int *__restrict__ plist, int n_list, const int *__restrict__ n_list_d,
     const double *__restrict__ t64, const float *__restrict__ t32, const double *__restrict__ up,
     const double *__restrict__ om, const int32_t *__restrict__ dims, T *const *uf, T *__restrict__ ebuf,
-    double *FD, double *TD) {
+    double *__restrict__ cbuf) {
     __shared__ double sh[6][32];
     if (n_list_d) n_list = *n_list_d;
-    for (int k = blockIdx.x; k < n_list; k += gridDim.x) {
+    for (int k = blockIdx.y; k < n_list; k += gridDim.y) {
         const int p = plist ? plist[k] : k;
         const PInfo Pp = P[p];
         const Grid g = scene_grid(dims, Pp.scene);
         const T *__restrict__ u = uf[Pp.scene];
         double acc[6] = {0, 0, 0, 0, 0, 0};
-        for (int l = threadIdx.x; l < Pp.nl; l += blockDim.x) {
+        for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Pp.nl; l += gridDim.x * blockDim.x) {
             const double *tt64 = t64 + 3ll * (Pp.toff + l);
             const float *tt32 = t32 + 3ll * (Pp.toff + l);
             Stencil<T> S;
@@ -291,12 +291,9 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
             acc[5] += rd[0] * ed[1] - rd[1] * ed[0];
         }
         block_sum<6>(acc, sh);
-        if (threadIdx.x == 0) {
-            for (int q = 0; q < 3; ++q) {
-                FD[3 * p + q] += acc[q];
-                TD[3 * p + q] += acc[3 + q];
-            }
-        }
+        // this chunk's partial sums; the spreading kernel adds the chunks in order
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 6; ++q) cbuf[(6ll * k) * gridDim.x + 6 * blockIdx.x + q] = acc[q];
     }
 }
 
@@ -306,15 +303,23 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_plain_spread(
     const PInfo *__restrict__ P, const int *__restrict__ plist, int n_list, const int *__restrict__ n_list_d,
     const double *__restrict__ t64, const float *__restrict__ t32, const int32_t *__restrict__ dims,
-    const T *__restrict__ vbuf, T scale, T *const *uf, T *const *ff, T finv) {
+    const T *__restrict__ vbuf, T scale, T *const *uf, T *const *ff, T finv, const double *__restrict__ cbuf,
+    double *FD, double *TD) {
     if (n_list_d) n_list = *n_list_d;
-    for (int k = blockIdx.x; k < n_list; k += gridDim.x) {
+    for (int k = blockIdx.y; k < n_list; k += gridDim.y) {
         const int p = plist ? plist[k] : k;
         const PInfo Pp = P[p];
         const Grid g = scene_grid(dims, Pp.scene);
         T *u = uf[Pp.scene];
         T *f = ff ? ff[Pp.scene] : nullptr;
-        for (int l = threadIdx.x; l < Pp.nl; l += blockDim.x) {
+        if (cbuf && blockIdx.x == 0 && threadIdx.x < 6) {
+            // the particle's loads of this iteration: its chunks' sums, in order
+            double s = 0.0;
+            for (int c = 0; c < (int)gridDim.x; ++c) s += cbuf[(6ll * k) * gridDim.x + 6 * c + threadIdx.x];
+            if (threadIdx.x < 3) FD[3 * p + threadIdx.x] += s;
+            else TD[3 * p + threadIdx.x - 3] += s;
+        }
+        for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Pp.nl; l += gridDim.x * blockDim.x) {
             const double *tt64 = t64 + 3ll * (Pp.toff + l);
             const float *tt32 = t32 + 3ll * (Pp.toff + l);
             Stencil<T> S;
@@ -766,28 +771,51 @@ ibm_status launch_marker_bases(ibm_ctx *ctx, int64_t *base_d) {
     return ibm_cuda_check(ctx, cudaGetLastError(), "marker bases");
 }
 
+// Grid of the plain kernels: y = particles of the list (grid-stride), x =
+// blocks sharing one particle's markers.  About 16 blocks per SM in all; a
+// whole bed has enough particles for one block each, a short list (the
+// clusters the shared-memory kernel cannot hold, counted on the device) splits
+// each particle into chunks of kBlock markers.
+static dim3 chunk_grid(const ibm_ctx *ctx, int n_list, bool count_on_device = false) {
+    const int gx = count_on_device ? std::max(1, (ctx->max_nl + kBlock - 1) / kBlock) : 1;
+    const int gy = std::max(1, std::min(n_list, 152 * 16 / gx));
+    return dim3((unsigned)gx, (unsigned)gy);
+}
+
 // One plain iteration over the particles in plist (all when plist == NULL).
 template <typename T>
-static void plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
-                            bool with_f) {
-    const int nb = blocks_for_particles(n_list);
+static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
+                                  bool with_f) {
+    const dim3 grid = chunk_grid(ctx, n_list, n_list_d != nullptr);
+    const size_t need = (size_t)std::max(1, n_list) * grid.x * 6 * sizeof(double);
+    if (ctx->cbuf_cap < need) {
+        if (ctx->cbuf) cudaFree(ctx->cbuf);
+        ctx->cbuf = nullptr;
+        ctx->cbuf_cap = 0;
+        CK(cudaMalloc(&ctx->cbuf, need), "alloc chunk sums");
+        ctx->cbuf_cap = need;
+    }
     T *const *uf = reinterpret_cast<T *const *>(ctx->uptr_d);
     T *const *ff = with_f ? reinterpret_cast<T *const *>(ctx->fptr_d) : nullptr;
-    k_plain_interp<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
-                                                      ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, uf,
-                                                      reinterpret_cast<T *>(ctx->ebuf), ctx->FD, ctx->TD);
-    k_plain_spread<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
-                                                      ctx->tmpl32, ctx->dims_d,
-                                                      reinterpret_cast<const T *>(ctx->ebuf), T(1), uf, ff,
-                                                      T(1.0 / tau));
+    k_plain_interp<T><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
+                                                        ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, uf,
+                                                        reinterpret_cast<T *>(ctx->ebuf), ctx->cbuf);
+    k_plain_spread<T><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
+                                                        ctx->tmpl32, ctx->dims_d,
+                                                        reinterpret_cast<const T *>(ctx->ebuf), T(1), uf, ff,
+                                                        T(1.0 / tau), ctx->cbuf, ctx->FD, ctx->TD);
     ctx->launches += 2;
+    return IBM_OK;
 }
 
 // FP32 plain iterations over a particle list whose length is n_list, or, when
 // n_list_d is given, the device value *n_list_d (at most n_list).
 ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
                                 bool with_f, int n_it) {
-    for (int it = 0; it < n_it; ++it) plain_iteration<float>(ctx, plist, n_list, n_list_d, tau, with_f);
+    for (int it = 0; it < n_it; ++it) {
+        const ibm_status st = plain_iteration<float>(ctx, plist, n_list, n_list_d, tau, with_f);
+        if (st != IBM_OK) return st;
+    }
     return ibm_cuda_check(ctx, cudaGetLastError(), "plain iteration");
 }
 
@@ -796,10 +824,9 @@ ibm_status plain_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, voi
     if (s != IBM_OK) return s;
     prof_begin(ctx);
     for (int it = 0; it < ctx->cfg.n_forcing; ++it) {
-        if (ctx->cfg.precision == IBM_FP64)
-            plain_iteration<double>(ctx, nullptr, ctx->n_p, nullptr, tau, f_out != nullptr);
-        else
-            plain_iteration<float>(ctx, nullptr, ctx->n_p, nullptr, tau, f_out != nullptr);
+        s = ctx->cfg.precision == IBM_FP64 ? plain_iteration<double>(ctx, nullptr, ctx->n_p, nullptr, tau, f_out != nullptr)
+                                           : plain_iteration<float>(ctx, nullptr, ctx->n_p, nullptr, tau, f_out != nullptr);
+        if (s != IBM_OK) return s;
     }
     prof_end(ctx);
     return ibm_cuda_check(ctx, cudaGetLastError(), "plain forcing step");
@@ -871,9 +898,9 @@ static ibm_status backward_impl(ibm_ctx *ctx, void *const *grad_u_out, void *con
         k_bw_fwd<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32, ctx->up, ctx->om,
                                                     ctx->dims_d, reinterpret_cast<T *const *>(ctx->uptr_d), hinv,
                                                     e_m, g_m);
-        k_plain_spread<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, nullptr, ctx->n_p, nullptr, ctx->tmpl64,
-                                                          ctx->tmpl32, ctx->dims_d, e_m, T(1),
-                                                          reinterpret_cast<T *const *>(ctx->uptr_d), nullptr, T(0));
+        k_plain_spread<T><<<chunk_grid(ctx, ctx->n_p), kBlock, 0, ctx->stream>>>(
+            ctx->pinfo, nullptr, ctx->n_p, nullptr, ctx->tmpl64, ctx->tmpl32, ctx->dims_d, e_m, T(1),
+            reinterpret_cast<T *const *>(ctx->uptr_d), nullptr, T(0), nullptr, nullptr, nullptr);
     }
     // reverse sweep on the gradient field
     st = ensure_field_ptrs(ctx, grad_u_in, nullptr);
@@ -884,10 +911,10 @@ static ibm_status backward_impl(ibm_ctx *ctx, void *const *grad_u_out, void *con
         k_bw_adj<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32, ctx->dims_d,
                                                     reinterpret_cast<T *const *>(ctx->uptr_d), hinv, e_m, g_m,
                                                     reinterpret_cast<T *>(ctx->ebuf), reinterpret_cast<double *>(ctx->gmk));
-        k_plain_spread<T><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, nullptr, ctx->n_p, nullptr, ctx->tmpl64,
-                                                          ctx->tmpl32, ctx->dims_d,
-                                                          reinterpret_cast<const T *>(ctx->ebuf), T(-1),
-                                                          reinterpret_cast<T *const *>(ctx->uptr_d), nullptr, T(0));
+        k_plain_spread<T><<<chunk_grid(ctx, ctx->n_p), kBlock, 0, ctx->stream>>>(
+            ctx->pinfo, nullptr, ctx->n_p, nullptr, ctx->tmpl64, ctx->tmpl32, ctx->dims_d,
+            reinterpret_cast<const T *>(ctx->ebuf), T(-1), reinterpret_cast<T *const *>(ctx->uptr_d), nullptr, T(0),
+            nullptr, nullptr, nullptr);
     }
     k_bw_reduce<<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64,
                                                 reinterpret_cast<const double *>(ctx->gmk), gU, gOmega, gX);

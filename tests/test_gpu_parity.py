@@ -299,6 +299,37 @@ def test_large_cluster_one_component_path(oracle_mod, mode):
     assert load_err(got["T"], ref["T"], 0.5 * sc.d_p * ref["Fabs"]) <= LOAD_TOL32
 
 
+def _diagonal_chain_scene():
+    # Fourteen D=12 spheres at the minimum gap along the (0, 1, 1) diagonal: one
+    # cluster whose box has ~136 x 136 rows, too many for a dense row table
+    # beside its cells, so the kernel numbers only the rows its stencils reach.
+    dims = (40, 256, 256)
+    n = 14
+    d = np.full(n, 12.0)
+    step = np.array([0.0, 1.0, 1.0]) / np.sqrt(2.0) * 13.0
+    x = np.array([20.3, 30.1, 28.7]) + np.arange(n)[:, None] * step
+    u_p, om, rho = synth.particle_state(n, 31)
+    return synth.Scene(dims, x, d, u_p, om, rho, field_seed=37)
+
+
+@pytest.mark.parametrize("mode", [ibm.IBM_SPREAD_CLUSTER, ibm.IBM_SPREAD_DETERMINISTIC])
+def test_elongated_cluster_sparse_rows(oracle_mod, mode):
+    sc = _diagonal_chain_scene()
+    # dense table: (x words) * (y rows) * (z rows) of the stencil box, far above
+    # what fits in shared memory beside the cells
+    ext = np.floor(sc.x_p + 0.5 * sc.d_p[:, None]).max(0) - np.floor(sc.x_p - 0.5 * sc.d_p[:, None]).min(0) + 3
+    assert ((ext[0] + 31) // 32) * ext[1] * ext[2] > 16000
+    u0 = f32_round(sc.field())
+    ref = _oracle_run(oracle_mod, sc, u0)
+    got = run_gpu(sc, u0, ibm.IBM_FP32, mode)
+    st = got["ctx"].stats()
+    assert st["clusters"] == 1 and st["markers_fallback"] == 0
+    assert st["touched_cells"] == oracle_mod.touched_count(sc.dims, sc.x_p, sc.d_p)
+    assert rel_err_u(got["u"], ref["u"], u0) <= U_TOL32
+    assert load_err(got["F"], ref["F"], ref["Fabs"]) <= LOAD_TOL32
+    assert load_err(got["T"], ref["T"], 0.5 * sc.d_p * ref["Fabs"]) <= LOAD_TOL32
+
+
 @pytest.mark.parametrize("name", ["small", "single64", "chain"])
 def test_touched_cells_match_oracle(oracle_mod, name):
     sc = SCENES[name]()
