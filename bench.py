@@ -33,6 +33,9 @@ WORKLOAD_DESC = {
     "bidisperse": "bidisperse bed: periodic 512x512x1024, 12000 spheres D=12h + 1500 D=24h, n_F=3, FP32",
     "mono": "monodisperse bed: periodic 256x256x512, 2000 spheres D=16h, n_F=3, FP32",
     "single64": "single sphere D=16h in a periodic 64^3 grid, n_F=3, FP32",
+    "diff128": "differentiation workload: periodic 128^3, 150 spheres D=16h, n_F=3, FP32",
+    "batched": "batched scenes: 512 periodic boxes, edge in {32,48,64,96,128}, 1-40 spheres each, "
+               "D ~ U[8,20]h, n_F=3, FP32, all scenes in one persistent launch per step",
 }
 KERNEL_SOURCES = ["paper_2109_03972_gb300/csrc/ibm_cluster.cu", "paper_2109_03972_gb300/csrc/ibm_device.cuh"]
 
@@ -45,7 +48,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bidisperse", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--mode", default="deterministic", choices=["cluster", "deterministic", "plain"])
-    ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = default)")
+    ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = default, -1 = autotune)")
+    ap.add_argument("--graph", action="store_true", help="replay the step from a CUDA graph")
+    ap.add_argument("--backward", action="store_true",
+                    help="also time forward + adjoint (ibm_backward) steps, FP32 and FP64")
     ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
     ap.add_argument("--e2e-steps", type=int, default=5)
     return ap.parse_args()
@@ -243,10 +249,11 @@ def our_arm(args):
             "plain": ibm.IBM_SPREAD_PLAIN}[args.mode]
     cfg = ibm.Config(dims=dims, n_forcing=W.n_forcing, precision=ibm.IBM_FP32, spread_mode=mode,
                      max_particles=n_p, newton_euler=True, rho_f=W.rho_f, g=W.g, profile=True,
-                     threads_per_block=args.threads)
+                     threads_per_block=args.threads, use_graph=args.graph)
     stream = torch.cuda.current_stream()
     ctx = ibm.Context(cfg, stream)
     ctx.set_particles(x, up, om, d, rho, so if len(dims) > 1 else None)
+
     us = [t.cuda() for t in u_host]
     for _ in range(args.warmup):
         ctx.forcing_step(us, W.tau)
@@ -272,9 +279,22 @@ def our_arm(args):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    k_ms, k_n = ctx.kernel_timing(reset=True)
-    k_avg = k_ms / max(1, k_n)
     stats = ctx.stats()
+    kctx = ctx
+    if args.graph:
+        # graph replays record no kernel events: time the kernel on an eager twin
+        # context running the same variant
+        kcfg = ibm.Config(**{**cfg.__dict__, "use_graph": False,
+                             "threads_per_block": stats["threads_per_block"]})
+        kctx = ibm.Context(kcfg, stream)
+        kctx.set_particles(x, up, om, d, rho, so if len(dims) > 1 else None)
+        kctx.forcing_step(us, W.tau)
+        kctx.kernel_timing(reset=True)
+        for _ in range(min(args.steps, 20)):
+            kctx.forcing_step(us, W.tau)
+        torch.cuda.synchronize()
+    k_ms, k_n = kctx.kernel_timing(reset=True)
+    k_avg = k_ms / max(1, k_n)
     value = world * n_mark * W.n_forcing / (ms / 1e3)
 
     peaks, peak_kind = measured_peaks()
@@ -300,7 +320,9 @@ def our_arm(args):
                        "spread_mode": args.mode, "n_forcing": W.n_forcing,
                        "l2": "inputs larger than L2 (u field %.1f GB, touched cells %.0f MB)" % (
                            sum(t.numel() for t in us) * 4 / 1e9, touched * 12 / 1e6),
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "cuda_graph": bool(args.graph), "threads_per_block": stats["threads_per_block"],
+                       "scenes": len(dims)},
             "roofline": roofline,
             "hbm_gbs_algorithmic_step": alg_bytes / (ms / 1e3) / 1e9,
             "slip": {"rms": slip[0], "max": slip[1], "after": "one step from the initial field"},
@@ -363,12 +385,54 @@ def our_arm(args):
                 "value": nm_cpu * W.n_forcing / (cms / 1e3), "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": f"particles with centres in a {S}^3 sub-box of the bed ({scene.n_p} spheres, "
                           f"{nm_cpu} markers) on a periodic {S}^3 grid; 3 steps, {cms:.0f} ms/step"}
+    if args.backward:
+        line["backward"] = backward_leg(args, W, dims, (x, up, om, d, rho, so), fields64, stream)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def backward_leg(args, W, dims, parts, fields64, stream):
+    """Forward step with requires_grad plus ibm_backward, timed per step with CUDA
+    events (loss L = 1/2 sum w |u|^2, so dL/du^{n_F} = w u), FP32 (plain spreading,
+    as the adjoint kernels) and the FP64 plain form."""
+    import torch
+    from paper_2109_03972_gb300 import ibm, synth
+    x, up, om, d, rho, so = parts
+    out = {"what": "one forcing step (requires_grad) + ibm_backward to du0, dU_p, dw_p, dx_p"}
+    for name, prec, dt in (("fp32", ibm.IBM_FP32, torch.float32), ("fp64", ibm.IBM_FP64, torch.float64)):
+        cfg = ibm.Config(dims=dims, n_forcing=W.n_forcing, precision=prec, spread_mode=ibm.IBM_SPREAD_PLAIN,
+                         max_particles=len(d), requires_grad=True)
+        ctx = ibm.Context(cfg, stream)
+        ctx.set_particles(x, up, om, d, rho, so if len(dims) > 1 else None)
+        u0 = [torch.from_numpy(f).to(device="cuda", dtype=dt) for f in fields64]
+        w = [torch.from_numpy(synth.loss_weights(dd, 7 + i)).to(device="cuda", dtype=dt)[None]
+             for i, dd in enumerate(dims)]
+        us = [t.clone() for t in u0]
+
+        def one():
+            for dst, src in zip(us, u0):
+                dst.copy_(src)
+            ctx.forcing_step(us, W.tau)
+            ctx.backward([wi * ui for wi, ui in zip(w, us)])
+
+        for _ in range(3):
+            one()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = max(3, min(args.steps, 50))
+        e0.record(stream)
+        for _ in range(n):
+            one()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_ms_per_step"] = e0.elapsed_time(e1) / n
+        del ctx, us, u0
+    out["speedup_fp32_vs_fp64"] = out["fp64_ms_per_step"] / out["fp32_ms_per_step"]
+    return out
 
 
 def main():

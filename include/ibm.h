@@ -80,8 +80,22 @@ typedef struct {
     double g[3];             /* gravity vector (Newton-Euler only)             */
     int max_particles;       /* capacity of the context                        */
     int requires_grad;       /* 1: keep what ibm_backward needs                */
-    int threads_per_block;   /* 0 = default (1024); else 512 or 1024 (CLUSTER)  */
+    int threads_per_block;   /* cluster kernel (CLUSTER, DETERMINISTIC): 0 =
+                                1024 threads, one CTA per SM; 512 = two
+                                512-thread CTAs per SM; -1 = autotune: the
+                                first step warms up, the next two time the
+                                two variants (with a host sync each), the
+                                faster is kept for the context's lifetime   */
     int profile;             /* 1: time the main forcing kernel with CUDA events */
+    int use_graph;           /* 1: ibm_forcing_step calls without slip_out (and
+                                without requires_grad) are replayed from a CUDA
+                                graph: a call runs eagerly while its field
+                                pointers, tau, sizes or buffers are new, the
+                                next call with the same ones captures the step
+                                (stream capture on the context's stream, which
+                                must not be captured by the caller) and later
+                                ones replay it.  The results are those of the
+                                eager step.                                   */
 } ibm_config;
 
 typedef struct ibm_ctx ibm_ctx;

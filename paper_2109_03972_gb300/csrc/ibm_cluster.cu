@@ -1519,7 +1519,10 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     ClusterScratch *S = reinterpret_cast<ClusterScratch *>(ctx->cl);
     const int n = ctx->n_p;
     cudaStream_t sm = ctx->stream;
-    const int tpb = ctx->cfg.threads_per_block ? ctx->cfg.threads_per_block : 1024;
+    // kernel variant: fixed, or autotuned over the first steps (see ibm_config)
+    const int req = ctx->cfg.threads_per_block;
+    const bool tuning = req < 0 && ctx->tune_step < 3;
+    const int tpb = req > 0 ? req : (req == 0 ? 1024 : (tuning ? (ctx->tune_step == 2 ? 512 : 1024) : ctx->tuned_tpb));
     const int cap_m = tpb * markers_per_thread(tpb);
     // row table may take at most half of the dynamic shared memory
     const int max_rows = (max_dyn_smem(ctas_per_sm(tpb)) - fixed_smem_bytes<1024, 12>()) / 16;
@@ -1585,6 +1588,12 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prm.n_forcing = ctx->cfg.n_forcing;
     prm.finv = (float)(1.0 / tau);
     prof_begin(ctx);
+    cudaEvent_t tev[2] = {nullptr, nullptr};
+    if (tuning && ctx->tune_step > 0) {
+        CK(cudaEventCreate(&tev[0]), "tuning event");
+        CK(cudaEventCreate(&tev[1]), "tuning event");
+        CK(cudaEventRecord(tev[0], sm), "tuning event");
+    }
     const bool det = ctx->cfg.spread_mode == IBM_SPREAD_DETERMINISTIC;
     if (tpb == 1024)
         st = det ? launch_cluster_kernel<1024, 12, 2, true, 1>(ctx, S, prm)
@@ -1593,12 +1602,41 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
         st = det ? launch_cluster_kernel<512, 12, 2, true, 2>(ctx, S, prm)
                  : launch_cluster_kernel<512, 12, 2, false, 2>(ctx, S, prm);
     prof_end(ctx);
+    if (tev[0]) {
+        // tuning step: time this variant (host sync), keep the faster after both
+        float ms = 0.f;
+        cudaEventRecord(tev[1], sm);
+        cudaEventSynchronize(tev[1]);
+        cudaEventElapsedTime(&ms, tev[0], tev[1]);
+        cudaEventDestroy(tev[0]);
+        cudaEventDestroy(tev[1]);
+        ctx->tune_ms[ctx->tune_step - 1] = ms;
+        if (ctx->tune_step == 2) ctx->tuned_tpb = ctx->tune_ms[0] <= ctx->tune_ms[1] ? 1024 : 512;
+    }
+    if (tuning) ctx->tune_step += 1;
     if (st != IBM_OK) return st;
     ctx->launches += 1;
     // clusters that did not fit: plain FP32 iterations over their particles
-    st = plain_iterations_f32(ctx, S->fb_list, n, S->cnt + C_NFB, tau, f_out != nullptr, ctx->cfg.n_forcing);
+    st = plain_iterations_f32(ctx, S->fb_list, n, S->cnt + C_NFB, tau, f_out != nullptr, ctx->cfg.n_forcing,
+                              det ? S->pcl : nullptr);
     if (st != IBM_OK) return st;
     return IBM_OK;
+}
+
+void cluster_graph_key(const ibm_ctx *ctx, std::vector<uintptr_t> &key) {
+    const ClusterScratch *S = reinterpret_cast<const ClusterScratch *>(ctx->cl);
+    if (!S) {
+        key.push_back(0);
+        return;
+    }
+    const void *bufs[] = {S->scene_bin_off, S->scene_nb, S->bin_cnt, S->bin_start, S->bin_cur, S->bin_items,
+                          S->parent, S->cand, S->cnt, S->tot, S->root_flag, S->cid, S->pcl, S->poff, S->cl_np,
+                          S->cl_nm, S->cl_first, S->cl_cur, S->cl_box, S->cl_plist, S->cl_bkt, S->bkt_cnt,
+                          S->bkt_start, S->order, S->fb_list, S->nm_ord, S->cum, S->cl_scene, S->batches, S->grec};
+    for (const void *b : bufs) key.push_back((uintptr_t)b);
+    const long long sizes[] = {S->cap_p, S->cap_bins, S->cap_cand, S->nbins, S->max_nl, S->n_scenes,
+                               S->smem_bytes, S->tpb, S->det, (long long)S->grec_bytes};
+    for (long long v : sizes) key.push_back((uintptr_t)v);
 }
 
 ibm_status cluster_stats(ibm_ctx *ctx, int64_t *stats) {

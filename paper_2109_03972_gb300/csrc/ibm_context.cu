@@ -74,24 +74,28 @@ static void prof_fold(ibm_ctx *ctx) {
 }
 
 void prof_begin(ibm_ctx *ctx) {
-    if (!ctx->cfg.profile || ctx->prof_ev.empty()) return;
+    if (!ctx->cfg.profile || ctx->prof_ev.empty() || ctx->capturing) return;
     if (ctx->prof_n == kProfPairs) prof_fold(ctx);
     cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], ctx->stream);
 }
 
 void prof_end(ibm_ctx *ctx) {
-    if (!ctx->cfg.profile || ctx->prof_ev.empty()) return;
+    if (!ctx->cfg.profile || ctx->prof_ev.empty() || ctx->capturing) return;
     cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);
     ctx->prof_n += 1;
 }
 
 static void free_all(ibm_ctx *ctx) {
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    ctx->cap_stream = nullptr;
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     ctx->prof_ev.clear();
     void *ptrs[] = {ctx->dims_d, ctx->x, ctx->up, ctx->om, ctx->d, ctx->rho, ctx->scene,
                     ctx->nl, ctx->moff, ctx->toff, ctx->pinfo, ctx->tmpl64, ctx->tmpl32,
                     ctx->tmpl_of_nl, ctx->FD, ctx->TD, ctx->Fout, ctx->Tout, ctx->x_new,
-                    ctx->u_new, ctx->om_new, ctx->slip_acc, ctx->ebuf, ctx->e_hist, ctx->cbuf,
+                    ctx->u_new, ctx->om_new, ctx->slip_acc, ctx->ebuf, ctx->e_hist, ctx->cbuf, ctx->fb_cm, ctx->fb_bits, ctx->cell_off_d,
                     ctx->gu_hist, ctx->gmk, ctx->err_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -138,7 +142,8 @@ ibm_status ibm_create(const ibm_config *cfg, void *cuda_stream, ibm_ctx **out) {
     if (cfg->newton_euler && (!(cfg->rho_f > 0.0) || !std::isfinite(cfg->g[0]) ||
                               !std::isfinite(cfg->g[1]) || !std::isfinite(cfg->g[2])))
         return IBM_ERR_INVALID_ARG;
-    if (cfg->threads_per_block != 0 && cfg->threads_per_block != 512 && cfg->threads_per_block != 1024)
+    if (cfg->threads_per_block != 0 && cfg->threads_per_block != -1 && cfg->threads_per_block != 512 &&
+        cfg->threads_per_block != 1024)
         return IBM_ERR_INVALID_ARG;
     int min_edge = 1 << 30;
     for (int s = 0; s < cfg->n_scenes; ++s)
@@ -252,17 +257,10 @@ ibm_status ibm_set_particles(ibm_ctx *ctx, int n_p, const double *x_p, const dou
     return IBM_OK;
 }
 
-ibm_status ibm_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out,
-                            double *slip_out) {
-    if (!ctx) return IBM_ERR_INVALID_ARG;
-    ctx->last_error.clear();
-    if (!u_ptrs) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "u_ptrs is NULL");
-    for (int s = 0; s < ctx->cfg.n_scenes; ++s)
-        if (!u_ptrs[s]) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "NULL velocity field");
-    if (f_out)
-        for (int s = 0; s < ctx->cfg.n_scenes; ++s)
-            if (!f_out[s]) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "NULL f_out field");
-    if (!(tau > 0.0) || !std::isfinite(tau)) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "tau must be > 0");
+// One forcing step without the slip diagnostic: Sec. 2.2.2 loop, loads, and
+// the Newton-Euler update.  Stream operations only (capturable into a graph
+// once the buffers exist).
+static ibm_status forcing_body(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
     ctx->have_step = false;
     ctx->last_tau = tau;
     ctx->launches = 0;
@@ -298,6 +296,97 @@ ibm_status ibm_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void 
     if (st != IBM_OK) return st;
     ctx->have_step = true;
     ctx->have_forward = ctx->cfg.requires_grad != 0;
+    return IBM_OK;
+}
+
+// Key of a captured step: everything whose change would make a replay of the
+// graph wrong (kernel arguments, launch shapes, buffers).
+static void graph_key(const ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out,
+                      std::vector<uintptr_t> &key) {
+    key.clear();
+    for (int s = 0; s < ctx->cfg.n_scenes; ++s) {
+        key.push_back((uintptr_t)u_ptrs[s]);
+        key.push_back(f_out ? (uintptr_t)f_out[s] : 0);
+    }
+    uint64_t tb;
+    memcpy(&tb, &tau, sizeof(tb));
+    key.push_back((uintptr_t)tb);
+    const void *bufs[] = {ctx->dims_d, ctx->x, ctx->up, ctx->om, ctx->d, ctx->rho, ctx->scene, ctx->nl, ctx->moff,
+                          ctx->toff, ctx->pinfo, ctx->tmpl64, ctx->tmpl32, ctx->tmpl_of_nl, ctx->FD, ctx->TD,
+                          ctx->Fout, ctx->Tout, ctx->x_new, ctx->u_new, ctx->om_new, ctx->ebuf, ctx->cbuf,
+                          ctx->uptr_d, ctx->fptr_d, ctx->err_d, ctx->fb_cm, ctx->fb_bits, ctx->cell_off_d};
+    for (const void *b : bufs) key.push_back((uintptr_t)b);
+    const long long sizes[] = {ctx->n_p, ctx->n_markers, ctx->max_nl, ctx->cap_p, ctx->tmpl_used, ctx->tuned_tpb};
+    for (long long v : sizes) key.push_back((uintptr_t)v);
+    if (ctx->cfg.spread_mode != IBM_SPREAD_PLAIN) cluster_graph_key(ctx, key);
+}
+
+// Forcing step replayed from a CUDA graph: eager while the key is new, captured
+// on the next call with the same key, replayed while the key holds.
+static ibm_status graph_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
+    std::vector<uintptr_t> key;
+    graph_key(ctx, u_ptrs, tau, f_out, key);
+    if (ctx->graph_exec && key == ctx->graph_key) {
+        CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream), "graph launch");
+        ctx->launches = ctx->graph_launches;
+        ctx->have_step = true;
+        ctx->have_forward = false;
+        ctx->last_tau = tau;
+        return IBM_OK;
+    }
+    if (key != ctx->warm_key) {
+        const ibm_status st = forcing_body(ctx, u_ptrs, tau, f_out);
+        if (st != IBM_OK) return st;
+        graph_key(ctx, u_ptrs, tau, f_out, ctx->warm_key);   // after any allocation the step made
+        return ibm_cuda_check(ctx, cudaGetLastError(), "kernel launch");
+    }
+    // capture on a stream of our own (the legacy default stream cannot be
+    // captured); the graph is launched on the context's stream
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream");
+    cudaGraph_t g = nullptr;
+    const cudaStream_t user = ctx->stream;
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    ctx->stream = ctx->cap_stream;
+    ctx->capturing = true;
+    const ibm_status st = forcing_body(ctx, u_ptrs, tau, f_out);
+    ctx->capturing = false;
+    ctx->stream = user;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (st != IBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (ce != cudaSuccess) return ibm_cuda_check(ctx, ce, "end capture");
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        ctx->graph_exec = nullptr;
+        return ibm_cuda_check(ctx, ie, "graph instantiate");
+    }
+    ctx->graph_key = key;
+    ctx->graph_launches = ctx->launches;
+    CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream), "graph launch");
+    return IBM_OK;
+}
+
+ibm_status ibm_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out,
+                            double *slip_out) {
+    if (!ctx) return IBM_ERR_INVALID_ARG;
+    ctx->last_error.clear();
+    if (!u_ptrs) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "u_ptrs is NULL");
+    for (int s = 0; s < ctx->cfg.n_scenes; ++s)
+        if (!u_ptrs[s]) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "NULL velocity field");
+    if (f_out)
+        for (int s = 0; s < ctx->cfg.n_scenes; ++s)
+            if (!f_out[s]) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "NULL f_out field");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "tau must be > 0");
+    if (ctx->cfg.use_graph && !slip_out && !ctx->cfg.requires_grad && ctx->n_p > 0 &&
+        (ctx->cfg.threads_per_block >= 0 || ctx->cfg.spread_mode == IBM_SPREAD_PLAIN || ctx->tune_step >= 3))
+        return graph_step(ctx, u_ptrs, tau, f_out);
+    ibm_status st = forcing_body(ctx, u_ptrs, tau, f_out);
+    if (st != IBM_OK) return st;
     if (slip_out) {
         CK(cudaMemsetAsync(ctx->slip_acc, 0, 2 * sizeof(double), ctx->stream), "zero slip");
         if (ctx->n_p > 0) {

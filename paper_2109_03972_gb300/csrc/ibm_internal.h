@@ -46,6 +46,18 @@ struct SceneDesc {
 
 struct ibm_ctx {
     ibm_config cfg;
+    // CUDA-graph replay of the forcing step (cfg.use_graph): the graph is
+    // captured from the call after an eager one with the same key (field
+    // pointers, tau, sizes and every device buffer the step touches)
+    bool capturing = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;   // capture stream (the caller's may be the legacy stream)
+    std::vector<uintptr_t> graph_key, warm_key;
+    int graph_launches = 0;
+    // autotune of the cluster kernel variant (cfg.threads_per_block < 0):
+    // step 0 warms up, steps 1 and 2 time the two variants, then the faster stays
+    int tune_step = 0, tuned_tpb = 0;
+    float tune_ms[2] = {0.f, 0.f};
     std::vector<int32_t> dims_h;   // [n_scenes][3]
     int32_t *dims_d = nullptr;
     int min_edge = 0;
@@ -73,6 +85,10 @@ struct ibm_ctx {
     double *FD = nullptr, *TD = nullptr;     // sum e*D, sum r x e*D (per particle)
     double *cbuf = nullptr;                  // plain path: per-(particle, chunk) load sums
     size_t cbuf_cap = 0;
+    // deterministic fallback: per-cluster maxima, grid-wide cell bitmap, scene cell offsets
+    unsigned *fb_cm = nullptr, *fb_bits = nullptr;
+    int fb_cm_cap = 0;
+    long long *cell_off_d = nullptr;
     double *Fout = nullptr, *Tout = nullptr; // F_p, T_p in physical units
     double *x_new = nullptr, *u_new = nullptr, *om_new = nullptr;
     double *slip_acc = nullptr;              // [2]
@@ -128,7 +144,7 @@ ibm_status launch_scan_int(ibm_ctx *ctx, const int *in, int *out_excl, int n, lo
 
 ibm_status ensure_field_ptrs(ibm_ctx *ctx, void *const *u_ptrs, void *const *f_out);
 ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
-                                bool with_f, int n_it);
+                                bool with_f, int n_it, const int *pcl);
 
 // profiling (ibm_context.cu): bracket the main kernel of a step
 void prof_begin(ibm_ctx *ctx);
@@ -138,3 +154,5 @@ void prof_end(ibm_ctx *ctx);
 ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out);
 void cluster_free(ibm_ctx *ctx);
 ibm_status cluster_stats(ibm_ctx *ctx, int64_t *stats);
+// appends the cluster path's device buffers and sizes to a graph key
+void cluster_graph_key(const ibm_ctx *ctx, std::vector<uintptr_t> &key);

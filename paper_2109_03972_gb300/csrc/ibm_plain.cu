@@ -233,13 +233,17 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[32]) {
 // Steps 1-2 of the outer forcing loop (Sec. 2.2.2): U = W u, e = U^d - U
 // (F = e / tau), one block per particle, one thread per marker.  Stores e and
 // adds sum e D and sum r x e D to the particle's load accumulators.
-template <typename T>
+// FB (deterministic fallback): also the per-cluster maxima of |u| over the
+// stencil cells, of |e| and of D (float bits in cm[3c..3c+2], atomicMax), from
+// which the spreading's fixed-point scale follows.
+template <typename T, bool FB = false>
 __global__ void __launch_bounds__(kBlock) k_plain_interp(
     const PInfo *__restrict__ P, const int *__restrict__ plist, int n_list, const int *__restrict__ n_list_d,
     const double *__restrict__ t64, const float *__restrict__ t32, const double *__restrict__ up,
     const double *__restrict__ om, const int32_t *__restrict__ dims, T *const *uf, T *__restrict__ ebuf,
-    double *__restrict__ cbuf) {
+    double *__restrict__ cbuf, const int *__restrict__ pcl = nullptr, unsigned *cm = nullptr) {
     __shared__ double sh[6][32];
+    __shared__ float shm[2][32];
     if (n_list_d) n_list = *n_list_d;
     for (int k = blockIdx.y; k < n_list; k += gridDim.y) {
         const int p = plist ? plist[k] : k;
@@ -247,6 +251,7 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
         const Grid g = scene_grid(dims, Pp.scene);
         const T *__restrict__ u = uf[Pp.scene];
         double acc[6] = {0, 0, 0, 0, 0, 0};
+        float umax = 0.f, emax = 0.f;
         for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Pp.nl; l += gridDim.x * blockDim.x) {
             const double *tt64 = t64 + 3ll * (Pp.toff + l);
             const float *tt32 = t32 + 3ll * (Pp.toff + l);
@@ -271,7 +276,11 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
                         const T w = wyz * S.w[0][cx];
                         const long long idx = row + ii[cx];
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) U[q] += w * u[q * g.ncell + idx];
+                        for (int q = 0; q < 3; ++q) {
+                            const T v = u[q * g.ncell + idx];
+                            U[q] += w * v;
+                            if (FB) umax = fmaxf(umax, fabsf((float)v));
+                        }
                     }
                 }
             }
@@ -280,6 +289,7 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
             for (int q = 0; q < 3; ++q) {
                 e[q] = ud[q] - U[q];
                 ebuf[3ll * (Pp.moff + l) + q] = e[q];
+                if (FB) emax = fmaxf(emax, fabsf((float)e[q]));
             }
             const double ed[3] = {(double)(e[0] * D), (double)(e[1] * D), (double)(e[2] * D)};
             const double rd[3] = {(double)r[0], (double)r[1], (double)r[2]};
@@ -294,17 +304,94 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
         // this chunk's partial sums; the spreading kernel adds the chunks in order
         if (threadIdx.x == 0)
             for (int q = 0; q < 6; ++q) cbuf[(6ll * k) * gridDim.x + 6 * blockIdx.x + q] = acc[q];
+        if (FB) {
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+            umax = warp_max(umax);
+            emax = warp_max(emax);
+            if (lane == 0) { shm[0][wid] = umax; shm[1][wid] = emax; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+                    umax = fmaxf(umax, shm[0][i]);
+                    emax = fmaxf(emax, shm[1][i]);
+                }
+                const int c = pcl[p];
+                atomicMax(cm + 3 * c, __float_as_uint(umax));
+                atomicMax(cm + 3 * c + 1, __float_as_uint(emax));
+                atomicMax(cm + 3 * c + 2, __float_as_uint(Pp.D));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Fixed-point scale of a fallback cluster (deterministic mode): the largest
+// power of two 2^k with (max|u| + 64 Dmax max|e|) 2^k < 2^30, as in the
+// shared-memory kernel.
+__device__ __forceinline__ float fb_scale(const unsigned *cm, int c, float *inv) {
+    const float range = __uint_as_float(cm[3 * c]) + 64.f * __uint_as_float(cm[3 * c + 2]) * __uint_as_float(cm[3 * c + 1]);
+    int ex = 100;
+    if (range > 0.f) ex = min(100, max(-100, 29 - (int)ceilf(log2f(range))));
+    *inv = ldexpf(1.f, -ex);
+    return ldexpf(1.f, ex);
+}
+
+// Converts the stencil cells of the fallback markers to the cluster's fixed
+// point (TO) or back, each cell once: the first marker to set (clear) the
+// cell's bit in a grid-wide bitmap converts it.
+template <bool TO>
+__global__ void __launch_bounds__(kBlock) k_fb_convert(const PInfo *__restrict__ P, const int *__restrict__ plist,
+                                                      const int *__restrict__ n_list_d, const double *__restrict__ t64,
+                                                      const float *__restrict__ t32, const int32_t *__restrict__ dims,
+                                                      const long long *__restrict__ cell_off, float *const *uf,
+                                                      const int *__restrict__ pcl, const unsigned *__restrict__ cm,
+                                                      unsigned *bits) {
+    const int n_list = *n_list_d;
+    for (int k = blockIdx.y; k < n_list; k += gridDim.y) {
+        const int p = plist[k];
+        const PInfo Pp = P[p];
+        const Grid g = scene_grid(dims, Pp.scene);
+        float *u = uf[Pp.scene];
+        float inv;
+        const float S = fb_scale(cm, pcl[p], &inv);
+        for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Pp.nl; l += gridDim.x * blockDim.x) {
+            Stencil<float> st;
+            marker_stencil(Pp, t64 + 3ll * (Pp.toff + l), t32 + 3ll * (Pp.toff + l), st);
+            for (int cz = 0; cz < 3; ++cz)
+                for (int cy = 0; cy < 3; ++cy)
+                    for (int cx = 0; cx < 3; ++cx) {
+                        const long long idx = ((long long)wrapi(st.b[2] - 1 + cz, g.nz) * g.ny +
+                                               wrapi(st.b[1] - 1 + cy, g.ny)) * g.nx + wrapi(st.b[0] - 1 + cx, g.nx);
+                        const long long gi = cell_off[Pp.scene] + idx;
+                        const unsigned bit = 1u << (gi & 31);
+                        if (TO) {
+                            if (atomicOr(bits + (gi >> 5), bit) & bit) continue;
+                            for (int q = 0; q < 3; ++q) {
+                                float *c = u + q * g.ncell + idx;
+                                *reinterpret_cast<int *>(c) = __float2int_rn(*c * S);
+                            }
+                        } else {
+                            if (!(atomicAnd(bits + (gi >> 5), ~bit) & bit)) continue;
+                            for (int q = 0; q < 3; ++q) {
+                                float *c = u + q * g.ncell + idx;
+                                *c = (float)*reinterpret_cast<const int *>(c) * inv;
+                            }
+                        }
+                    }
+        }
     }
 }
 
 // Steps 3-4 (Sec. 2.2.2): u += tau f with f = sum_l F_l w D_l, i.e.
 // u += scale * sum_l w D_l v_l for v = e (scale 1).  Optional f_out += that / tau.
-template <typename T>
+// FB (deterministic fallback, FP32): the cells hold the cluster's fixed point
+// (k_fb_convert) and the contributions are added as rounded integers.
+template <typename T, bool FB = false>
 __global__ void __launch_bounds__(kBlock) k_plain_spread(
     const PInfo *__restrict__ P, const int *__restrict__ plist, int n_list, const int *__restrict__ n_list_d,
     const double *__restrict__ t64, const float *__restrict__ t32, const int32_t *__restrict__ dims,
     const T *__restrict__ vbuf, T scale, T *const *uf, T *const *ff, T finv, const double *__restrict__ cbuf,
-    double *FD, double *TD) {
+    double *FD, double *TD, const int *__restrict__ pcl = nullptr, const unsigned *__restrict__ cm = nullptr) {
     if (n_list_d) n_list = *n_list_d;
     for (int k = blockIdx.y; k < n_list; k += gridDim.y) {
         const int p = plist ? plist[k] : k;
@@ -328,6 +415,8 @@ __global__ void __launch_bounds__(kBlock) k_plain_spread(
             T gv[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) gv[q] = scale * D * vbuf[3ll * (Pp.moff + l) + q];
+            float fs = 1.f, finv_s = 0.f;
+            if (FB) fs = fb_scale(cm, pcl[p], &finv_s);
             int ii[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) ii[a] = wrapi(S.b[0] - 1 + a, g.nx);
@@ -345,7 +434,11 @@ __global__ void __launch_bounds__(kBlock) k_plain_spread(
                         const long long idx = row + ii[cx];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
-                            atomicAdd(u + q * g.ncell + idx, w * gv[q]);
+                            if (FB)
+                                atomicAdd(reinterpret_cast<int *>(u + q * g.ncell + idx),
+                                          __float2int_rn((float)(w * gv[q]) * fs));
+                            else
+                                atomicAdd(u + q * g.ncell + idx, w * gv[q]);
                             if (f) atomicAdd(f + q * g.ncell + idx, w * gv[q] * finv);
                         }
                     }
@@ -783,9 +876,12 @@ static dim3 chunk_grid(const ibm_ctx *ctx, int n_list, bool count_on_device = fa
 }
 
 // One plain iteration over the particles in plist (all when plist == NULL).
+// pcl (FP32 list only): cluster of each particle; spreading then runs in the
+// deterministic fixed point of the cluster (interpolate with the maxima,
+// convert the stencil cells, integer spreading, convert back).
 template <typename T>
 static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
-                                  bool with_f) {
+                                  bool with_f, const int *pcl = nullptr) {
     const dim3 grid = chunk_grid(ctx, n_list, n_list_d != nullptr);
     const size_t need = (size_t)std::max(1, n_list) * grid.x * 6 * sizeof(double);
     if (ctx->cbuf_cap < need) {
@@ -797,6 +893,46 @@ static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, co
     }
     T *const *uf = reinterpret_cast<T *const *>(ctx->uptr_d);
     T *const *ff = with_f ? reinterpret_cast<T *const *>(ctx->fptr_d) : nullptr;
+    if (pcl && sizeof(T) == 4) {
+        if (!ctx->fb_bits) {
+            long long off = 0;
+            std::vector<long long> offs(ctx->cfg.n_scenes);
+            for (int s = 0; s < ctx->cfg.n_scenes; ++s) {
+                offs[s] = off;
+                off += (long long)ctx->dims_h[3 * s] * ctx->dims_h[3 * s + 1] * ctx->dims_h[3 * s + 2];
+            }
+            const size_t words = (size_t)(off + 31) / 32 + 1;
+            CK(cudaMalloc(&ctx->cell_off_d, offs.size() * sizeof(long long)), "alloc scene offsets");
+            CK(cudaMemcpy(ctx->cell_off_d, offs.data(), offs.size() * sizeof(long long), cudaMemcpyHostToDevice),
+               "copy scene offsets");
+            CK(cudaMalloc(&ctx->fb_bits, words * sizeof(unsigned)), "alloc cell bitmap");
+            CK(cudaMemset(ctx->fb_bits, 0, words * sizeof(unsigned)), "zero cell bitmap");
+        }
+        if (ctx->fb_cm_cap < ctx->cap_p) {
+            if (ctx->fb_cm) cudaFree(ctx->fb_cm);
+            ctx->fb_cm = nullptr;
+            CK(cudaMalloc(&ctx->fb_cm, 3 * (size_t)ctx->cap_p * sizeof(unsigned)), "alloc cluster maxima");
+            ctx->fb_cm_cap = ctx->cap_p;
+        }
+        float *const *u32 = reinterpret_cast<float *const *>(ctx->uptr_d);
+        float *const *f32 = with_f ? reinterpret_cast<float *const *>(ctx->fptr_d) : nullptr;
+        CK(cudaMemsetAsync(ctx->fb_cm, 0, 3 * (size_t)ctx->cap_p * sizeof(unsigned), ctx->stream), "zero maxima");
+        k_plain_interp<float, true><<<grid, kBlock, 0, ctx->stream>>>(
+            ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, u32,
+            reinterpret_cast<float *>(ctx->ebuf), ctx->cbuf, pcl, ctx->fb_cm);
+        k_fb_convert<true><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list_d, ctx->tmpl64, ctx->tmpl32,
+                                                             ctx->dims_d, ctx->cell_off_d, u32, pcl, ctx->fb_cm,
+                                                             ctx->fb_bits);
+        k_plain_spread<float, true><<<grid, kBlock, 0, ctx->stream>>>(
+            ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->dims_d,
+            reinterpret_cast<const float *>(ctx->ebuf), 1.f, u32, f32, (float)(1.0 / tau), ctx->cbuf, ctx->FD,
+            ctx->TD, pcl, ctx->fb_cm);
+        k_fb_convert<false><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list_d, ctx->tmpl64, ctx->tmpl32,
+                                                              ctx->dims_d, ctx->cell_off_d, u32, pcl, ctx->fb_cm,
+                                                              ctx->fb_bits);
+        ctx->launches += 4;
+        return IBM_OK;
+    }
     k_plain_interp<T><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
                                                         ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, uf,
                                                         reinterpret_cast<T *>(ctx->ebuf), ctx->cbuf);
@@ -809,11 +945,12 @@ static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, co
 }
 
 // FP32 plain iterations over a particle list whose length is n_list, or, when
-// n_list_d is given, the device value *n_list_d (at most n_list).
+// n_list_d is given, the device value *n_list_d (at most n_list).  pcl != NULL:
+// deterministic fixed-point spreading per cluster.
 ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
-                                bool with_f, int n_it) {
+                                bool with_f, int n_it, const int *pcl) {
     for (int it = 0; it < n_it; ++it) {
-        const ibm_status st = plain_iteration<float>(ctx, plist, n_list, n_list_d, tau, with_f);
+        const ibm_status st = plain_iteration<float>(ctx, plist, n_list, n_list_d, tau, with_f, pcl);
         if (st != IBM_OK) return st;
     }
     return ibm_cuda_check(ctx, cudaGetLastError(), "plain iteration");

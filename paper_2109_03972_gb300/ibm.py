@@ -40,7 +40,7 @@ class _Config(ctypes.Structure):
                 ("newton_euler", ctypes.c_int), ("rho_f", ctypes.c_double),
                 ("g", ctypes.c_double * 3), ("max_particles", ctypes.c_int),
                 ("requires_grad", ctypes.c_int), ("threads_per_block", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("use_graph", ctypes.c_int)]
 
 
 _lib = None
@@ -101,8 +101,9 @@ class Config:
     max_particles: int = 1
     requires_grad: bool = False
     kernel_width: int = 3
-    threads_per_block: int = 0
+    threads_per_block: int = 0        # 0: 1024 threads; 512; -1: autotune
     profile: bool = False
+    use_graph: bool = False
     extra: dict = field(default_factory=dict)
 
 
@@ -130,6 +131,7 @@ class Context:
         c.requires_grad = int(cfg.requires_grad)
         c.threads_per_block = cfg.threads_per_block
         c.profile = int(cfg.profile)
+        c.use_graph = int(cfg.use_graph)
         h = ctypes.c_void_p()
         st = self.L.ibm_create(ctypes.byref(c), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
         if st != 0:

@@ -95,21 +95,18 @@ def rsa_spheres(dims, diameters, seed: int, gap: float = 1.0, h: float = 1.0,
         for _ in range(max_attempts):
             x = rng.uniform(0.0, 1.0, size=3) * L
             ci = np.minimum((x // csz).astype(np.int64), ncell - 1)
+            # neighbouring buckets, each once (boxes with fewer than 3 buckets per axis
+            # would otherwise list the same bucket several times)
+            keys = {((int(ci[0]) + ox) % int(ncell[0]), (int(ci[1]) + oy) % int(ncell[1]),
+                     (int(ci[2]) + oz) % int(ncell[2]))
+                    for ox in (-1, 0, 1) for oy in (-1, 0, 1) for oz in (-1, 0, 1)}
             ok = True
-            for ox in (-1, 0, 1):
-                for oy in (-1, 0, 1):
-                    for oz in (-1, 0, 1):
-                        key = ((ci[0] + ox) % ncell[0], (ci[1] + oy) % ncell[1],
-                               (ci[2] + oz) % ncell[2])
-                        for j in buckets.get(key, ()):
-                            dv = x - centres[j]
-                            dv -= L * np.round(dv / L)
-                            if math.sqrt(float(dv @ dv)) < 0.5 * (d + kept[j]) + gap:
-                                ok = False
-                                break
-                        if not ok:
-                            break
-                    if not ok:
+            for key in keys:
+                for j in buckets.get(key, ()):
+                    dv = x - centres[j]
+                    dv -= L * np.round(dv / L)
+                    if math.sqrt(float(dv @ dv)) < 0.5 * (d + kept[j]) + gap:
+                        ok = False
                         break
                 if not ok:
                     break
@@ -168,13 +165,14 @@ def make_scene(dims, diameters, seed, gap=1.0, h=1.0, max_attempts=1000):
                  field_seed=seed + 2, h=h)
 
 
-def workload(name: str, seed: int = 2109) -> Workload:
+def workload(name: str, seed: int = 2109, n_scenes: int = 512) -> Workload:
     """The named synthetic workloads (all periodic, h = 1, n_F = 3, tau = 0.01).
 
     single64   : 64^3 grid, one sphere D=16 at a random position (~804 markers)
     mono       : 256x256x512, 2000 spheres D=16, gap >= 1h (~12.8% solid)
     bidisperse : 512x512x1024, 1500 spheres D=24 then 12000 spheres D=12, gap >= 1h
     batched    : 512 scenes, edge in {32,48,64,96,128}, n in U{1..40}, D ~ U[8,20]
+                 (the first n_scenes of them; the draws do not depend on n_scenes)
     diff128    : 128^3, 150 spheres D=16 (differentiation workload)
     small      : 40x36x44, 6 spheres D in {6,8,10} (fast parity case, ragged dims)
     """
@@ -194,7 +192,7 @@ def workload(name: str, seed: int = 2109) -> Workload:
         edges = rng.choice([32, 48, 64, 96, 128], size=512)
         counts = rng.integers(1, 41, size=512)
         scenes = []
-        for s in range(512):
+        for s in range(min(512, n_scenes)):
             ds = np.sort(rng.uniform(8.0, 20.0, size=int(counts[s])))[::-1]
             e = int(edges[s])
             scenes.append(make_scene((e, e, e), ds, seed + 7 * s + 11))
