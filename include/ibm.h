@@ -71,7 +71,10 @@ typedef struct {
     int n_scenes;            /* >= 1; independent periodic boxes               */
     const int32_t *dims;     /* HOST [n_scenes][3] = nx, ny, nz (each >= 8)    */
     double h;                /* grid spacing (> 0), isotropic (Sec. 2.1)       */
-    int kernel_width;        /* 3: three-point kernel, Eq. (3pt-stencil)       */
+    int kernel_width;        /* 3: three-point kernel, Eq. (3pt-stencil);
+                                4: four-point kernel of Sec. 2.2.3 (cells
+                                floor(x/h - 1/2) - 1 .. + 2), PLAIN mode
+                                only, no requires_grad                        */
     int n_forcing;           /* n_F >= 1 outer forcing iterations (Sec. 2.2.2) */
     int precision;           /* IBM_FP32 or IBM_FP64                           */
     int spread_mode;         /* IBM_SPREAD_*                                   */
@@ -103,8 +106,9 @@ typedef struct ibm_ctx ibm_ctx;
 /* Create a context.  cuda_stream is a cudaStream_t (NULL = legacy default
  * stream).  cfg->dims is copied.  On success *out owns device scratch sized for
  * cfg->max_particles; release it with ibm_destroy.
- * Errors: INVALID_ARG (bad config; kernel_width other than 3; FP64 with a mode
- * other than PLAIN), OOM, CUDA. */
+ * Errors: INVALID_ARG (bad config; kernel_width other than 3 or 4; width 4
+ * with a mode other than PLAIN or with requires_grad; FP64 with a mode other
+ * than PLAIN), OOM, CUDA. */
 ibm_status ibm_create(const ibm_config *cfg, void *cuda_stream, ibm_ctx **out);
 
 /* Release a context and all memory it owns.  NULL is accepted. */

@@ -381,21 +381,27 @@ __global__ void k_cluster_fill(int n_p, const int *pcl, const int *cl_first, int
 // Route each cluster: shared-memory path if it fits the CTA's capacities and
 // its box is consistently unwrapped, else the plain fallback.
 __global__ void k_cluster_route(const long long *n_clust_d, const PInfo *P, const int32_t *dims, const int *cl_np,
-                                const int *cl_nm, const int *cl_first, const int *cl_plist, const int *cl_box,
+                                const int *cl_nm, const int *cl_first, const int *cl_plist, int *cl_box,
                                 int cap_m, int max_rows, int *cl_bkt, int *bkt_cnt, int *fb_list, int *cl_scene,
                                 int *cnt) {
     const int n = (int)*n_clust_d;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const int np = cl_np[c], nm = cl_nm[c];
         const int s = P[cl_plist[cl_first[c]]].scene;
-        cl_scene[c] = s;
         bool ok = np <= kCapP && nm <= cap_m;
-        int R = 1;
+        int R = 1, wrap = 0;
         for (int k = 0; k < 3; ++k) {
             const int n_k = dims[3 * s + k];
-            const int ext = cl_box[12 * c + 3 + k] - cl_box[12 * c + k] + 1;
+            int ext = cl_box[12 * c + 3 + k] - cl_box[12 * c + k] + 1;
             const int cext = cl_box[12 * c + 9 + k] - cl_box[12 * c + 6 + k] + 1;
-            ok = ok && ext <= n_k && 2 * cext < n_k;
+            if (!(ext <= n_k && 2 * cext < n_k)) {
+                // the cluster cannot be unwrapped along this axis: its box is the
+                // whole period (rows wrap in y and z; in x one ghost column each side)
+                wrap |= 1 << k;
+                cl_box[12 * c + k] = k == 0 ? -1 : 0;
+                cl_box[12 * c + 3 + k] = k == 0 ? n_k : n_k - 1;
+                ext = cl_box[12 * c + 3 + k] - cl_box[12 * c + k] + 1;
+            }
             R *= (k == 0) ? (ext + 31) / 32 : ext;
         }
         // a dense row table over max_rows entries is replaced by a sparse one
@@ -405,6 +411,7 @@ __global__ void k_cluster_route(const long long *n_clust_d, const PInfo *P, cons
         // bitmask entry decode words hold y, z < 1024 and 16 words (512 cells) per row
         ok = ok && (cl_box[12 * c + 4] - cl_box[12 * c + 1]) < 1023 && (cl_box[12 * c + 5] - cl_box[12 * c + 2]) < 1023 &&
              (cl_box[12 * c + 3] - cl_box[12 * c]) < 511;
+        cl_scene[c] = s | (wrap << 28);   // scene, and the wrapped axes in the top bits
         if (ok) {
             const int b = min(kBuckets - 1, nm / 8);
             cl_bkt[c] = kBuckets - 1 - b;   // larger clusters first
@@ -536,6 +543,8 @@ struct CS {          // cluster record in shared memory
     int pstart;      // first particle of the cluster in the batch (before sorting)
     int first, np;   // particles in cl_plist
     int scene;
+    int wrap;        // bit k: axis k is periodic in the box (whole period; x with ghost columns)
+    int n[3];        // the scene's grid
     float dmax, S, invS;
     unsigned umax, emax;   // float bits (non-negative), atomicMax
 };
@@ -586,26 +595,42 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
 }
 
 // Box-relative base cell and fractional position of a marker (FP32 path).
-__device__ __forceinline__ void rel_base(const PS &s, const float *t32, const double *t64, int l, int b[3],
-                                         float f[3]) {
+// Along a periodic axis of the box the base is first taken modulo the period.
+__device__ __forceinline__ void rel_base(const PS &s, const CS &cs, const float *t32, const double *t64, int l,
+                                         int b[3], float f[3]) {
     const float *t = t32 + 3ll * (s.P.toff + l);
     const double *t6 = t64 + 3ll * (s.P.toff + l);
+    const int wrap = cs.wrap;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) b[c] = marker_split32(s.P, t, t6, c, &f[c]) + s.off[c];
+    for (int c = 0; c < 3; ++c) {
+        const int raw = marker_split32(s.P, t, t6, c, &f[c]);
+        b[c] = (wrap && ((wrap >> c) & 1) ? wrapi(raw, cs.n[c]) : raw) + s.off[c];
+    }
+}
+
+// Box row of stencil row (dz, dy) of a marker with box-relative base b
+// (modulo the period along periodic y or z).
+__device__ __forceinline__ int box_row(const CS &cs, const int b[3], int dz, int dy) {
+    int y = b[1] + dy, z = b[2] + dz;
+    if (cs.wrap & 2) y = wrapi(y, cs.By);
+    if (cs.wrap & 4) z = wrapi(z, cs.Bz);
+    return z * cs.By + y;
 }
 
 // Slots of the nine row runs of a marker's stencil.  rix (sparse row table)
 // maps a box row to its compact row, nullptr for the dense table.
-__device__ __forceinline__ void row_slots(const uint2 *rt, const unsigned short *rix, int W, int By, const int b[3],
+__device__ __forceinline__ void row_slots(const uint2 *rt, const unsigned short *rix, const CS &cs, const int b[3],
                                           int slot[9]) {
     const int x = b[0] - 1;
     const int wx = x >> 5;
     const unsigned lowmask = (1u << (x & 31)) - 1u;
+    const int W = cs.W, By = cs.By;
+    const bool wrap = cs.wrap != 0;
 #pragma unroll
     for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
-            const int r = (b[2] + dz - 1) * By + (b[1] + dy - 1);
+            const int r = wrap ? box_row(cs, b, dz - 1, dy - 1) : (b[2] + dz - 1) * By + (b[1] + dy - 1);
             const int row = rix ? (int)rix[r] : r;
             const uint2 e = rt[row * W + wx];
             slot[dz * 3 + dy] = (int)e.y + __popc(e.x & lowmask);
@@ -630,6 +655,7 @@ __host__ __device__ constexpr int fixed_smem_bytes() {
 
 struct Batch {
     int nb, np, nm, R, C;
+    int gx;                      // some cluster is periodic in x (ghost columns)
     const unsigned short *rix;   // sparse row table: box row -> compact row (else nullptr)
     const unsigned short *rowid; // sparse row table: compact row -> box row
 };
@@ -644,11 +670,14 @@ struct Batch {
 template <int TPB, int NC, bool LOAD>
 __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, const CS *s_cs, const uint2 *s_row,
                                            const unsigned short *s_inv, float *s_u, int q0) {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, C = bt.C;
     for (int j = 0; j < bt.nb; ++j) {
         const int x0 = s_cs[j].x0, y0 = s_cs[j].y0, z0 = s_cs[j].z0;
         const int W = s_cs[j].W, By = s_cs[j].By, row0 = s_cs[j].row0;
         const int sc = s_cs[j].scene;
+        // ghost columns of a box periodic in x are copies: gathered, not written back
+        const bool skip_ghosts = !LOAD && (s_cs[j].wrap & 1);
+        const int Bx = s_cs[j].Bx;
         const int nx = prm.dims[3 * sc], ny = prm.dims[3 * sc + 1], nz = prm.dims[3 * sc + 2];
         const long long ncell = (long long)nx * ny * nz;
         float *u = prm.uf[sc] + (long long)q0 * ncell;
@@ -668,9 +697,9 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
 #pragma unroll
             for (int q = 0; q < NC; ++q) {
                 if (LOAD) {
-                    cp_async4(su + q * bt.C + sl, u + q * ncell + g);
+                    cp_async4(su + q * C + sl, u + q * ncell + g);
                 } else {
-                    const float v = su[q * bt.C + sl];
+                    const float v = su[q * C + sl];
                     if (f) f[q * ncell + g] = (v - u[q * ncell + g]) * prm.finv;
                     u[q * ncell + g] = v;
                 }
@@ -683,8 +712,9 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
                 const uint2 rw = s_row[i];
                 int wx;
                 const long long rb = row_base((int)i - row0, wx);
-                const int bit = (int)__fns(rw.x, 0u, base + sl - (int)rw.y + 1);
-                move(rb + wrapi(x0 + 32 * wx + bit, nx), sl);
+                const int xb = 32 * wx + (int)__fns(rw.x, 0u, base + sl - (int)rw.y + 1);
+                if (skip_ghosts && (xb == 0 || xb == Bx - 1)) continue;
+                move(rb + wrapi(x0 + xb, nx), sl);
             }
         } else {
             for (int li = tid; li < s_cs[j].R; li += TPB) {
@@ -694,9 +724,9 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
                 const long long rb = row_base(li, wx);
                 int sl = (int)s_row[row0 + li].y - s_cs[j].slot0;
                 while (mask) {
-                    const int bit = __ffs(mask) - 1;
+                    const int xb = 32 * wx + __ffs(mask) - 1;
                     mask &= mask - 1u;
-                    move(rb + wrapi(x0 + 32 * wx + bit, nx), sl);
+                    if (!(skip_ghosts && (xb == 0 || xb == Bx - 1))) move(rb + wrapi(x0 + xb, nx), sl);
                     ++sl;
                 }
             }
@@ -710,22 +740,81 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
 // stencil leaves the box (never expected: the box bounds every stencil of the
 // cluster).
 __device__ __forceinline__ bool in_box(const CS &cs, const int b[3]) {
-    return b[0] >= 1 && b[0] <= cs.Bx - 2 && b[1] >= 1 && b[1] <= cs.By - 2 && b[2] >= 1 && b[2] <= cs.Bz - 2;
+    // along periodic y or z every row of the period is in the box
+    return b[0] >= 1 && b[0] <= cs.Bx - 2 &&
+           ((cs.wrap & 2) ? (b[1] >= 0 && b[1] < cs.By) : (b[1] >= 1 && b[1] <= cs.By - 2)) &&
+           ((cs.wrap & 4) ? (b[2] >= 0 && b[2] < cs.Bz) : (b[2] >= 1 && b[2] <= cs.Bz - 2));
 }
 
+// Along periodic x, box columns 0 and Bx-1 are ghosts of the period's last
+// and first column (box columns Bx-2 and 1); a stencil that reaches a ghost
+// also marks its partner, so that both copies have slots.
 __device__ __forceinline__ bool mark_stencil(uint2 *rt, const unsigned short *rix, const CS &cs, const int b[3]) {
+    if (!cs.wrap) {
+        // a box that is not periodic: plain row arithmetic
+        const int Bx = cs.Bx, By = cs.By, Bz = cs.Bz, W = cs.W;
+        if (b[0] < 1 || b[0] > Bx - 2 || b[1] < 1 || b[1] > By - 2 || b[2] < 1 || b[2] > Bz - 2) return false;
+        const int x = b[0] - 1, wx = x >> 5, bit = x & 31;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int r = (b[2] + dz) * By + (b[1] + dy);
+                const int row = rix ? (int)rix[r] : r;
+                atomicOr(&rt[row * W + wx].x, 7u << bit);
+                if (bit > 29) atomicOr(&rt[row * W + wx + 1].x, 7u >> (32 - bit));
+            }
+        return true;
+    }
     if (!in_box(cs, b)) return false;
     const int x = b[0] - 1, wx = x >> 5, bit = x & 31;
+    const bool gl = (cs.wrap & 1) && b[0] == 1, gr = (cs.wrap & 1) && b[0] == cs.Bx - 2;
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
-            const int r = (b[2] + dz) * cs.By + (b[1] + dy);
+            const int r = box_row(cs, b, dz, dy);
             const int row = rix ? (int)rix[r] : r;
             atomicOr(&rt[row * cs.W + wx].x, 7u << bit);
             if (bit > 29) atomicOr(&rt[row * cs.W + wx + 1].x, 7u >> (32 - bit));
+            if (gl) atomicOr(&rt[row * cs.W + ((cs.Bx - 2) >> 5)].x, 1u << ((cs.Bx - 2) & 31));
+            if (gr) atomicOr(&rt[row * cs.W].x, 2u);
         }
     return true;
+}
+
+// Slot of box column x in a row's bitmask entries e (bit assumed set).
+__device__ __forceinline__ int col_slot(const uint2 *e, int x) {
+    const uint2 w = e[x >> 5];
+    return (int)w.y + __popc(w.x & ((1u << (x & 31)) - 1u));
+}
+
+// Ghost columns of the clusters that are periodic in x: G = 0 copies the real
+// cells into the ghosts (before an interpolation), G = 1 zeroes the ghosts
+// (before spreading), G = 2 adds the ghosts' spread contributions to the real
+// cells (after spreading; integer adds in deterministic mode, so the sum is
+// exact).
+template <int TPB, int NC, int G, bool DET>
+__device__ __forceinline__ void ghost_pass(const Batch &bt, const CS *s_cs, const uint2 *s_row, float *s_u) {
+    const int C = bt.C;
+    for (int j = 0; j < bt.nb; ++j) {
+        if (!(s_cs[j].wrap & 1)) continue;
+        const int W = s_cs[j].W, Bx = s_cs[j].Bx, nrow = s_cs[j].R / W;
+        for (int k = threadIdx.x; k < 2 * nrow; k += TPB) {
+            const uint2 *e = s_row + s_cs[j].row0 + (k >> 1) * W;
+            const int gx = (k & 1) ? Bx - 1 : 0, rx = (k & 1) ? 1 : Bx - 2;
+            if (!((e[gx >> 5].x >> (gx & 31)) & 1u)) continue;
+            const int g = col_slot(e, gx), r = col_slot(e, rx);
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                float *ug = s_u + q * C + g, *ur = s_u + q * C + r;
+                if (G == 0) *ug = *ur;
+                else if (G == 1) *ug = 0.f;
+                else if (DET) *reinterpret_cast<int *>(ur) += *reinterpret_cast<const int *>(ug);
+                else *ur += *ug;
+            }
+        }
+    }
 }
 
 // Deterministic mode keeps the touched cells in fixed point while markers
@@ -745,13 +834,14 @@ __device__ __forceinline__ bool mark_stencil(uint2 *rt, const unsigned short *ri
 // zero on entry).
 template <int TPB, int NC>
 __device__ __forceinline__ void det_scan(const Batch &bt, CS *s_cs, const float *s_u) {
+    const int C = bt.C;
     const int tid = threadIdx.x, lane = tid & 31;
     for (int j = 0; j < bt.nb; ++j) {
         const int n4 = (s_cs[j].ncell + 3) >> 2;
         float um = 0.f;
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-            const float4 *p = reinterpret_cast<const float4 *>(s_u + q * bt.C + s_cs[j].slot0);
+            const float4 *p = reinterpret_cast<const float4 *>(s_u + q * C + s_cs[j].slot0);
             for (int i = tid; i < n4; i += TPB) {
                 const float4 v = p[i];
                 um = fmaxf(um, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
@@ -781,13 +871,14 @@ __device__ __forceinline__ void det_scale(const Batch &bt, CS *s_cs) {
 // u -> round(u S) (TO) or back, components 0..NC-1 of every cluster.
 template <int TPB, int NC, bool TO>
 __device__ __forceinline__ void det_convert(const Batch &bt, const CS *s_cs, float *s_u) {
+    const int C = bt.C;
     const int tid = threadIdx.x;
     for (int j = 0; j < bt.nb; ++j) {
         const int n4 = (s_cs[j].ncell + 3) >> 2;
         const float S = TO ? s_cs[j].S : s_cs[j].invS;
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-            float4 *p = reinterpret_cast<float4 *>(s_u + q * bt.C + s_cs[j].slot0);
+            float4 *p = reinterpret_cast<float4 *>(s_u + q * C + s_cs[j].slot0);
             for (int i = tid; i < n4; i += TPB) {
                 if (TO) {
                     const float4 v = p[i];
@@ -807,10 +898,11 @@ __device__ __forceinline__ void det_convert(const Batch &bt, const CS *s_cs, flo
 // Zero the padding slots of every cluster (components 0..NC-1).
 template <int TPB, int NC>
 __device__ __forceinline__ void zero_padding(const Batch &bt, const CS *s_cs, float *s_u) {
+    const int C = bt.C;
     for (int j = threadIdx.x; j < bt.nb; j += TPB) {
         const int s0 = s_cs[j].slot0 + s_cs[j].ncell, s1 = s_cs[j].slot0 + ((s_cs[j].ncell + 3) & ~3);
         for (int q = 0; q < NC; ++q)
-            for (int i = s0; i < s1; ++i) s_u[q * bt.C + i] = 0.f;
+            for (int i = s0; i < s1; ++i) s_u[q * C + i] = 0.f;
     }
 }
 
@@ -856,6 +948,10 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
     const int C = bt.C, nm = bt.nm;
     load_cells<TPB, NC, DET>(prm, bt, s_cs, s_row, s_inv, s_u, q0);
     for (int iter = 0; iter < prm.n_forcing; ++iter) {
+        if (bt.gx && iter > 0) {
+            ghost_pass<TPB, NC, 0, DET>(bt, s_cs, s_row, s_u);
+            __syncthreads();
+        }
         float e[KR][NC];
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
@@ -935,6 +1031,10 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
             det_convert<TPB, NC, true>(bt, s_cs, s_u);
             __syncthreads();
         }
+        if (bt.gx) {
+            ghost_pass<TPB, NC, 1, DET>(bt, s_cs, s_row, s_u);
+            __syncthreads();
+        }
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
             const int m = tid + k * TPB;
@@ -970,6 +1070,10 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
                 }
         }
         __syncthreads();
+        if (bt.gx) {
+            ghost_pass<TPB, NC, 2, DET>(bt, s_cs, s_row, s_u);
+            __syncthreads();
+        }
         if (DET) {
             det_convert<TPB, NC, false>(bt, s_cs, s_u);
             __syncthreads();
@@ -994,7 +1098,7 @@ __device__ __noinline__ void build_sparse_rows(CS *s_cs, const float4 *ra, int n
                                   int *s_scan, int *flag, Batch &bt, uint2 *&s_row) {
     const int tid = threadIdx.x;
     CS &cs = s_cs[0];
-    const int By = cs.By, W = cs.W, nyz = cs.By * cs.Bz;
+    const int W = cs.W, nyz = cs.By * cs.Bz;
     unsigned short *rix = reinterpret_cast<unsigned short *>(base);
     unsigned *rbits = align16_to<unsigned>(rix + nyz);
     const int nw = (nyz + 31) >> 5;
@@ -1007,10 +1111,10 @@ __device__ __noinline__ void build_sparse_rows(CS *s_cs, const float4 *ra, int n
         for (int m = tid; m < nm; m += TPB) {
             const unsigned bp = __float_as_uint(ra[m].w);
             if (bp == kNoMarker) continue;
-            const int b1 = (int)((bp >> 10) & 1023u), b2 = (int)(bp >> 20);
+            const int b[3] = {0, (int)((bp >> 10) & 1023u), (int)(bp >> 20)};
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy) {
-                    const int r = (b2 + dz) * By + (b1 + dy);
+                    const int r = box_row(cs, b, dz, dy);
                     atomicOr(&rbits[r >> 5], 1u << (r & 31));
                 }
         }
@@ -1099,7 +1203,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                     cs.R = cs.By * cs.Bz * cs.W;
                     cs.first = prm.cl_first[id];
                     cs.np = prm.cl_np[id];
-                    cs.scene = prm.cl_scene[id];
+                    const int sw = prm.cl_scene[id];
+                    cs.scene = sw & 0x0fffffff;
+                    cs.wrap = sw >> 28;
+                    cs.n[0] = prm.dims[3 * cs.scene];
+                    cs.n[1] = prm.dims[3 * cs.scene + 1];
+                    cs.n[2] = prm.dims[3 * cs.scene + 2];
                     cnp = cs.np;
                     cR = cs.R;
                 }
@@ -1117,12 +1226,20 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                 if (tid == 0) s_flag = 0;
             }
             __syncthreads();
-            Batch bt;
+            // batch-wide values live in shared memory (every thread writes the same
+            // value), which keeps them out of the registers of the forcing loop
+            __shared__ Batch s_bt;
+            Batch &bt = s_bt;
             bt.nb = nbl;
             bt.np = s_np;
             bt.R = s_R;
             bt.rix = nullptr;
             bt.rowid = nullptr;
+            {
+                int gx = 0;
+                for (int j = 0; j < nbl; ++j) gx |= s_cs[j].wrap & 1;
+                bt.gx = gx;
+            }
             const int np = bt.np;
             // a single cluster whose dense row table is too large gets a sparse one
             const bool sparse = bt.nb == 1 && bt.R > prm.max_rows;
@@ -1152,9 +1269,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                 const int p = s_ps[tid].gid;
                 const CS &cs = s_cs[s_ps[tid].cl];
                 s_ps[tid].P = prm.P[p];
-                s_ps[tid].off[0] = prm.poff[3 * p] - cs.x0;
-                s_ps[tid].off[1] = prm.poff[3 * p + 1] - cs.y0;
-                s_ps[tid].off[2] = prm.poff[3 * p + 2] - cs.z0;
+                // periodic axes of the box take the base modulo the period instead
+                s_ps[tid].off[0] = ((cs.wrap & 1) ? 0 : prm.poff[3 * p]) - cs.x0;
+                s_ps[tid].off[1] = ((cs.wrap & 2) ? 0 : prm.poff[3 * p + 1]) - cs.y0;
+                s_ps[tid].off[2] = ((cs.wrap & 4) ? 0 : prm.poff[3 * p + 2]) - cs.z0;
             }
             if (!sparse)
                 for (int i = tid; i < bt.R; i += TPB) s_row[i].x = 0u;
@@ -1201,8 +1319,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                 }
                 int b[3];
                 float f[3];
-                rel_base(s, prm.t32, prm.t64, l, b, f);
                 const CS &cs = s_cs[s.cl];
+                rel_base(s, cs, prm.t32, prm.t64, l, b, f);
                 if (!sparse && !mark_stencil(s_row + cs.row0, nullptr, cs, b)) s_flag = 1;
                 if (sparse && !in_box(cs, b)) s_flag = 1;
                 ra0[m] = make_float4(f[0], f[1], f[2],
@@ -1326,7 +1444,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                     const CS &cs = s_cs[s_ps[s_chunk[m >> 5]].cl];
                     const int b[3] = {(int)(bp & 1023u), (int)((bp >> 10) & 1023u), (int)(bp >> 20)};
                     int sl[9];
-                    row_slots(s_row + cs.row0, bt.rix, cs.W, cs.By, b, sl);
+                    row_slots(s_row + cs.row0, bt.rix, cs, b, sl);
                     rb[m] = make_uint4((unsigned)sl[0] | ((unsigned)sl[1] << 16), (unsigned)sl[2] | ((unsigned)sl[3] << 16),
                                        (unsigned)sl[4] | ((unsigned)sl[5] << 16), (unsigned)sl[6] | ((unsigned)sl[7] << 16));
                     a.w = __uint_as_float((unsigned)sl[8]);

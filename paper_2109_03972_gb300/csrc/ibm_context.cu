@@ -133,7 +133,10 @@ ibm_status ibm_create(const ibm_config *cfg, void *cuda_stream, ibm_ctx **out) {
     *out = nullptr;
     if (!cfg || cfg->n_scenes < 1 || !cfg->dims) return IBM_ERR_INVALID_ARG;
     if (!(cfg->h > 0.0) || !std::isfinite(cfg->h)) return IBM_ERR_INVALID_ARG;
-    if (cfg->kernel_width != 3) return IBM_ERR_INVALID_ARG;
+    // four-point kernel (Sec. 2.2.3): plain path, forward only
+    if (cfg->kernel_width != 3 && cfg->kernel_width != 4) return IBM_ERR_INVALID_ARG;
+    if (cfg->kernel_width == 4 && (cfg->spread_mode != IBM_SPREAD_PLAIN || cfg->requires_grad))
+        return IBM_ERR_INVALID_ARG;
     if (cfg->n_forcing < 1 || cfg->n_forcing > 64) return IBM_ERR_INVALID_ARG;
     if (cfg->precision != IBM_FP32 && cfg->precision != IBM_FP64) return IBM_ERR_INVALID_ARG;
     if (cfg->spread_mode < 0 || cfg->spread_mode > 2) return IBM_ERR_INVALID_ARG;

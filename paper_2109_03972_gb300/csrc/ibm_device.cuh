@@ -50,6 +50,24 @@ __device__ __forceinline__ void phi3_dweights(T f, T dw[3]) {
     dw[2] = (T(1) - q) * T(0.5);
 }
 
+// Four-point regularised delta (Sec. 2.2.3, the |r| form: the first branch
+// for |r| <= 1, the second for 1 <= |r| <= 2).  Its stencil starts one cell
+// below b = floor(xi - 1/2); with g = (xi - 1/2) - b in [0, 1) the four cells
+// sit at r = -1 - g, -g, 1 - g, 2 - g, and the radicands of both branches at
+// these offsets are the same number 1 + 4g - 4g^2, so
+//   phi4(-1-g) = (3 - 2g - q)/8,  phi4(-g)  = (3 - 2g + q)/8,
+//   phi4(1-g)  = (1 + 2g + q)/8,  phi4(2-g) = (1 + 2g - q)/8,
+// q = sqrt(1 + 4g - 4g^2): one square root per axis, and the four weights
+// sum to 1 by construction.
+template <typename T>
+__device__ __forceinline__ void phi4_weights(T g, T w[4]) {
+    const T q = sqrt(T(1) + T(4) * g - T(4) * g * g);
+    w[0] = (T(3) - T(2) * g - q) * T(0.125);
+    w[1] = (T(3) - T(2) * g + q) * T(0.125);
+    w[2] = (T(1) + T(2) * g + q) * T(0.125);
+    w[3] = (T(1) + T(2) * g - q) * T(0.125);
+}
+
 __device__ __forceinline__ int wrapi(int i, int n) {
     int m = i % n;
     return m < 0 ? m + n : m;
@@ -79,6 +97,29 @@ __device__ __forceinline__ int marker_split32(const PInfo &P, const float *t32, 
     }
     *frac = fr;
     return P.base[c] + (int)fl;
+}
+
+// FP32 split of xi - 1/2 (the four-point kernel's base and fraction), from
+// the three-point split of xi; within the FP32 error bound of a half-integer
+// the coordinate is recomputed in FP64, so the base is exactly floor(xi - 1/2)
+// of the FP64 position.
+__device__ __forceinline__ int marker_split32_half(const PInfo &P, const float *t32, const double *t64, int c,
+                                                   float *g) {
+    float f;
+    const int b = marker_split32(P, t32, t64, c, &f);
+    const float tol = 8.0f * 5.9604645e-8f * (P.af + 2.0f);
+    if (fabsf(f - 0.5f) < tol) {
+        const double xh = marker_xi64(P, t64, c) - 0.5;
+        const double fb = floor(xh);
+        *g = (float)(xh - fb);
+        return (int)fb;
+    }
+    if (f >= 0.5f) {
+        *g = f - 0.5f;
+        return b;
+    }
+    *g = f + 0.5f;
+    return b - 1;
 }
 
 template <typename T>

@@ -142,11 +142,13 @@ __global__ void k_pinfo(int n_p, const double *x, const double *up, const double
 
 // ------------------------------------------------------- marker evaluation
 
-template <typename T>
+// K = 3: base b = floor(xi), cells b-1..b+1, Eq. (3pt-stencil).  K = 4:
+// b = floor(xi - 1/2), cells b-1..b+2, the four-point kernel of Sec. 2.2.3.
+template <typename T, int K = 3>
 struct Stencil {
-    int b[3];      // absolute (unwrapped) base cell floor(xi)
-    T w[3][3];     // [axis][cell b-1, b, b+1]
-    T f[3];        // xi - b
+    int b[3];      // absolute (unwrapped) base cell
+    T w[3][K];     // [axis][cell b-1, b, ...]
+    T f[3];        // fraction: xi - b (K = 3), xi - 1/2 - b (K = 4)
 };
 
 __device__ __forceinline__ void marker_stencil(const PInfo &P, const double *t64, const float *,
@@ -169,6 +171,29 @@ __device__ __forceinline__ void marker_stencil(const PInfo &P, const double *t64
         S.b[c] = marker_split32(P, t32, t64, c, &fr);
         S.f[c] = fr;
         phi3_weights(fr, S.w[c]);
+    }
+}
+
+__device__ __forceinline__ void marker_stencil(const PInfo &P, const double *t64, const float *,
+                                               Stencil<double, 4> &S) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double xh = marker_xi64(P, t64, c) - 0.5;
+        const double fb = floor(xh);
+        S.b[c] = (int)fb;
+        S.f[c] = xh - fb;
+        phi4_weights<double>(S.f[c], S.w[c]);
+    }
+}
+
+__device__ __forceinline__ void marker_stencil(const PInfo &P, const double *t64, const float *t32,
+                                               Stencil<float, 4> &S) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float g;
+        S.b[c] = marker_split32_half(P, t32, t64, c, &g);
+        S.f[c] = g;
+        phi4_weights<float>(g, S.w[c]);
     }
 }
 
@@ -236,7 +261,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[32]) {
 // FB (deterministic fallback): also the per-cluster maxima of |u| over the
 // stencil cells, of |e| and of D (float bits in cm[3c..3c+2], atomicMax), from
 // which the spreading's fixed-point scale follows.
-template <typename T, bool FB = false>
+template <typename T, bool FB = false, int K = 3>
 __global__ void __launch_bounds__(kBlock) k_plain_interp(
     const PInfo *__restrict__ P, const int *__restrict__ plist, int n_list, const int *__restrict__ n_list_d,
     const double *__restrict__ t64, const float *__restrict__ t32, const double *__restrict__ up,
@@ -255,24 +280,24 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
         for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Pp.nl; l += gridDim.x * blockDim.x) {
             const double *tt64 = t64 + 3ll * (Pp.toff + l);
             const float *tt32 = t32 + 3ll * (Pp.toff + l);
-            Stencil<T> S;
+            Stencil<T, K> S;
             marker_stencil(Pp, tt64, tt32, S);
             T ud[3], r[3], D;
             marker_kinematics(up, om, p, Pp, tt64, tt32, ud, r, D);
             T U[3] = {T(0), T(0), T(0)};
-            int ii[3];
+            int ii[K];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) ii[a] = wrapi(S.b[0] - 1 + a, g.nx);
+            for (int a = 0; a < K; ++a) ii[a] = wrapi(S.b[0] - 1 + a, g.nx);
 #pragma unroll
-            for (int cz = 0; cz < 3; ++cz) {
+            for (int cz = 0; cz < K; ++cz) {
                 const int kk = wrapi(S.b[2] - 1 + cz, g.nz);
 #pragma unroll
-                for (int cy = 0; cy < 3; ++cy) {
+                for (int cy = 0; cy < K; ++cy) {
                     const int jj = wrapi(S.b[1] - 1 + cy, g.ny);
                     const long long row = ((long long)kk * g.ny + jj) * g.nx;
                     const T wyz = S.w[2][cz] * S.w[1][cy];
 #pragma unroll
-                    for (int cx = 0; cx < 3; ++cx) {
+                    for (int cx = 0; cx < K; ++cx) {
                         const T w = wyz * S.w[0][cx];
                         const long long idx = row + ii[cx];
 #pragma unroll
@@ -386,7 +411,7 @@ __global__ void __launch_bounds__(kBlock) k_fb_convert(const PInfo *__restrict__
 // u += scale * sum_l w D_l v_l for v = e (scale 1).  Optional f_out += that / tau.
 // FB (deterministic fallback, FP32): the cells hold the cluster's fixed point
 // (k_fb_convert) and the contributions are added as rounded integers.
-template <typename T, bool FB = false>
+template <typename T, bool FB = false, int K = 3>
 __global__ void __launch_bounds__(kBlock) k_plain_spread(
     const PInfo *__restrict__ P, const int *__restrict__ plist, int n_list, const int *__restrict__ n_list_d,
     const double *__restrict__ t64, const float *__restrict__ t32, const int32_t *__restrict__ dims,
@@ -409,7 +434,7 @@ __global__ void __launch_bounds__(kBlock) k_plain_spread(
         for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Pp.nl; l += gridDim.x * blockDim.x) {
             const double *tt64 = t64 + 3ll * (Pp.toff + l);
             const float *tt32 = t32 + 3ll * (Pp.toff + l);
-            Stencil<T> S;
+            Stencil<T, K> S;
             marker_stencil(Pp, tt64, tt32, S);
             const T D = sizeof(T) == 8 ? (T)Pp.D64 : (T)Pp.D;
             T gv[3];
@@ -417,19 +442,19 @@ __global__ void __launch_bounds__(kBlock) k_plain_spread(
             for (int q = 0; q < 3; ++q) gv[q] = scale * D * vbuf[3ll * (Pp.moff + l) + q];
             float fs = 1.f, finv_s = 0.f;
             if (FB) fs = fb_scale(cm, pcl[p], &finv_s);
-            int ii[3];
+            int ii[K];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) ii[a] = wrapi(S.b[0] - 1 + a, g.nx);
+            for (int a = 0; a < K; ++a) ii[a] = wrapi(S.b[0] - 1 + a, g.nx);
 #pragma unroll
-            for (int cz = 0; cz < 3; ++cz) {
+            for (int cz = 0; cz < K; ++cz) {
                 const int kk = wrapi(S.b[2] - 1 + cz, g.nz);
 #pragma unroll
-                for (int cy = 0; cy < 3; ++cy) {
+                for (int cy = 0; cy < K; ++cy) {
                     const int jj = wrapi(S.b[1] - 1 + cy, g.ny);
                     const long long row = ((long long)kk * g.ny + jj) * g.nx;
                     const T wyz = S.w[2][cz] * S.w[1][cy];
 #pragma unroll
-                    for (int cx = 0; cx < 3; ++cx) {
+                    for (int cx = 0; cx < K; ++cx) {
                         const T w = wyz * S.w[0][cx];
                         const long long idx = row + ii[cx];
 #pragma unroll
@@ -450,7 +475,7 @@ __global__ void __launch_bounds__(kBlock) k_plain_spread(
 
 // Slip after the loop: eps_l = |U^d - W u^{n_F}| (Sec. 2.2.2); sum of squares
 // and maximum over all markers.
-template <typename T>
+template <typename T, int K = 3>
 __global__ void __launch_bounds__(kBlock) k_slip(const PInfo *__restrict__ P, int n_p,
                                                  const double *__restrict__ t64, const float *__restrict__ t32,
                                                  const double *__restrict__ up, const double *__restrict__ om,
@@ -466,18 +491,18 @@ __global__ void __launch_bounds__(kBlock) k_slip(const PInfo *__restrict__ P, in
         for (int l = threadIdx.x; l < Pp.nl; l += blockDim.x) {
             const double *tt64 = t64 + 3ll * (Pp.toff + l);
             const float *tt32 = t32 + 3ll * (Pp.toff + l);
-            Stencil<T> S;
+            Stencil<T, K> S;
             marker_stencil(Pp, tt64, tt32, S);
             T ud[3], r[3], D;
             marker_kinematics(up, om, p, Pp, tt64, tt32, ud, r, D);
             // evaluated in the path's own precision T; summed over markers in FP64
             T U[3] = {T(0), T(0), T(0)};
-            for (int cz = 0; cz < 3; ++cz) {
+            for (int cz = 0; cz < K; ++cz) {
                 const int kk = wrapi(S.b[2] - 1 + cz, g.nz);
-                for (int cy = 0; cy < 3; ++cy) {
+                for (int cy = 0; cy < K; ++cy) {
                     const int jj = wrapi(S.b[1] - 1 + cy, g.ny);
                     const long long row = ((long long)kk * g.ny + jj) * g.nx;
-                    for (int cx = 0; cx < 3; ++cx) {
+                    for (int cx = 0; cx < K; ++cx) {
                         const T w = S.w[2][cz] * S.w[1][cy] * S.w[0][cx];
                         const long long idx = row + wrapi(S.b[0] - 1 + cx, g.nx);
                         for (int q = 0; q < 3; ++q) U[q] += w * u[q * g.ncell + idx];
@@ -545,13 +570,13 @@ __global__ void k_finalize(int n_p, const double *FD, const double *TD, double h
     }
 }
 
-template <typename T>
+template <typename T, int K = 3>
 __global__ void k_marker_bases(const PInfo *__restrict__ P, int n_p, const double *t64, const float *t32,
                                int64_t *out) {
     for (int p = blockIdx.x; p < n_p; p += gridDim.x) {
         const PInfo Pp = P[p];
         for (int l = threadIdx.x; l < Pp.nl; l += blockDim.x) {
-            Stencil<T> S;
+            Stencil<T, K> S;
             marker_stencil(Pp, t64 + 3ll * (Pp.toff + l), t32 + 3ll * (Pp.toff + l), S);
             for (int c = 0; c < 3; ++c) out[3ll * (Pp.moff + l) + c] = S.b[c];
         }
@@ -856,11 +881,17 @@ ibm_status launch_pinfo(ibm_ctx *ctx) {
 ibm_status launch_marker_bases(ibm_ctx *ctx, int64_t *base_d) {
     const int nb = blocks_for_particles(ctx->n_p);
     if (ctx->cfg.precision == IBM_FP64)
-        k_marker_bases<double><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32,
-                                                               base_d);
+        ctx->cfg.kernel_width == 4
+            ? k_marker_bases<double, 4><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64,
+                                                                        ctx->tmpl32, base_d)
+            : k_marker_bases<double><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64,
+                                                                     ctx->tmpl32, base_d);
     else
-        k_marker_bases<float><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32,
-                                                              base_d);
+        ctx->cfg.kernel_width == 4
+            ? k_marker_bases<float, 4><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64,
+                                                                       ctx->tmpl32, base_d)
+            : k_marker_bases<float><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64,
+                                                                    ctx->tmpl32, base_d);
     return ibm_cuda_check(ctx, cudaGetLastError(), "marker bases");
 }
 
@@ -933,13 +964,22 @@ static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, co
         ctx->launches += 4;
         return IBM_OK;
     }
-    k_plain_interp<T><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
-                                                        ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, uf,
-                                                        reinterpret_cast<T *>(ctx->ebuf), ctx->cbuf);
-    k_plain_spread<T><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
-                                                        ctx->tmpl32, ctx->dims_d,
-                                                        reinterpret_cast<const T *>(ctx->ebuf), T(1), uf, ff,
-                                                        T(1.0 / tau), ctx->cbuf, ctx->FD, ctx->TD);
+    if (ctx->cfg.kernel_width == 4) {
+        k_plain_interp<T, false, 4><<<grid, kBlock, 0, ctx->stream>>>(
+            ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, uf,
+            reinterpret_cast<T *>(ctx->ebuf), ctx->cbuf);
+        k_plain_spread<T, false, 4><<<grid, kBlock, 0, ctx->stream>>>(
+            ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->dims_d,
+            reinterpret_cast<const T *>(ctx->ebuf), T(1), uf, ff, T(1.0 / tau), ctx->cbuf, ctx->FD, ctx->TD);
+    } else {
+        k_plain_interp<T><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
+                                                            ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, uf,
+                                                            reinterpret_cast<T *>(ctx->ebuf), ctx->cbuf);
+        k_plain_spread<T><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
+                                                            ctx->tmpl32, ctx->dims_d,
+                                                            reinterpret_cast<const T *>(ctx->ebuf), T(1), uf, ff,
+                                                            T(1.0 / tau), ctx->cbuf, ctx->FD, ctx->TD);
+    }
     ctx->launches += 2;
     return IBM_OK;
 }
@@ -974,13 +1014,25 @@ ibm_status plain_slip(ibm_ctx *ctx, void *const *u_ptrs) {
     if (s != IBM_OK) return s;
     const int nb = blocks_for_particles(ctx->n_p);
     if (ctx->cfg.precision == IBM_FP64)
-        k_slip<double><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32, ctx->up,
-                                                       ctx->om, ctx->dims_d,
-                                                       reinterpret_cast<double *const *>(ctx->uptr_d), ctx->slip_acc);
+        ctx->cfg.kernel_width == 4
+            ? k_slip<double, 4><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32,
+                                                                ctx->up, ctx->om, ctx->dims_d,
+                                                                reinterpret_cast<double *const *>(ctx->uptr_d),
+                                                                ctx->slip_acc)
+            : k_slip<double><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32,
+                                                             ctx->up, ctx->om, ctx->dims_d,
+                                                             reinterpret_cast<double *const *>(ctx->uptr_d),
+                                                             ctx->slip_acc);
     else
-        k_slip<float><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32, ctx->up,
-                                                      ctx->om, ctx->dims_d,
-                                                      reinterpret_cast<float *const *>(ctx->uptr_d), ctx->slip_acc);
+        ctx->cfg.kernel_width == 4
+            ? k_slip<float, 4><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32,
+                                                               ctx->up, ctx->om, ctx->dims_d,
+                                                               reinterpret_cast<float *const *>(ctx->uptr_d),
+                                                               ctx->slip_acc)
+            : k_slip<float><<<nb, kBlock, 0, ctx->stream>>>(ctx->pinfo, ctx->n_p, ctx->tmpl64, ctx->tmpl32,
+                                                            ctx->up, ctx->om, ctx->dims_d,
+                                                            reinterpret_cast<float *const *>(ctx->uptr_d),
+                                                            ctx->slip_acc);
     return ibm_cuda_check(ctx, cudaGetLastError(), "slip");
 }
 

@@ -44,7 +44,9 @@ def test_create_rejects_bad_config_without_touching_gpu():
     dims = (ctypes.c_int32 * 3)(32, 32, 32)
     for bad in ({"h": -1.0}, {"kernel_width": 5}, {"n_forcing": 0}, {"precision": 9},
                 {"max_particles": 0}, {"precision": ibm.IBM_FP64, "spread_mode": ibm.IBM_SPREAD_CLUSTER},
-                {"threads_per_block": 256}, {"threads_per_block": -2}):
+                {"threads_per_block": 256}, {"threads_per_block": -2},
+                {"kernel_width": 4, "spread_mode": ibm.IBM_SPREAD_DETERMINISTIC},
+                {"kernel_width": 4, "requires_grad": 1}):
         c = ibm._Config()
         c.n_scenes, c.dims, c.h, c.kernel_width, c.n_forcing = 1, dims, 1.0, 3, 3
         c.precision, c.spread_mode, c.max_particles = ibm.IBM_FP32, ibm.IBM_SPREAD_PLAIN, 4

@@ -365,3 +365,66 @@ def test_deterministic_fallback_is_bit_reproducible_and_matches_oracle(oracle_mo
         b = run_gpu(sc, u0, ibm.IBM_FP32, ibm.IBM_SPREAD_DETERMINISTIC)
         assert np.array_equal(a["u"], b["u"])
         assert np.array_equal(a["F"], b["F"]) and np.array_equal(a["T"], b["T"])
+
+
+def _ring_scene(axis):
+    # four D=10 spheres at the minimum gap spaced 11 cells apart along one axis of
+    # a 44-cell period: a cluster that closes on itself across the seam
+    dims = [36, 40, 38]
+    dims[axis] = 44
+    x = np.tile(np.array([17.3, 19.6, 18.2]), (4, 1))
+    x[:, axis] = 3.7 + 11.0 * np.arange(4)
+    u_p, om, rho = synth.particle_state(4, 41 + axis)
+    return synth.Scene(tuple(dims), x, np.full(4, 10.0), u_p, om, rho, field_seed=43 + axis)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("mode", [ibm.IBM_SPREAD_CLUSTER, ibm.IBM_SPREAD_DETERMINISTIC])
+def test_periodic_cluster_in_shared_memory(oracle_mod, axis, mode):
+    # the ring cannot be unwrapped: its box is the whole period along that axis
+    # (ghost columns in x), and it must still run in the shared-memory kernel
+    sc = _ring_scene(axis)
+    u0 = f32_round(sc.field())
+    ref = _oracle_run(oracle_mod, sc, u0)
+    got = run_gpu(sc, u0, ibm.IBM_FP32, mode)
+    st = got["ctx"].stats()
+    assert st["clusters"] == 1 and st["markers_fallback"] == 0
+    assert rel_err_u(got["u"], ref["u"], u0) <= U_TOL32
+    assert load_err(got["F"], ref["F"], ref["Fabs"]) <= LOAD_TOL32
+    assert load_err(got["T"], ref["T"], 0.5 * sc.d_p * ref["Fabs"]) <= LOAD_TOL32
+    if mode == ibm.IBM_SPREAD_DETERMINISTIC:
+        again = run_gpu(sc, u0, ibm.IBM_FP32, mode)
+        assert np.array_equal(got["u"], again["u"])
+
+
+@pytest.mark.parametrize("k", [2, 8])
+def test_dense_small_box_matches_oracle(oracle_mod, k):
+    # dense 32^3 scenes of the batched workload: clusters wrap in several axes
+    sc = synth.workload("batched", n_scenes=k + 1).scenes[k]
+    u0 = f32_round(sc.field())
+    ref = _oracle_run(oracle_mod, sc, u0)
+    got = run_gpu(sc, u0, ibm.IBM_FP32, ibm.IBM_SPREAD_DETERMINISTIC)
+    assert got["ctx"].stats()["markers_fallback"] == 0
+    assert rel_err_u(got["u"], ref["u"], u0) <= U_TOL32
+    assert load_err(got["F"], ref["F"], ref["Fabs"]) <= LOAD_TOL32
+
+
+@pytest.mark.parametrize("name", ["small", "single64", "chain"])
+@pytest.mark.parametrize("precision", [ibm.IBM_FP64, ibm.IBM_FP32])
+def test_four_point_kernel_matches_oracle(oracle_mod, name, precision):
+    # the four-point kernel of Sec. 2.2.3 on the plain path: bins bit-exact,
+    # FP64 at 1e-12, FP32 at the FP32 tolerances
+    sc = SCENES[name]()
+    from tests._helpers import gpu_context
+    ctx = gpu_context([sc.dims], sc.n_p, precision, ibm.IBM_SPREAD_PLAIN, width=4)
+    ctx.set_particles(sc.x_p, sc.u_p, sc.omega_p, sc.d_p)
+    xi, base = oracle_mod.marker_positions(sc.x_p, sc.d_p, width=4)
+    assert np.array_equal(ctx.marker_bases(), base)
+    u0 = sc.field() if precision == ibm.IBM_FP64 else f32_round(sc.field())
+    ref = oracle_mod.forcing_step(u0, sc.x_p, sc.u_p, sc.omega_p, sc.d_p, n_forcing=3, tau=0.01, width=4)
+    got = run_gpu(sc, u0, precision, ibm.IBM_SPREAD_PLAIN, width=4)
+    tu, tl = (1e-12, 1e-12) if precision == ibm.IBM_FP64 else (U_TOL32, LOAD_TOL32)
+    assert rel_err_u(got["u"], ref["u"], u0) <= tu
+    assert load_err(got["F"], ref["F"], ref["Fabs"]) <= tl
+    assert load_err(got["T"], ref["T"], 0.5 * sc.d_p * ref["Fabs"]) <= tl
+    assert got["slip"][0] == pytest.approx(ref["slip"][0], rel=1e-10 if precision == ibm.IBM_FP64 else SLIP_TOL32)

@@ -492,3 +492,54 @@ def test_backward_finite_differences(oracle):
         a2 = u0.copy(); a2[k] -= eps
         fd = (_loss(oracle, a1, x_p, u_p, om, d_p, wgt)[0] - _loss(oracle, a2, x_p, u_p, om, d_p, wgt)[0]) / (2 * eps)
         assert abs(fd - gi[k]) <= 1e-6 * max(1.0, np.abs(gi).max())
+
+
+# ------------------------------------------- four-point kernel (Sec. 2.2.3)
+
+def test_four_point_stencil_equals_brute_force(oracle):
+    # the 4-cell stencil (base floor(xi - 1/2)) against delta at every cell
+    dims = (10, 9, 11)
+    x_p, d_p, u_p, om, u = _small_problem(seed=5, dims=dims)
+    a = oracle.forcing_step(u, x_p, u_p, om, d_p, want_f=True, width=4)
+    b = oracle.forcing_step(u, x_p, u_p, om, d_p, want_f=True, width=4, brute=True)
+    for k in ("u", "F", "T", "f"):
+        assert np.allclose(a[k], b[k], rtol=0, atol=1e-12 * max(1.0, np.abs(b[k]).max()))
+
+
+def test_four_point_interp_matches_dense_W(oracle):
+    dims = (9, 8, 10)
+    x_p, d_p, u_p, om, u = _small_problem(seed=13, dims=dims, n=3)
+    W = _dense_W(oracle, dims, x_p, d_p, kernel="phi4")
+    U = oracle.interpolate(u, x_p, d_p, width=4)
+    Ud = np.stack([W @ u[c].ravel() for c in range(3)], 1)
+    assert np.allclose(U, Ud, atol=1e-13)
+
+
+def test_four_point_interp_linear_exact(oracle):
+    # phi4 has unit mass and zero first moment (Sec. 2.2.3): linear fields are exact
+    dims = (32, 32, 32)
+    x_p = np.array([[16.2, 15.7, 16.9]])
+    d_p = np.array([12.0])
+    z, y, x = np.meshgrid(*(np.arange(32) + 0.5,) * 3, indexing="ij")
+    A = np.array([[0.3, -1.2, 0.7], [2.0, 0.1, -0.4], [-0.5, 0.25, 1.5]])
+    b = np.array([0.2, -0.3, 1.1])
+    u = np.stack([A[c, 0] * x + A[c, 1] * y + A[c, 2] * z + b[c] for c in range(3)])
+    U = oracle.interpolate(u, x_p, d_p, width=4)
+    xi, base = oracle.marker_positions(x_p, d_p, width=4)
+    assert np.array_equal(base, np.floor(xi - 0.5).astype(np.int64))
+    assert np.abs(U - (xi @ A.T + b)).max() < 1e-12
+
+
+def test_four_point_spread_is_weighted_adjoint(oracle):
+    dims = (12, 10, 14)
+    h = 0.5
+    rng = np.random.default_rng(17)
+    x_p = rng.uniform(0, 1, size=(3, 3)) * np.array(dims) * h
+    d_p = np.array([2.0, 1.5, 2.5])
+    n = sum(oracle.marker_count(d, h) for d in d_p)
+    F = rng.normal(size=(n, 3))
+    v = rng.normal(size=(3, 14, 10, 12))
+    f = oracle.spread(F, dims, x_p, d_p, h=h, width=4)
+    Wv = oracle.interpolate(v, x_p, d_p, h=h, width=4)
+    dv = np.concatenate([[oracle.marker_volume(d, h)] * oracle.marker_count(d, h) for d in d_p])
+    assert h ** 3 * (f * v).sum() == pytest.approx((dv[:, None] * F * Wv).sum(), rel=1e-12)
