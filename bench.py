@@ -158,7 +158,8 @@ def scene_arrays(W):
 def cpu_sample(W, target_s, rng_seed=7):
     """Bounded sample of the workload for the oracle: the particles whose centres
     lie in a cubic sub-box of edge S (a periodic S^3 grid of its own), S chosen so
-    one oracle step takes about target_s seconds on one core."""
+    one oracle step takes about target_s seconds on the oracle's threads (all host
+    cores unless OMP_NUM_THREADS says otherwise)."""
     from oracle import oracle as O
     from paper_2109_03972_gb300 import synth
     sc = W.scenes[0]
@@ -180,6 +181,21 @@ def cpu_sample(W, target_s, rng_seed=7):
     grow = (target_s / max(t1, 1e-3)) ** (1.0 / 3.0)
     S2 = int(min(min(nx, ny, nz), max(S, int(S * grow) // 16 * 16)))
     return sub(S2), S2
+
+
+def host_desc():
+    """Host CPU of the oracle timing: architecture, logical cores, model name."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{platform.machine()}, {os.cpu_count()} logical cores" + (f", {model}" if model else "")
 
 
 def time_oracle(scene, W, steps):
@@ -215,7 +231,8 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD_DESC[args.workload], "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                             "sample": sample, "host": host_desc()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -382,7 +399,8 @@ def our_arm(args):
             nm_cpu, t = time_oracle(scene, W, 3)
             cms = float(np.mean(t)) * 1e3
             line["cpu_baseline"] = {
-                "value": nm_cpu * W.n_forcing / (cms / 1e3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "value": nm_cpu * W.n_forcing / (cms / 1e3), "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                "host": host_desc(),
                 "sample": f"particles with centres in a {S}^3 sub-box of the bed ({scene.n_p} spheres, "
                           f"{nm_cpu} markers) on a periodic {S}^3 grid; 3 steps, {cms:.0f} ms/step"}
     if args.backward:

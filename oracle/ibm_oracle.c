@@ -27,6 +27,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORA_PI 3.14159265358979323846
 
@@ -222,6 +225,8 @@ static void ora_interp_all(int width, int mode, long nx, long ny, long nz,
                            const double *u, const ora_markers *M, double *U)
 {
     const long ncell = nx * ny * nz;
+    /* markers are independent: parallel over markers, results as in serial */
+#pragma omp parallel for schedule(static) if (mode == 0)
     for (long m = 0; m < M->n; ++m) {
         double acc[3] = {0.0, 0.0, 0.0};
         const double *xi = M->xi + 3 * m;
@@ -261,6 +266,47 @@ static void ora_spread_all(int width, int mode, long nx, long ny, long nz,
                            const ora_markers *M, const double *F, double *f)
 {
     const long ncell = nx * ny * nz;
+    if (mode == 0) {
+        /* Each thread owns a range of whole k-planes and visits every marker in
+         * order, adding only to its own planes: every cell receives its
+         * contributions in marker order, exactly as in the serial loop. */
+#pragma omp parallel
+        {
+            long k0 = 0, k1 = nz;
+#ifdef _OPENMP
+            const int nt = omp_get_num_threads(), t = omp_get_thread_num();
+            k0 = nz * t / nt;
+            k1 = nz * (t + 1) / nt;
+#endif
+            for (long m = 0; m < M->n; ++m) {
+                const double *xi = M->xi + 3 * m;
+                double wx[4], wy[4], wz[4];
+                long fz = ora_axis_stencil(width, xi[2], wz, NULL);
+                int any = 0;
+                for (int c = 0; c < width; ++c) {
+                    long k = iwrap(fz + c, nz);
+                    if (k >= k0 && k < k1) any = 1;
+                }
+                if (!any) continue;
+                long fx = ora_axis_stencil(width, xi[0], wx, NULL);
+                long fy = ora_axis_stencil(width, xi[1], wy, NULL);
+                double g[3];
+                for (int q = 0; q < 3; ++q) g[q] = F[3 * m + q] * M->D[m];
+                for (int c = 0; c < width; ++c) {
+                    long k = iwrap(fz + c, nz);
+                    if (k < k0 || k >= k1) continue;
+                    for (int b = 0; b < width; ++b)
+                        for (int a = 0; a < width; ++a) {
+                            long i = iwrap(fx + a, nx), j = iwrap(fy + b, ny);
+                            long idx = i + nx * (j + ny * k);
+                            double w = wx[a] * wy[b] * wz[c];
+                            for (int q = 0; q < 3; ++q) f[q * ncell + idx] += w * g[q];
+                        }
+                }
+            }
+        }
+        return;
+    }
     for (long m = 0; m < M->n; ++m) {
         const double *xi = M->xi + 3 * m;
         double g[3];
@@ -422,10 +468,13 @@ int ora_forcing_step(int width, int mode, long nx, long ny, long nz, double h,
         for (long m = 0; m < M.n; ++m)
             for (int q = 0; q < 3; ++q)
                 F[3 * m + q] = (M.Ud[3 * m + q] - U[3 * m + q]) / tau;
-        memset(f, 0, sizeof(double) * 3 * (size_t)ncell);
+#pragma omp parallel for schedule(static)
+        for (long c = 0; c < 3 * ncell; ++c) f[c] = 0.0;
         ora_spread_all(width, mode, nx, ny, nz, &M, F, f);
+#pragma omp parallel for schedule(static)
         for (long c = 0; c < 3 * ncell; ++c) u[c] += tau * f[c];
         if (f_tot)
+#pragma omp parallel for schedule(static)
             for (long c = 0; c < 3 * ncell; ++c) f_tot[c] += f[c];
         for (long m = 0; m < M.n; ++m) {
             long p = M.pid[m];
@@ -457,6 +506,19 @@ int ora_forcing_step(int width, int mode, long nx, long ny, long nz, double h,
     free(U); free(F); free(f);
     ora_free_markers(&M);
     return 0;
+}
+
+/* Number of OpenMP threads of the oracle (1 without OpenMP); n > 0 sets it.
+ * The results do not depend on it. */
+int ora_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* Rigid-body Newton-Euler update of Eq. (basic-particle a-c) with no collision

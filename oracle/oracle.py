@@ -2,7 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
 CPU-baseline leg load this module; the GPU library never does.  It builds
-``liboracle.so`` next to the C source with plain ``cc -O2 -ffp-contract=off``.
+``liboracle.so`` next to the C source with plain ``cc -O2 -ffp-contract=off``
+and OpenMP (interpolation over markers, spreading over owned z-slabs; the
+results do not depend on the thread count).
 """
 from __future__ import annotations
 
@@ -31,7 +33,7 @@ def build(force: bool = False) -> str:
         if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
             tmp = LIB + f".{os.getpid()}.tmp"
             cc = os.environ.get("CC", "cc")
-            subprocess.check_call([cc, "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+            subprocess.check_call([cc, "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                    "-o", tmp, SRC, "-lm"])
             os.replace(tmp, LIB)
     return LIB
@@ -52,6 +54,7 @@ def lib():
         L.ora_interpolate.argtypes = [_i, _i, _l, _l, _l, _d, _l, _p, _p, _p, _p]
         L.ora_spread.restype = _l
         L.ora_spread.argtypes = [_i, _i, _l, _l, _l, _d, _l, _p, _p, _p, _p]
+        L.ora_threads.restype, L.ora_threads.argtypes = _i, [_i]
         L.ora_marker_positions.restype = _l
         L.ora_marker_positions.argtypes = [_i, _d, _l, _p, _p, _p, _p]
         L.ora_touched_count.restype = _l
@@ -124,6 +127,11 @@ def spread(F, dims, x_p, d_p, h=1.0, width=3, brute=False):
     lib().ora_spread(width, int(brute), nx, ny, nz, h, d_p.size, _ptr(x_p), _ptr(d_p),
                      _ptr(F), _ptr(f))
     return f
+
+
+def threads(n: int = 0) -> int:
+    """OpenMP threads of the oracle; n > 0 sets the count.  Returns the count."""
+    return int(lib().ora_threads(int(n)))
 
 
 def marker_positions(x_p, d_p, h=1.0, width=3):

@@ -543,3 +543,25 @@ def test_four_point_spread_is_weighted_adjoint(oracle):
     Wv = oracle.interpolate(v, x_p, d_p, h=h, width=4)
     dv = np.concatenate([[oracle.marker_volume(d, h)] * oracle.marker_count(d, h) for d in d_p])
     assert h ** 3 * (f * v).sum() == pytest.approx((dv[:, None] * F * Wv).sum(), rel=1e-12)
+
+
+def test_threaded_oracle_is_bitwise_serial(oracle):
+    # interpolation over markers, spreading over owned z-slabs in marker order:
+    # the thread count does not change a bit
+    dims = (20, 18, 22)
+    rng = np.random.default_rng(21)
+    x_p = rng.uniform(0, 1, size=(4, 3)) * np.array(dims)
+    d_p = rng.uniform(4.0, 7.0, size=4)
+    u_p = rng.normal(0, 0.3, size=(4, 3))
+    om = rng.normal(0, 0.3, size=(4, 3))
+    u = rng.normal(0, 1, size=(3, dims[2], dims[1], dims[0]))
+    n0 = oracle.threads()
+    try:
+        oracle.threads(1)
+        a = oracle.forcing_step(u, x_p, u_p, om, d_p, want_f=True)
+        oracle.threads(4)
+        b = oracle.forcing_step(u, x_p, u_p, om, d_p, want_f=True)
+    finally:
+        oracle.threads(n0)
+    for k in ("u", "F", "T", "f", "slip"):
+        assert np.array_equal(a[k], b[k]), k
