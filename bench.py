@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--workload", default="bidisperse", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--mode", default="deterministic", choices=["cluster", "deterministic", "plain"])
     ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = default, -1 = autotune)")
-    ap.add_argument("--graph", action="store_true", help="replay the step from a CUDA graph")
+    ap.add_argument("--graph", dest="graph", action="store_true", default=True,
+                    help="replay the step from a CUDA graph (default)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false", help="launch the step eagerly")
     ap.add_argument("--backward", action="store_true",
                     help="also time forward + adjoint (ibm_backward) steps, FP32 and FP64")
     ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")

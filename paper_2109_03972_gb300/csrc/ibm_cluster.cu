@@ -1244,25 +1244,28 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
             // a single cluster whose dense row table is too large gets a sparse one
             const bool sparse = bt.nb == 1 && bt.R > prm.max_rows;
             uint2 *s_row = s_row0;
-            // particle table, sorted by global index (fixed marker numbering)
-            if (tid < np) {
-                const int j = [&] {
+            // particle table, sorted by global index (fixed marker numbering): warp 0,
+            // lane i ranks its particle among the batch's (np <= 32, indices distinct)
+            if (tid < 32) {
+                int gid = INT_MAX, cl = 0;
+                if (tid < np) {
                     int lo = 0, hi = bt.nb - 1;
-                    while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (s_cs[mid].pstart <= tid) lo = mid; else hi = mid - 1; }
-                    return lo;
-                }();
-                s_ps[tid].gid = prm.cl_plist[s_cs[j].first + tid - s_cs[j].pstart];
-                s_ps[tid].cl = j;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                for (int i = 1; i < np; ++i) {
-                    const int v = s_ps[i].gid, vc = s_ps[i].cl;
-                    int j = i - 1;
-                    while (j >= 0 && s_ps[j].gid > v) { s_ps[j + 1].gid = s_ps[j].gid; s_ps[j + 1].cl = s_ps[j].cl; --j; }
-                    s_ps[j + 1].gid = v;
-                    s_ps[j + 1].cl = vc;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_cs[mid].pstart <= tid) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    cl = lo;
+                    gid = prm.cl_plist[s_cs[lo].first + tid - s_cs[lo].pstart];
                 }
+                int rank = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) rank += __shfl_sync(0xffffffffu, gid, j) < gid;
+                if (tid < np) {
+                    s_ps[rank].gid = gid;
+                    s_ps[rank].cl = cl;
+                }
+                if (tid < bt.nb) s_cs[tid].dmax = 0.f;
             }
             __syncthreads();
             if (tid < np) {
@@ -1277,15 +1280,21 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
             if (!sparse)
                 for (int i = tid; i < bt.R; i += TPB) s_row[i].x = 0u;
             __syncthreads();
-            if (tid == 0) {
-                int m = 0;
-                for (int i = 0; i < np; ++i) { s_ps[i].mstart = m; m += (s_ps[i].P.nl + 31) & ~31; }
-                s_nm = m;
-                for (int j = 0; j < bt.nb; ++j) s_cs[j].dmax = 0.f;
-                for (int i = 0; i < np; ++i) {
-                    CS &cs = s_cs[s_ps[i].cl];
-                    cs.dmax = fmaxf(cs.dmax, s_ps[i].P.D);
+            if (tid < 32) {
+                // first marker of each particle (padded to 32-marker chunks): warp scan;
+                // largest D of each cluster (non-negative float bits order like ints)
+                const int pad = tid < np ? (s_ps[tid].P.nl + 31) & ~31 : 0;
+                int inc = pad;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (tid >= o) inc += y;
                 }
+                if (tid < np) {
+                    s_ps[tid].mstart = inc - pad;
+                    atomicMax(reinterpret_cast<unsigned *>(&s_cs[s_ps[tid].cl].dmax), __float_as_uint(s_ps[tid].P.D));
+                }
+                if (tid == 31) s_nm = inc;
             }
             __syncthreads();
             bt.nm = s_nm;
