@@ -382,27 +382,31 @@ __global__ void __launch_bounds__(kBlock) k_fb_convert(const PInfo *__restrict__
         for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Pp.nl; l += gridDim.x * blockDim.x) {
             Stencil<float> st;
             marker_stencil(Pp, t64 + 3ll * (Pp.toff + l), t32 + 3ll * (Pp.toff + l), st);
-            for (int cz = 0; cz < 3; ++cz)
-                for (int cy = 0; cy < 3; ++cy)
-                    for (int cx = 0; cx < 3; ++cx) {
-                        const long long idx = ((long long)wrapi(st.b[2] - 1 + cz, g.nz) * g.ny +
-                                               wrapi(st.b[1] - 1 + cy, g.ny)) * g.nx + wrapi(st.b[0] - 1 + cx, g.nx);
-                        const long long gi = cell_off[Pp.scene] + idx;
-                        const unsigned bit = 1u << (gi & 31);
-                        if (TO) {
-                            if (atomicOr(bits + (gi >> 5), bit) & bit) continue;
-                            for (int q = 0; q < 3; ++q) {
-                                float *c = u + q * g.ncell + idx;
-                                *reinterpret_cast<int *>(c) = __float2int_rn(*c * S);
-                            }
-                        } else {
-                            if (!(atomicAnd(bits + (gi >> 5), ~bit) & bit)) continue;
-                            for (int q = 0; q < 3; ++q) {
-                                float *c = u + q * g.ncell + idx;
-                                *c = (float)*reinterpret_cast<const int *>(c) * inv;
-                            }
-                        }
-                    }
+            // claim the 27 cells first (independent atomics in flight), then convert
+            // the ones this marker claimed
+            auto cell = [&](int n) {
+                const int cx = n % 3, cy = (n / 3) % 3, cz = n / 9;
+                return ((long long)wrapi(st.b[2] - 1 + cz, g.nz) * g.ny + wrapi(st.b[1] - 1 + cy, g.ny)) * g.nx +
+                       wrapi(st.b[0] - 1 + cx, g.nx);
+            };
+            unsigned mine = 0u;
+#pragma unroll
+            for (int n = 0; n < 27; ++n) {
+                const long long gi = cell_off[Pp.scene] + cell(n);
+                const unsigned bit = 1u << (gi & 31);
+                const unsigned old = TO ? atomicOr(bits + (gi >> 5), bit) : atomicAnd(bits + (gi >> 5), ~bit);
+                if (TO ? !(old & bit) : (old & bit)) mine |= 1u << n;
+            }
+            while (mine) {
+                const int n = __ffs(mine) - 1;
+                mine &= mine - 1u;
+                const long long idx = cell(n);
+                for (int q = 0; q < 3; ++q) {
+                    float *c = u + q * g.ncell + idx;
+                    if (TO) *reinterpret_cast<int *>(c) = __float2int_rn(*c * S);
+                    else *c = (float)*reinterpret_cast<const int *>(c) * inv;
+                }
+            }
         }
     }
 }
