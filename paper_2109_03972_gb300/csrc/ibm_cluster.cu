@@ -14,9 +14,14 @@
 //      on the shared-memory copy, with __syncthreads between the phases,
 //   4. writes the touched cells back once, and the particle loads.
 // HBM sees one read and one write per touched cell per step instead of one
-// per iteration.  Clusters too large for one CTA's shared memory run the plain
-// FP32 path (one thread per marker, global atomics), which touches disjoint
-// cells and can therefore follow in any order.
+// per iteration.  Each marker's stencil is kept as a 32-byte record (fractional
+// position and the slots of its nine row runs), in shared memory when it fits
+// and in an L2-resident global scratch otherwise.  A cluster that cannot be
+// unwrapped along an axis of the periodic domain gets the whole period as its
+// box there (rows wrap in y and z, ghost columns in x).  Clusters too large for
+// one CTA's shared memory run the plain FP32 path (global atomics; in the
+// deterministic mode fixed point per cluster), which touches disjoint cells
+// and can therefore follow in any order.
 //
 // Clustering per step: particles are binned on a coarse grid, candidate pairs
 // (centre distance < a_p + a_q + 3 sqrt 3, the largest distance at which two
