@@ -66,6 +66,17 @@ def dist_env():
     return rank, world, local
 
 
+def rank_reduce(v, world, op, device):
+    """A per-rank scalar reduced over the ranks (MAX for times, SUM for counts)."""
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -294,10 +305,9 @@ def our_arm(args):
     barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / max(1, args.steps)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rank_reduce(ms, world, dist.ReduceOp.MAX if world > 1 else None, "cuda")
+    # markers of all ranks' beds (each rank runs its own seeded bed)
+    n_all = rank_reduce(n_mark, world, dist.ReduceOp.SUM if world > 1 else None, "cuda")
     stats = ctx.stats()
     kctx = ctx
     if args.graph:
@@ -314,7 +324,7 @@ def our_arm(args):
         torch.cuda.synchronize()
     k_ms, k_n = kctx.kernel_timing(reset=True)
     k_avg = k_ms / max(1, k_n)
-    value = world * n_mark * W.n_forcing / (ms / 1e3)
+    value = n_all * W.n_forcing / (ms / 1e3)
 
     peaks, peak_kind = measured_peaks()
     touched = stats["touched_cells"]
@@ -365,10 +375,11 @@ def our_arm(args):
             for dst, src in zip(back, us):
                 dst.copy_(src, non_blocking=True)
             torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        e2e_s = rank_reduce((time.perf_counter() - t0) / args.e2e_steps, world,
+                            dist.ReduceOp.MAX if world > 1 else None, "cuda")
         ubytes = sum(t.numel() * 4 for t in u_host)
         pbytes = n_p * 8 * (3 * 3 + 2) + (n_p * 4 if len(dims) > 1 else 0)
-        line["e2e"] = {"value": world * n_mark * W.n_forcing / e2e_s, "unit": UNIT,
+        line["e2e"] = {"value": n_all * W.n_forcing / e2e_s, "unit": UNIT,
                        "h2d_bytes_per_step": ubytes + pbytes, "d2h_bytes_per_step": ubytes + n_p * 8 * 15,
                        "ms_per_step": e2e_s * 1e3}
         # plain FP64 form (the denominator of the speed-up), same workload
@@ -386,11 +397,11 @@ def our_arm(args):
             c64.forcing_step(u64, W.tau)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1) / n64
+        ms64 = rank_reduce(e0.elapsed_time(e1) / n64, world, dist.ReduceOp.MAX if world > 1 else None, "cuda")
         for dst, f in zip(u64, fields64):
             dst.copy_(torch.from_numpy(f))
         slip64 = c64.forcing_step(u64, W.tau, want_slip=True)
-        line["fp64_plain"] = {"value": world * n_mark * W.n_forcing / (ms64 / 1e3), "unit": UNIT,
+        line["fp64_plain"] = {"value": n_all * W.n_forcing / (ms64 / 1e3), "unit": UNIT,
                               "ms_per_step": ms64, "slip": {"rms": slip64[0], "max": slip64[1]}}
         line["speedup_vs_fp64_plain"] = ms64 / ms
         del u64, c64
