@@ -87,3 +87,26 @@ def test_autotuned_variant_matches_fixed_variant():
             scale = a.abs().max().item()
             assert (a - b).abs().max().item() <= 2e-5 * scale
     assert tuned.stats()["threads_per_block"] in (512, 1024)
+
+
+def test_graph_follows_new_particle_sets():
+    # a new particle set (other count, other buffers) must not replay the old
+    # graph: the step runs eagerly, is captured again, and matches the eager context
+    a = [synth.workload("small").scenes[0]]
+    b = [synth.workload("single64").scenes[0]]
+    dims = [a[0].dims]
+    cfg = dict(dims=dims, n_forcing=3, precision=ibm.IBM_FP32, spread_mode=ibm.IBM_SPREAD_DETERMINISTIC,
+               max_particles=max(a[0].n_p, b[0].n_p) + 4)
+    eager, graph = ibm.Context(ibm.Config(**cfg)), ibm.Context(ibm.Config(**cfg, use_graph=True))
+    ua, ub = _fields(a), _fields(a)
+    for scenes in (a, b, a):
+        sc = scenes[0]
+        x = sc.x_p % np.array(dims[0])            # positions inside the first scene's box
+        for ctx in (eager, graph):
+            ctx.set_particles(x, sc.u_p, sc.omega_p, sc.d_p)
+        for _ in range(4):
+            eager.forcing_step(ua, 0.01)
+            graph.forcing_step(ub, 0.01)
+            torch.cuda.synchronize()
+            assert torch.equal(ua[0], ub[0])
+            assert np.array_equal(eager.particle_loads()["F"], graph.particle_loads()["F"])
