@@ -5,8 +5,9 @@
  * Yao et al., "Particle-resolved simulations of four-way coupled polydispersed,
  * particle-laden flows" (arXiv 2109.03972), Sec. 2.2.2 "Outer forcing", on a
  * periodic collocated grid (Sec. 2.2, Fig. 1b) with the three-point
- * regularised delta kernel (Eq. 3pt-delta / 3pt-stencil), for spheres whose
- * surface is represented by Lagrangian markers (Sec. 2.1).  For every outer
+ * regularised delta kernel (Eq. 3pt-delta / 3pt-stencil; the four-point kernel
+ * of Sec. 2.2.3 on the plain path), for spheres whose surface is represented
+ * by Lagrangian markers (Sec. 2.1).  For every outer
  * forcing iteration m = 1..n_F it
  *   1. interpolates the cell-centred velocity to every marker,
  *   2. forms the marker force F = (U^d - U)/tau, U^d = u_p + w_p x r_l,
@@ -59,9 +60,13 @@ enum { IBM_FP64 = 0, IBM_FP32 = 1 };
  *                            a cell are grouped; each group's touched cells
  *                            stay in shared memory for all n_F iterations
  *                            (spreading by shared-memory atomics; the FP32
- *                            summation order is unspecified).
+ *                            summation order is unspecified).  Groups too
+ *                            large for one SM's shared memory run the plain
+ *                            path with global atomics.
  *  IBM_SPREAD_DETERMINISTIC  As CLUSTER, but spreading accumulates in integer
- *                            fixed point, so results are bit-reproducible.
+ *                            fixed point (per group and iteration a power-of-
+ *                            two scale), in shared memory and on the plain
+ *                            path alike, so results are bit-reproducible.
  *  IBM_SPREAD_PLAIN          One thread per marker, global atomics into u, two
  *                            kernels per iteration.  The only mode for FP64
  *                            ("plain FP64 form"). */
@@ -172,7 +177,8 @@ ibm_status ibm_backward(ibm_ctx *ctx, void *const *grad_u_out, void *const *grad
                         double *gU, double *gOmega, double *gX);
 
 /* Diagnostics.  Stencil base cell of every marker, in particle-then-l order,
- * as the active precision path computes it: floor(X_l/h) per axis, NOT wrapped
+ * as the active precision path computes it: floor(X_l/h) per axis
+ * (floor(X_l/h - 1/2) for kernel_width 4), NOT wrapped
  * (int64 [n_markers][3], HOST).  *n_markers receives the count; pass base_out
  * = NULL to query it.  Synchronises.  Errors: STATE, INVALID_ARG, CUDA. */
 ibm_status ibm_marker_bases(ibm_ctx *ctx, int64_t *base_out, int64_t *n_markers);
