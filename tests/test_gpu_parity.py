@@ -428,3 +428,16 @@ def test_four_point_kernel_matches_oracle(oracle_mod, name, precision):
     assert load_err(got["F"], ref["F"], ref["Fabs"]) <= tl
     assert load_err(got["T"], ref["T"], 0.5 * sc.d_p * ref["Fabs"]) <= tl
     assert got["slip"][0] == pytest.approx(ref["slip"][0], rel=1e-10 if precision == ibm.IBM_FP64 else SLIP_TOL32)
+
+
+@pytest.mark.parametrize("name", ["small", "chain"])
+def test_two_ctas_per_sm_variant_matches_oracle(oracle_mod, name):
+    # the 512-thread variant (two CTAs per SM, half the shared memory each)
+    sc = SCENES[name]()
+    u0 = f32_round(sc.field())
+    ref = _oracle_run(oracle_mod, sc, u0)
+    got = run_gpu(sc, u0, ibm.IBM_FP32, ibm.IBM_SPREAD_DETERMINISTIC, tpb=512)
+    assert got["ctx"].stats()["threads_per_block"] == 512
+    assert rel_err_u(got["u"], ref["u"], u0) <= U_TOL32
+    assert load_err(got["F"], ref["F"], ref["Fabs"]) <= LOAD_TOL32
+    assert load_err(got["T"], ref["T"], 0.5 * sc.d_p * ref["Fabs"]) <= LOAD_TOL32
