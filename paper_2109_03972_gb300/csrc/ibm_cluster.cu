@@ -677,7 +677,11 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
                                            const unsigned short *s_inv, float *s_u, int q0) {
     const int tid = threadIdx.x, C = bt.C;
     for (int j = 0; j < bt.nb; ++j) {
-        const int x0 = s_cs[j].x0, y0 = s_cs[j].y0, z0 = s_cs[j].z0;
+        const int sc0 = s_cs[j].scene;
+        // box origin taken into the period once; a cell's coordinate is then the
+        // origin plus at most the box extent (<= period + 2), i.e. below 3 periods
+        const int x0 = wrapi(s_cs[j].x0, prm.dims[3 * sc0]), y0 = wrapi(s_cs[j].y0, prm.dims[3 * sc0 + 1]),
+                  z0 = wrapi(s_cs[j].z0, prm.dims[3 * sc0 + 2]);
         const int W = s_cs[j].W, By = s_cs[j].By, row0 = s_cs[j].row0;
         const int sc = s_cs[j].scene;
         // ghost columns of a box periodic in x are copies: gathered, not written back
@@ -696,7 +700,7 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
             const int row = bt.rowid ? (int)bt.rowid[rc] : rc;
             const int rz = (int)(((float)row + 0.5f) * rBy);
             const int ry = row - rz * By;
-            return ((long long)wrapi(z0 + rz, nz) * ny + wrapi(y0 + ry, ny)) * nx;
+            return ((long long)wrap_lt3(z0 + rz, nz) * ny + wrap_lt3(y0 + ry, ny)) * nx;
         };
         auto move = [&](long long g, int sl) {
 #pragma unroll
@@ -719,7 +723,7 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
                 const long long rb = row_base((int)i - row0, wx);
                 const int xb = 32 * wx + (int)__fns(rw.x, 0u, base + sl - (int)rw.y + 1);
                 if (skip_ghosts && (xb == 0 || xb == Bx - 1)) continue;
-                move(rb + wrapi(x0 + xb, nx), sl);
+                move(rb + wrap_lt3(x0 + xb, nx), sl);
             }
         } else {
             for (int li = tid; li < s_cs[j].R; li += TPB) {
@@ -731,7 +735,7 @@ __device__ __forceinline__ void move_cells(const KParams &prm, const Batch &bt, 
                 while (mask) {
                     const int xb = 32 * wx + __ffs(mask) - 1;
                     mask &= mask - 1u;
-                    if (!(skip_ghosts && (xb == 0 || xb == Bx - 1))) move(rb + wrapi(x0 + xb, nx), sl);
+                    if (!(skip_ghosts && (xb == 0 || xb == Bx - 1))) move(rb + wrap_lt3(x0 + xb, nx), sl);
                     ++sl;
                 }
             }

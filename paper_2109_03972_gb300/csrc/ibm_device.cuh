@@ -73,6 +73,13 @@ __device__ __forceinline__ int wrapi(int i, int n) {
     return m < 0 ? m + n : m;
 }
 
+// i modulo n for 0 <= i < 3n, without a division.
+__device__ __forceinline__ int wrap_lt3(int i, int n) {
+    if (i >= n) i -= n;
+    if (i >= n) i -= n;
+    return i;
+}
+
 // Marker position in grid units, FP64, rounded exactly as
 // xi = x_p/h + ((d_p/2)/h) * t  (multiply, then add; no fused multiply-add).
 __device__ __forceinline__ double marker_xi64(const PInfo &P, const double *t, int c) {
