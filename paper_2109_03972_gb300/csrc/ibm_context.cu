@@ -95,8 +95,8 @@ static void free_all(ibm_ctx *ctx) {
     void *ptrs[] = {ctx->dims_d, ctx->x, ctx->up, ctx->om, ctx->d, ctx->rho, ctx->scene,
                     ctx->nl, ctx->moff, ctx->toff, ctx->pinfo, ctx->tmpl64, ctx->tmpl32,
                     ctx->tmpl_of_nl, ctx->FD, ctx->TD, ctx->Fout, ctx->Tout, ctx->x_new,
-                    ctx->u_new, ctx->om_new, ctx->slip_acc, ctx->ebuf, ctx->e_hist, ctx->cbuf, ctx->fb_cm, ctx->fb_bits, ctx->cell_off_d,
-                    ctx->gu_hist, ctx->gmk, ctx->err_d};
+                    ctx->u_new, ctx->om_new, ctx->slip_acc, ctx->ebuf, ctx->e_hist, ctx->cbuf, ctx->fb_cm, ctx->fb_bits,
+                    ctx->cell_off_d, ctx->fb_own, ctx->gu_hist, ctx->gmk, ctx->err_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (void *p : ctx->u0_saved)
@@ -317,7 +317,8 @@ static void graph_key(const ibm_ctx *ctx, void *const *u_ptrs, double tau, void 
     const void *bufs[] = {ctx->dims_d, ctx->x, ctx->up, ctx->om, ctx->d, ctx->rho, ctx->scene, ctx->nl, ctx->moff,
                           ctx->toff, ctx->pinfo, ctx->tmpl64, ctx->tmpl32, ctx->tmpl_of_nl, ctx->FD, ctx->TD,
                           ctx->Fout, ctx->Tout, ctx->x_new, ctx->u_new, ctx->om_new, ctx->ebuf, ctx->cbuf,
-                          ctx->uptr_d, ctx->fptr_d, ctx->err_d, ctx->fb_cm, ctx->fb_bits, ctx->cell_off_d};
+                          ctx->uptr_d, ctx->fptr_d, ctx->err_d, ctx->fb_cm, ctx->fb_bits, ctx->cell_off_d,
+                          ctx->fb_own};
     for (const void *b : bufs) key.push_back((uintptr_t)b);
     const long long sizes[] = {ctx->n_p, ctx->n_markers, ctx->max_nl, ctx->cap_p, ctx->tmpl_used, ctx->tuned_tpb};
     for (long long v : sizes) key.push_back((uintptr_t)v);

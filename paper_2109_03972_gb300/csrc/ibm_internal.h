@@ -89,6 +89,8 @@ struct ibm_ctx {
     unsigned *fb_cm = nullptr, *fb_bits = nullptr;
     int fb_cm_cap = 0;
     long long *cell_off_d = nullptr;
+    unsigned *fb_own = nullptr;      // deterministic fallback: owned stencil cells per marker
+    long long fb_own_cap = 0;
     double *Fout = nullptr, *Tout = nullptr; // F_p, T_p in physical units
     double *x_new = nullptr, *u_new = nullptr, *om_new = nullptr;
     double *slip_acc = nullptr;              // [2]

@@ -361,16 +361,52 @@ __device__ __forceinline__ float fb_scale(const unsigned *cm, int c, float *inv)
     return ldexpf(1.f, ex);
 }
 
-// Converts the stencil cells of the fallback markers to the cluster's fixed
-// point (TO) or back, each cell once: the first marker to set (clear) the
-// cell's bit in a grid-wide bitmap converts it.
+// Cell (n = 0..26) of a marker's 3-point stencil, as a linear index of its scene.
+__device__ __forceinline__ long long fb_cell(const Stencil<float> &st, const Grid &g, int n) {
+    const int cx = n % 3, cy = (n / 3) % 3, cz = n / 9;
+    return ((long long)wrapi(st.b[2] - 1 + cz, g.nz) * g.ny + wrapi(st.b[1] - 1 + cy, g.ny)) * g.nx +
+           wrapi(st.b[0] - 1 + cx, g.nx);
+}
+
+// Once per step, before the fallback iterations (deterministic mode): every
+// stencil cell of the fallback markers gets one owner, the first marker to set
+// the cell's bit in a grid-wide bitmap; own[moff + l] is the 27-bit mask of
+// the cells marker l of the particle owns.  The first conversion clears the
+// bits again.
+__global__ void __launch_bounds__(kBlock) k_fb_claim(const PInfo *__restrict__ P, const int *__restrict__ plist,
+                                                    const int *__restrict__ n_list_d, const double *__restrict__ t64,
+                                                    const float *__restrict__ t32, const int32_t *__restrict__ dims,
+                                                    const long long *__restrict__ cell_off, unsigned *bits,
+                                                    unsigned *__restrict__ own) {
+    const int n_list = *n_list_d;
+    for (int k = blockIdx.y; k < n_list; k += gridDim.y) {
+        const PInfo Pp = P[plist[k]];
+        const Grid g = scene_grid(dims, Pp.scene);
+        for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Pp.nl; l += gridDim.x * blockDim.x) {
+            Stencil<float> st;
+            marker_stencil(Pp, t64 + 3ll * (Pp.toff + l), t32 + 3ll * (Pp.toff + l), st);
+            unsigned mine = 0u;
+#pragma unroll
+            for (int n = 0; n < 27; ++n) {
+                const long long gi = cell_off[Pp.scene] + fb_cell(st, g, n);
+                const unsigned bit = 1u << (gi & 31);
+                if (!(atomicOr(bits + (gi >> 5), bit) & bit)) mine |= 1u << n;
+            }
+            own[Pp.moff + l] = mine;
+        }
+    }
+}
+
+// Converts the cells owned by the fallback markers (k_fb_claim) to the
+// cluster's fixed point (TO) or back, each cell once.  clear != NULL: also
+// zeroes the cells' bitmap words (no thread of this launch reads them).
 template <bool TO>
 __global__ void __launch_bounds__(kBlock) k_fb_convert(const PInfo *__restrict__ P, const int *__restrict__ plist,
                                                       const int *__restrict__ n_list_d, const double *__restrict__ t64,
                                                       const float *__restrict__ t32, const int32_t *__restrict__ dims,
                                                       const long long *__restrict__ cell_off, float *const *uf,
                                                       const int *__restrict__ pcl, const unsigned *__restrict__ cm,
-                                                      unsigned *bits) {
+                                                      const unsigned *__restrict__ own, unsigned *clear) {
     const int n_list = *n_list_d;
     for (int k = blockIdx.y; k < n_list; k += gridDim.y) {
         const int p = plist[k];
@@ -380,27 +416,15 @@ __global__ void __launch_bounds__(kBlock) k_fb_convert(const PInfo *__restrict__
         float inv;
         const float S = fb_scale(cm, pcl[p], &inv);
         for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Pp.nl; l += gridDim.x * blockDim.x) {
+            unsigned mine = own[Pp.moff + l];
+            if (!mine) continue;
             Stencil<float> st;
             marker_stencil(Pp, t64 + 3ll * (Pp.toff + l), t32 + 3ll * (Pp.toff + l), st);
-            // claim the 27 cells first (independent atomics in flight), then convert
-            // the ones this marker claimed
-            auto cell = [&](int n) {
-                const int cx = n % 3, cy = (n / 3) % 3, cz = n / 9;
-                return ((long long)wrapi(st.b[2] - 1 + cz, g.nz) * g.ny + wrapi(st.b[1] - 1 + cy, g.ny)) * g.nx +
-                       wrapi(st.b[0] - 1 + cx, g.nx);
-            };
-            unsigned mine = 0u;
-#pragma unroll
-            for (int n = 0; n < 27; ++n) {
-                const long long gi = cell_off[Pp.scene] + cell(n);
-                const unsigned bit = 1u << (gi & 31);
-                const unsigned old = TO ? atomicOr(bits + (gi >> 5), bit) : atomicAnd(bits + (gi >> 5), ~bit);
-                if (TO ? !(old & bit) : (old & bit)) mine |= 1u << n;
-            }
             while (mine) {
                 const int n = __ffs(mine) - 1;
                 mine &= mine - 1u;
-                const long long idx = cell(n);
+                const long long idx = fb_cell(st, g, n);
+                if (clear) clear[(cell_off[Pp.scene] + idx) >> 5] = 0u;
                 for (int q = 0; q < 3; ++q) {
                     float *c = u + q * g.ncell + idx;
                     if (TO) *reinterpret_cast<int *>(c) = __float2int_rn(*c * S);
@@ -910,13 +934,49 @@ static dim3 chunk_grid(const ibm_ctx *ctx, int n_list, bool count_on_device = fa
     return dim3((unsigned)gx, (unsigned)gy);
 }
 
+// Buffers of the deterministic fallback: scene cell offsets, the grid-wide
+// cell bitmap (kept zero between steps), per-cluster maxima and per-marker
+// owned-cell masks.
+static ibm_status fb_prepare(ibm_ctx *ctx) {
+    if (!ctx->fb_bits) {
+        long long off = 0;
+        std::vector<long long> offs(ctx->cfg.n_scenes);
+        for (int s = 0; s < ctx->cfg.n_scenes; ++s) {
+            offs[s] = off;
+            off += (long long)ctx->dims_h[3 * s] * ctx->dims_h[3 * s + 1] * ctx->dims_h[3 * s + 2];
+        }
+        const size_t words = (size_t)(off + 31) / 32 + 1;
+        CK(cudaMalloc(&ctx->cell_off_d, offs.size() * sizeof(long long)), "alloc scene offsets");
+        CK(cudaMemcpy(ctx->cell_off_d, offs.data(), offs.size() * sizeof(long long), cudaMemcpyHostToDevice),
+           "copy scene offsets");
+        CK(cudaMalloc(&ctx->fb_bits, words * sizeof(unsigned)), "alloc cell bitmap");
+        CK(cudaMemset(ctx->fb_bits, 0, words * sizeof(unsigned)), "zero cell bitmap");
+    }
+    if (ctx->fb_cm_cap < ctx->cap_p) {
+        if (ctx->fb_cm) cudaFree(ctx->fb_cm);
+        ctx->fb_cm = nullptr;
+        ctx->fb_cm_cap = 0;
+        CK(cudaMalloc(&ctx->fb_cm, 3 * (size_t)ctx->cap_p * sizeof(unsigned)), "alloc cluster maxima");
+        ctx->fb_cm_cap = ctx->cap_p;
+    }
+    if (ctx->fb_own_cap < ctx->n_markers) {
+        if (ctx->fb_own) cudaFree(ctx->fb_own);
+        ctx->fb_own = nullptr;
+        ctx->fb_own_cap = 0;
+        CK(cudaMalloc(&ctx->fb_own, (size_t)ctx->n_markers * sizeof(unsigned)), "alloc owned-cell masks");
+        ctx->fb_own_cap = ctx->n_markers;
+    }
+    return IBM_OK;
+}
+
 // One plain iteration over the particles in plist (all when plist == NULL).
 // pcl (FP32 list only): cluster of each particle; spreading then runs in the
 // deterministic fixed point of the cluster (interpolate with the maxima,
-// convert the stencil cells, integer spreading, convert back).
+// convert the cells claimed by k_fb_claim, integer spreading, convert back);
+// first: the first iteration of the step, whose conversion clears the bitmap.
 template <typename T>
 static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
-                                  bool with_f, const int *pcl = nullptr) {
+                                  bool with_f, const int *pcl = nullptr, bool first = false) {
     const dim3 grid = chunk_grid(ctx, n_list, n_list_d != nullptr);
     const size_t need = (size_t)std::max(1, n_list) * grid.x * 6 * sizeof(double);
     if (ctx->cbuf_cap < need) {
@@ -929,26 +989,6 @@ static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, co
     T *const *uf = reinterpret_cast<T *const *>(ctx->uptr_d);
     T *const *ff = with_f ? reinterpret_cast<T *const *>(ctx->fptr_d) : nullptr;
     if (pcl && sizeof(T) == 4) {
-        if (!ctx->fb_bits) {
-            long long off = 0;
-            std::vector<long long> offs(ctx->cfg.n_scenes);
-            for (int s = 0; s < ctx->cfg.n_scenes; ++s) {
-                offs[s] = off;
-                off += (long long)ctx->dims_h[3 * s] * ctx->dims_h[3 * s + 1] * ctx->dims_h[3 * s + 2];
-            }
-            const size_t words = (size_t)(off + 31) / 32 + 1;
-            CK(cudaMalloc(&ctx->cell_off_d, offs.size() * sizeof(long long)), "alloc scene offsets");
-            CK(cudaMemcpy(ctx->cell_off_d, offs.data(), offs.size() * sizeof(long long), cudaMemcpyHostToDevice),
-               "copy scene offsets");
-            CK(cudaMalloc(&ctx->fb_bits, words * sizeof(unsigned)), "alloc cell bitmap");
-            CK(cudaMemset(ctx->fb_bits, 0, words * sizeof(unsigned)), "zero cell bitmap");
-        }
-        if (ctx->fb_cm_cap < ctx->cap_p) {
-            if (ctx->fb_cm) cudaFree(ctx->fb_cm);
-            ctx->fb_cm = nullptr;
-            CK(cudaMalloc(&ctx->fb_cm, 3 * (size_t)ctx->cap_p * sizeof(unsigned)), "alloc cluster maxima");
-            ctx->fb_cm_cap = ctx->cap_p;
-        }
         float *const *u32 = reinterpret_cast<float *const *>(ctx->uptr_d);
         float *const *f32 = with_f ? reinterpret_cast<float *const *>(ctx->fptr_d) : nullptr;
         CK(cudaMemsetAsync(ctx->fb_cm, 0, 3 * (size_t)ctx->cap_p * sizeof(unsigned), ctx->stream), "zero maxima");
@@ -957,14 +997,14 @@ static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, co
             reinterpret_cast<float *>(ctx->ebuf), ctx->cbuf, pcl, ctx->fb_cm);
         k_fb_convert<true><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list_d, ctx->tmpl64, ctx->tmpl32,
                                                              ctx->dims_d, ctx->cell_off_d, u32, pcl, ctx->fb_cm,
-                                                             ctx->fb_bits);
+                                                             ctx->fb_own, first ? ctx->fb_bits : nullptr);
         k_plain_spread<float, true><<<grid, kBlock, 0, ctx->stream>>>(
             ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->dims_d,
             reinterpret_cast<const float *>(ctx->ebuf), 1.f, u32, f32, (float)(1.0 / tau), ctx->cbuf, ctx->FD,
             ctx->TD, pcl, ctx->fb_cm);
         k_fb_convert<false><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list_d, ctx->tmpl64, ctx->tmpl32,
                                                               ctx->dims_d, ctx->cell_off_d, u32, pcl, ctx->fb_cm,
-                                                              ctx->fb_bits);
+                                                              ctx->fb_own, nullptr);
         ctx->launches += 4;
         return IBM_OK;
     }
@@ -993,8 +1033,16 @@ static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, co
 // deterministic fixed-point spreading per cluster.
 ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
                                 bool with_f, int n_it, const int *pcl) {
+    if (pcl && n_it > 0) {
+        const ibm_status st = fb_prepare(ctx);
+        if (st != IBM_OK) return st;
+        k_fb_claim<<<chunk_grid(ctx, n_list, true), kBlock, 0, ctx->stream>>>(
+            ctx->pinfo, plist, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->dims_d, ctx->cell_off_d, ctx->fb_bits,
+            ctx->fb_own);
+        ctx->launches += 1;
+    }
     for (int it = 0; it < n_it; ++it) {
-        const ibm_status st = plain_iteration<float>(ctx, plist, n_list, n_list_d, tau, with_f, pcl);
+        const ibm_status st = plain_iteration<float>(ctx, plist, n_list, n_list_d, tau, with_f, pcl, it == 0);
         if (st != IBM_OK) return st;
     }
     return ibm_cuda_check(ctx, cudaGetLastError(), "plain iteration");
