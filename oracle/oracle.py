@@ -197,3 +197,10 @@ def backward(u0, x_p, u_p, om_p, d_p, grad_u_out, h=1.0, n_forcing=3, width=3):
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return gi, gU, gW, gX
+
+
+def mean_force(f) -> np.ndarray:
+    """Grid-pass mean IBM force, Sec. 2.2.5 Eq. (fe_IBM): the negated average
+    of f_IBM over all N_i N_j N_k cells, per component.  f: [3][nz][ny][nx]."""
+    f = _f64(f)
+    return -f.reshape(3, -1).sum(axis=1) / float(f[0].size)

@@ -565,3 +565,32 @@ def test_threaded_oracle_is_bitwise_serial(oracle):
         oracle.threads(n0)
     for k in ("u", "F", "T", "f", "slip"):
         assert np.array_equal(a[k], b[k]), k
+
+
+# ----------------------------------------------- mean force (Sec. 2.2.5)
+
+def test_mean_force_closed_forms(oracle):
+    # Eq. (fe_IBM): minus the cell average, per component, over N_i N_j N_k cells.
+    nz, ny, nx = 5, 6, 7
+    c = np.array([1.5, -2.0, 0.25])
+    f = np.broadcast_to(c.reshape(3, 1, 1, 1), (3, nz, ny, nx)).copy()
+    assert np.array_equal(oracle.mean_force(f), -c)
+    g = np.zeros((3, nz, ny, nx))
+    g[1, 4, 2, 6] = 21.0
+    assert np.allclose(oracle.mean_force(g), [0.0, -21.0 / (nx * ny * nz), 0.0], rtol=0, atol=1e-15)
+
+
+def test_mean_force_equals_minus_summed_loads(oracle):
+    # sum_c f_c h^3 = sum_p F_p (spreading carries each marker's F_l dV_l to
+    # the grid, partition of unity), so fbar N h^3 = -sum_p F_p: the grid pass
+    # and the independent per-particle FP64 sums agree.
+    dims = (48, 40, 44)
+    x_p = np.array([[10.2, 11.7, 12.1], [30.8, 25.4, 30.3], [40.1, 8.9, 35.6]])
+    d_p = np.array([12.0, 10.0, 8.0])
+    rng = np.random.default_rng(52)
+    u0 = rng.normal(size=(3, dims[2], dims[1], dims[0]))
+    out = oracle.forcing_step(u0, x_p, rng.normal(0, 0.1, (3, 3)), rng.normal(0, 0.1, (3, 3)), d_p,
+                              want_f=True)
+    n = dims[0] * dims[1] * dims[2]
+    fbar = oracle.mean_force(out["f"])
+    assert np.allclose(fbar * n, -out["F"].sum(0), rtol=1e-11, atol=1e-9)
