@@ -56,6 +56,8 @@ def parse():
                     help="also time forward + adjoint (ibm_backward) steps, FP32 and FP64")
     ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--mean-force", action="store_true",
+                    help="time the grid-pass mean force even with --quick")
     return ap.parse_args()
 
 
@@ -359,6 +361,8 @@ def our_arm(args):
             "gpu_launches": int(stats["launches"]) * args.steps,
             "clocks": clocks}
 
+    if not args.quick or args.mean_force:
+        line["mean_force"] = mean_force_leg(ctx, us, W, dims, stream, peaks)
     if not args.quick:
         # end to end through the C ABI with host buffers: H2D of u and the particle
         # state, the step, D2H of u and the loads, every step
@@ -424,6 +428,41 @@ def our_arm(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def mean_force_leg(ctx, us, W, dims, stream, peaks):
+    """Grid-pass mean IBM force (Eq. fe_IBM) over the f_out of one step: one
+    read of every cell of the force field (12 B per cell, FP32), timed with
+    CUDA events on the library's stream over back-to-back calls."""
+    import torch
+    fs = [torch.zeros_like(u) for u in us]
+    ctx.forcing_step(us, W.tau, f_out=fs)
+    F = ctx.particle_loads()["F"]
+    out = torch.empty((len(dims), 3), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ctx.mean_force(fs, device=True)
+    torch.cuda.synchronize()
+    n = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        out = ctx.mean_force(fs, device=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    fbar = out.cpu().numpy()
+    cells = sum(int(u[0].numel()) for u in us)
+    nbytes = 3 * cells * 4
+    gbs = nbytes / (ms / 1e3) / 1e9
+    # one scene: the grid pass and the summed loads are the same sum (cells vs markers)
+    resid = None
+    if len(dims) == 1:
+        resid = float(np.abs(fbar[0] * cells + F.sum(0)).max() / np.abs(F).sum())
+    del fs
+    return {"kernel": "k_mf_partial + k_mf_final", "ms": ms, "bytes_per_call": nbytes, "bound": "hbm",
+            "achieved_gbs": gbs, "peak": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
+            "fbar_scene0": [float(v) for v in fbar[0]], "loads_identity_residual": resid,
+            "l2": "field %.1f GB, larger than L2" % (nbytes / 1e9)}
 
 
 def backward_leg(args, W, dims, parts, fields64, stream):

@@ -164,6 +164,24 @@ ibm_status ibm_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau,
 ibm_status ibm_particle_loads(ibm_ctx *ctx, double *F, double *T, double *x_p, double *u_p,
                               double *omega_p, int on_device);
 
+/* Mean IBM force of each scene over its grid, Eq. (fe_IBM) of Sec. 2.2.5:
+ *   fbar_s = -(1 / (nx ny nz)) sum over all cells of f,   per component,
+ * the volume-averaged forcing that a triply-periodic fluid solver removes from
+ * its momentum equation.  (The paper's integral form of the same average, the
+ * aperiodic pressure gradient of Sec. 2.2.5, carries the opposite sign; this
+ * call returns the grid-pass form with its minus sign.)
+ * f_ptrs[n_scenes]: HOST array of DEVICE pointers to force fields of the
+ *   precision's type, layout [3][nz][ny][nx] (for example the f_out of
+ *   ibm_forcing_step, whose cell sum equals the summed fluid-side loads F_p / h^3).
+ * fbar_out: double [n_scenes][3], HOST (on_device = 0; the call synchronises
+ *   the context's stream) or DEVICE memory (asynchronous).
+ * One pass over every cell of the fields (12 B per cell in FP32, 24 B in FP64),
+ * sums in FP64 in a fixed order, so the result is bit-reproducible; FP32 fields
+ * are added in groups of at most 16 values in FP32 first.  Independent of the
+ * particles; may be called before ibm_set_particles.
+ * Errors: INVALID_ARG (NULL pointers), CUDA. */
+ibm_status ibm_mean_force(ibm_ctx *ctx, void *const *f_ptrs, double *fbar_out, int on_device);
+
 /* Backward pass of the last forcing step (requires requires_grad = 1 at
  * create).  For a loss L(u^{n_F}) with grad_u_out[s] = dL/du^{n_F} (DEVICE,
  * same layout/type as u), writes grad_u_in[s] = dL/du^0 (DEVICE, may alias

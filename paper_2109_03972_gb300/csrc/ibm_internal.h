@@ -94,6 +94,12 @@ struct ibm_ctx {
     double *Fout = nullptr, *Tout = nullptr; // F_p, T_p in physical units
     double *x_new = nullptr, *u_new = nullptr, *om_new = nullptr;
     double *slip_acc = nullptr;              // [2]
+    // mean force (ibm_meanforce.cu): segment table, cells per scene, partials, result, field pointers
+    long long *mf_seg = nullptr, *mf_cells = nullptr;
+    double *mf_part = nullptr, *mf_out = nullptr;
+    void **mf_ptr = nullptr;
+    long long mf_nseg = 0;
+    std::vector<void *> mf_ptr_h;
 
     // plain-path scratch
     void *ebuf = nullptr;     // [markers][3] real

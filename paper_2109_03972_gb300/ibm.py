@@ -62,6 +62,7 @@ def load_library(path: str = LIB_PATH):
     L.ibm_forcing_step.argtypes = [vp, vp, d, vp, vp]
     L.ibm_particle_loads.argtypes = [vp, vp, vp, vp, vp, vp, i]
     L.ibm_backward.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.ibm_mean_force.argtypes = [vp, vp, vp, i]
     L.ibm_marker_bases.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
     L.ibm_step_stats.argtypes = [vp, vp]
     L.ibm_kernel_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i]
@@ -187,6 +188,14 @@ class Context:
         self._check(self.L.ibm_particle_loads(self.h, *[_ptr(o) for o in out], int(device)))
         keys = ("F", "T", "x_p", "u_p", "omega_p")
         return dict(zip(keys, out))
+
+    def mean_force(self, f_fields, device=False):
+        """Mean IBM force per scene over its grid, Eq. (fe_IBM): [n_scenes][3] FP64."""
+        f_fields = list(f_fields) if isinstance(f_fields, (list, tuple)) else [f_fields]
+        n = len(self._dims)
+        out = torch.empty((n, 3), dtype=torch.float64, device="cuda") if device else np.empty((n, 3))
+        self._check(self.L.ibm_mean_force(self.h, _ptr_array(f_fields), _ptr(out), int(device)))
+        return out
 
     def backward(self, grad_u_out, grad_u_in=None):
         gos = list(grad_u_out) if isinstance(grad_u_out, (list, tuple)) else [grad_u_out]

@@ -15,7 +15,7 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ("ibm_create", "ibm_destroy", "ibm_set_particles", "ibm_forcing_step",
-              "ibm_particle_loads", "ibm_backward"):
+              "ibm_particle_loads", "ibm_backward", "ibm_mean_force"):
         assert n in names
 
 
