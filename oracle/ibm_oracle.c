@@ -445,11 +445,16 @@ long ora_touched_count(int width, long nx, long ny, long nz, double h, long np,
  * Returns 0, or -1 on allocation failure.
  * Parity: pinned by the single-marker closed form, the dense linear-algebra
  * recursion, the no-op cases and the load identities (tests). */
-int ora_forcing_step(int width, int mode, long nx, long ny, long nz, double h,
-                     int n_forcing, double tau, long np,
-                     const double *x_p, const double *u_p, const double *om_p,
-                     const double *d_p, double *u, double *F_out, double *T_out,
-                     double *f_tot, double *slip, double *Fabs_out)
+/* Forcing loop of Sec. 2.2.2 with some markers left out of f_IBM (Sec. 2.2.6):
+ * disabled[m] != 0 (markers in particle-then-l order; NULL = none) gives
+ * marker m the force F_m = 0 in every iteration, so it neither spreads nor adds
+ * to the loads.  The slip is still reported over all markers. */
+int ora_forcing_step_masked(int width, int mode, long nx, long ny, long nz, double h,
+                            int n_forcing, double tau, long np,
+                            const double *x_p, const double *u_p, const double *om_p,
+                            const double *d_p, double *u, double *F_out, double *T_out,
+                            double *f_tot, double *slip, double *Fabs_out,
+                            const unsigned char *disabled)
 {
     const long ncell = nx * ny * nz;
     ora_markers M;
@@ -467,7 +472,7 @@ int ora_forcing_step(int width, int mode, long nx, long ny, long nz, double h,
         ora_interp_all(width, mode, nx, ny, nz, u, &M, U);
         for (long m = 0; m < M.n; ++m)
             for (int q = 0; q < 3; ++q)
-                F[3 * m + q] = (M.Ud[3 * m + q] - U[3 * m + q]) / tau;
+                F[3 * m + q] = (disabled && disabled[m]) ? 0.0 : (M.Ud[3 * m + q] - U[3 * m + q]) / tau;
 #pragma omp parallel for schedule(static)
         for (long c = 0; c < 3 * ncell; ++c) f[c] = 0.0;
         ora_spread_all(width, mode, nx, ny, nz, &M, F, f);
@@ -506,6 +511,86 @@ int ora_forcing_step(int width, int mode, long nx, long ny, long nz, double h,
     free(U); free(F); free(f);
     ora_free_markers(&M);
     return 0;
+}
+
+int ora_forcing_step(int width, int mode, long nx, long ny, long nz, double h,
+                     int n_forcing, double tau, long np,
+                     const double *x_p, const double *u_p, const double *om_p,
+                     const double *d_p, double *u, double *F_out, double *T_out,
+                     double *f_tot, double *slip, double *Fabs_out)
+{
+    return ora_forcing_step_masked(width, mode, nx, ny, nz, h, n_forcing, tau, np, x_p, u_p, om_p, d_p, u,
+                                   F_out, T_out, f_tot, slip, Fabs_out, NULL);
+}
+
+/* SplitMix64 output function (Steele, Lea and Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014): the state advanced once by the
+ * golden-ratio increment, then two xor-shift-multiply rounds and a final
+ * xor-shift.  Used as a counter-based coin for the pair choice below. */
+static uint64_t ora_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Marker exclusion near contact, Sec. 2.2.6 (reading).  For every pair p < q
+ * of the scene whose surface gap zeta = |x_q - x_p| - a_p - a_q (minimum
+ * image) is below 2 eps_sep, one particle of the pair is chosen at random: with
+ * i < j the pair's ids (ids[p], ids[q], or p, q when ids is NULL),
+ * z = splitmix64(seed ^ (i << 32 | j)) and the chosen one is j if the top bit of
+ * z is set, else i.  The chosen particle's markers whose distance to the other
+ * particle's surface, |X_l - x_other| - a_other (minimum image), is below
+ * 2 eps_sep are disabled.  All pairs by brute force, FP64, grid units.
+ * disabled[n_markers] receives 0/1 (particle-then-l order); returns the marker
+ * count, -1 on allocation failure.
+ * Pinned by: no pair within reach leaves every marker on; the disabled set is a
+ * cap facing the partner whose size matches the spherical-cap area; the choice
+ * falls on either particle about equally often. */
+long ora_contact_exclusion(long nx, long ny, long nz, double h, long np, const double *x_p,
+                           const double *d_p, double eps_sep, uint64_t seed, const int64_t *ids,
+                           unsigned char *disabled)
+{
+    ora_markers M;
+    double *zero = (double *)calloc(3 * (size_t)(np ? np : 1), sizeof(double));
+    long *first = (long *)malloc(sizeof(long) * (size_t)(np + 1));
+    if (!zero || !first || ora_build_markers(h, np, x_p, zero, zero, d_p, &M)) return -1;
+    first[0] = 0;
+    for (long p = 0; p < np; ++p) first[p + 1] = first[p] + ora_marker_count(d_p[p], h);
+    for (long m = 0; m < M.n; ++m) disabled[m] = 0;
+    const long n[3] = {nx, ny, nz};
+    const double lim = 2.0 * eps_sep / h;
+    for (long p = 0; p < np; ++p)
+        for (long q = p + 1; q < np; ++q) {
+            const double ap = 0.5 * d_p[p] / h, aq = 0.5 * d_p[q] / h;
+            double d2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                double dv = ora_min_image(x_p[3 * q + c] / h - x_p[3 * p + c] / h, n[c]);
+                d2 += dv * dv;
+            }
+            if (!(sqrt(d2) - ap - aq < lim)) continue;
+            uint64_t i = ids ? (uint64_t)ids[p] : (uint64_t)p, j = ids ? (uint64_t)ids[q] : (uint64_t)q;
+            int swap = i > j;
+            if (swap) { uint64_t t = i; i = j; j = t; }
+            const int pick_j = (int)(ora_splitmix64(seed ^ ((i << 32) | j)) >> 63);
+            /* pick_j chooses the particle with the larger id */
+            const long e = (pick_j != swap) ? q : p, o = (e == q) ? p : q;
+            const double ao = 0.5 * d_p[o] / h;
+            for (long m = first[e]; m < first[e + 1]; ++m) {
+                double r2 = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    double dv = ora_min_image(M.xi[3 * m + c] - x_p[3 * o + c] / h, n[c]);
+                    r2 += dv * dv;
+                }
+                if (sqrt(r2) - ao < lim) disabled[m] = 1;
+            }
+        }
+    long nm = M.n;
+    ora_free_markers(&M);
+    free(zero);
+    free(first);
+    return nm;
 }
 
 /* Number of OpenMP threads of the oracle (1 without OpenMP); n > 0 sets it.

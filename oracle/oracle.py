@@ -62,6 +62,10 @@ def lib():
         L.ora_forcing_step.restype = _i
         L.ora_forcing_step.argtypes = [_i, _i, _l, _l, _l, _d, _i, _d, _l,
                                        _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
+        L.ora_forcing_step_masked.restype = _i
+        L.ora_forcing_step_masked.argtypes = L.ora_forcing_step.argtypes + [_p]
+        L.ora_contact_exclusion.restype = _l
+        L.ora_contact_exclusion.argtypes = [_l, _l, _l, _d, _l, _p, _p, _d, ctypes.c_uint64, _p, _p]
         L.ora_newton_euler.restype = None
         L.ora_newton_euler.argtypes = [_l, _p, _p, _p, _p, _p, _d, _p, _d, _p, _p]
         L.ora_backward.restype = _i
@@ -151,8 +155,9 @@ def touched_count(dims, x_p, d_p, h=1.0, width=3) -> int:
 
 
 def forcing_step(u, x_p, u_p, om_p, d_p, h=1.0, n_forcing=3, tau=0.01, width=3,
-                 brute=False, want_f=False, want_slip=True):
-    """Run the forcing loop on a copy of u.  Returns dict(u, F, T, f, slip)."""
+                 brute=False, want_f=False, want_slip=True, disabled=None):
+    """Run the forcing loop on a copy of u.  Returns dict(u, F, T, f, slip).
+    disabled: optional per-marker 0/1 array (markers left out of f_IBM)."""
     u = _f64(u).copy()
     nz, ny, nx = u.shape[1:]
     x_p, u_p, om_p = (_f64(a, (-1, 3)) for a in (x_p, u_p, om_p))
@@ -163,9 +168,10 @@ def forcing_step(u, x_p, u_p, om_p, d_p, h=1.0, n_forcing=3, tau=0.01, width=3,
     f = np.zeros_like(u) if want_f else None
     slip = np.zeros(2) if want_slip else None
     Fabs = np.zeros(np_)
-    rc = lib().ora_forcing_step(width, int(brute), nx, ny, nz, h, n_forcing, tau, np_,
-                                _ptr(x_p), _ptr(u_p), _ptr(om_p), _ptr(d_p), _ptr(u),
-                                _ptr(F), _ptr(T), _ptr(f), _ptr(slip), _ptr(Fabs))
+    mask = None if disabled is None else np.ascontiguousarray(disabled, dtype=np.uint8)
+    rc = lib().ora_forcing_step_masked(width, int(brute), nx, ny, nz, h, n_forcing, tau, np_,
+                                       _ptr(x_p), _ptr(u_p), _ptr(om_p), _ptr(d_p), _ptr(u),
+                                       _ptr(F), _ptr(T), _ptr(f), _ptr(slip), _ptr(Fabs), _ptr(mask))
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return {"u": u, "F": F, "T": T, "f": f, "slip": slip, "Fabs": Fabs}
@@ -204,3 +210,25 @@ def mean_force(f) -> np.ndarray:
     of f_IBM over all N_i N_j N_k cells, per component.  f: [3][nz][ny][nx]."""
     f = _f64(f)
     return -f.reshape(3, -1).sum(axis=1) / float(f[0].size)
+
+
+def eps_sep(width=3, h=1.0) -> float:
+    """Threshold separation of Sec. 2.2.6: 1.5h for the three-point kernel, 2h for four."""
+    return (2.0 if width == 4 else 1.5) * h
+
+
+def contact_exclusion(dims, x_p, d_p, h=1.0, eps=None, seed=0, ids=None, width=3) -> np.ndarray:
+    """Markers left out of f_IBM near contact (Sec. 2.2.6, reading in
+    ora_contact_exclusion): bool [n_markers], particle-then-l order."""
+    nx, ny, nz = dims
+    x_p = _f64(x_p, (-1, 3))
+    d_p = _f64(d_p, (-1,))
+    n = total_markers(d_p, h)
+    out = np.zeros(n, dtype=np.uint8)
+    idv = None if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
+    e = eps_sep(width, h) if eps is None else float(eps)
+    got = lib().ora_contact_exclusion(nx, ny, nz, h, d_p.size, _ptr(x_p), _ptr(d_p), e, int(seed) & (2**64 - 1),
+                                      _ptr(idv), _ptr(out))
+    if got != n:
+        raise MemoryError("oracle allocation failed")
+    return out.astype(bool)

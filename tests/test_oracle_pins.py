@@ -594,3 +594,100 @@ def test_mean_force_equals_minus_summed_loads(oracle):
     n = dims[0] * dims[1] * dims[2]
     fbar = oracle.mean_force(out["f"])
     assert np.allclose(fbar * n, -out["F"].sum(0), rtol=1e-11, atol=1e-9)
+
+
+# --------------------------------------- marker exclusion near contact (Sec. 2.2.6)
+
+def _pair(rng, d1, d2, zeta, dims=(96, 96, 96)):
+    v = rng.normal(size=3)
+    v /= np.linalg.norm(v)
+    x1 = rng.uniform(0, dims[0], 3)
+    x2 = (x1 + (0.5 * (d1 + d2) + zeta) * v) % np.array(dims, float)   # may cross the periodic seam
+    return np.array([x1, x2]), v
+
+
+def test_exclusion_off_beyond_reach(oracle):
+    # zeta >= 2 eps_sep: no marker of either particle is left out, for both kernels
+    rng = np.random.default_rng(61)
+    for width in (3, 4):
+        lim = 2 * oracle.eps_sep(width)
+        for d1, d2 in ((12.0, 12.0), (8.0, 24.0), (24.0, 16.0)):
+            x, _ = _pair(rng, d1, d2, lim + 0.05)
+            assert not oracle.contact_exclusion((96, 96, 96), x, [d1, d2], seed=3, width=width).any()
+
+
+def test_exclusion_is_a_facing_cap_of_one_particle(oracle):
+    # Inside reach exactly one particle of the pair loses markers; they face the
+    # partner, and their number matches the spherical-cap area of the points of
+    # the chosen sphere (radius a, centre distance D) within a_o + 2 eps_sep of
+    # the partner's centre: N_l (1 - cos t0) / 2 with
+    # cos t0 = (D^2 + a^2 - (a_o + 2 eps)^2) / (2 D a)  (law of cosines; the
+    # golden-spiral markers are close to uniform in area).
+    rng = np.random.default_rng(62)
+    dims = (96, 96, 96)
+    for trial in range(24):
+        d1, d2 = rng.choice([8.0, 12.0, 16.0, 24.0], 2)
+        zeta = rng.uniform(0.05, 2.9)
+        x, v = _pair(rng, d1, d2, zeta, dims)
+        m = oracle.contact_exclusion(dims, x, [d1, d2], seed=trial)
+        n1, n2 = oracle.marker_count(d1), oracle.marker_count(d2)
+        c = (m[:n1].sum(), m[n1:].sum())
+        assert (c[0] == 0) != (c[1] == 0)
+        e = 0 if c[0] else 1
+        a, ao = (0.5 * d1, 0.5 * d2) if e == 0 else (0.5 * d2, 0.5 * d1)
+        n = (n1, n2)[e]
+        D = 0.5 * (d1 + d2) + zeta
+        cos0 = (D * D + a * a - (ao + 3.0) ** 2) / (2 * D * a)
+        want = n * (1 - cos0) / 2
+        assert abs(c[e] - want) <= 1 + math.sqrt(want), (trial, c[e], want)
+        toward = v if e == 0 else -v
+        t = oracle.marker_dirs(n)[(m[:n1] if e == 0 else m[n1:])]
+        assert (t @ toward > 0).all()
+
+
+def test_exclusion_choice_is_fair_and_keyed(oracle):
+    # the chosen particle of a pair is either one about equally often over seeds
+    # (binomial, 5 sigma), and the choice follows the ids, not the array order
+    rng = np.random.default_rng(63)
+    x, _ = _pair(rng, 12.0, 12.0, 1.0)
+    n1 = oracle.marker_count(12.0)
+    first = 0
+    N = 400
+    for seed in range(N):
+        m = oracle.contact_exclusion((96, 96, 96), x, [12.0, 12.0], seed=seed)
+        first += bool(m[:n1].any())
+        swapped = oracle.contact_exclusion((96, 96, 96), x[::-1], [12.0, 12.0], seed=seed, ids=[1, 0])
+        assert np.array_equal(swapped, np.concatenate([m[n1:], m[:n1]]))
+    assert abs(first - N / 2) <= 5 * math.sqrt(N / 4)
+
+
+def test_masked_forcing_dense_recursion(oracle):
+    # With a set E of markers left out, F_l = 0 for l not in E in every
+    # iteration: e_E^{m+1} = (I - W_E W_E^T D_E) e_E^m and
+    # u^n = u^0 + W_E^T D_E sum_m e_E^m (dense numpy on a tiny grid).
+    dims = (10, 9, 11)
+    x_p, d_p, u_p, om, u0 = _small_problem(seed=64, dims=dims, n=3)
+    tau, nf = 0.37, 3
+    W = _dense_W(oracle, dims, x_p, d_p)
+    counts = [oracle.marker_count(d) for d in d_p]
+    Dl = np.concatenate([[oracle.marker_volume(d)] * c for d, c in zip(d_p, counts)])
+    r = np.concatenate([0.5 * d * oracle.marker_dirs(c) for d, c in zip(d_p, counts)])
+    pid = np.repeat(np.arange(len(d_p)), counts)
+    dis = np.random.default_rng(65).random(len(Dl)) < 0.3
+    on = ~dis
+    Ud = u_p[pid] + np.cross(om[pid], r)
+    We, De = W[on], Dl[on]
+    e = Ud[on] - np.stack([We @ u0[c].ravel() for c in range(3)], 1)
+    E = np.zeros_like(e)
+    for _ in range(nf):
+        E += e
+        e = e - (We @ We.T * De[None, :]) @ e
+    du = (We.T @ (De[:, None] * E)).T.reshape(u0.shape)
+    out = oracle.forcing_step(u0, x_p, u_p, om, d_p, n_forcing=nf, tau=tau, disabled=dis)
+    assert np.abs(out["u"] - (u0 + du)).max() < 1e-12
+    Fp = np.zeros((3, 3))
+    np.add.at(Fp, pid[on], De[:, None] * E / tau)
+    assert np.allclose(out["F"], Fp, rtol=1e-11, atol=1e-11)
+    # every marker left out: nothing happens
+    allout = oracle.forcing_step(u0, x_p, u_p, om, d_p, n_forcing=nf, tau=tau, disabled=np.ones(len(Dl), bool))
+    assert np.array_equal(allout["u"], u0) and not allout["F"].any()
