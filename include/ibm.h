@@ -182,6 +182,34 @@ ibm_status ibm_particle_loads(ibm_ctx *ctx, double *F, double *T, double *x_p, d
  * Errors: INVALID_ARG (NULL pointers), CUDA. */
 ibm_status ibm_mean_force(ibm_ctx *ctx, void *const *f_ptrs, double *fbar_out, int on_device);
 
+/* Marker exclusion near contact, Sec. 2.2.6: from the next forcing step on,
+ * markers are left out of f_IBM where two particles come within reach of each
+ * other.  For every pair (p, q) of a scene whose surface gap
+ *   zeta = |x_q - x_p| - d_p/2 - d_q/2   (minimum image)
+ * is below 2 eps_sep, one particle of the pair is chosen at random and its
+ * markers whose distance to the partner's surface, |X_l - x_o| - d_o/2, is
+ * below 2 eps_sep get F_l = 0 in every iteration (they neither spread nor add
+ * to the loads; the slip of ibm_forcing_step still covers every marker).  The
+ * paper names the pair criterion and the random choice of one particle; which
+ * of its markers go is this library's reading: those facing the partner within
+ * the same reach.  The choice: with i < j the pair's particle indices (the
+ * order of ibm_set_particles, across scenes), z = SplitMix64(seed ^ (i << 32 | j))
+ * (Steele, Lea and Flood, 2014) and particle j is chosen when the top bit of
+ * z is set, else particle i.
+ * enable: 1 on, 0 off.  eps_sep: the threshold separation in physical units;
+ *   0 takes the paper's value, 1.5 h for kernel_width 3 and 2 h for 4.
+ * Needs spread_mode PLAIN and requires_grad = 0 (INVALID_ARG otherwise).
+ * Errors: INVALID_ARG.  A step whose pairs in reach exceed 32 per particle
+ * reports CAPACITY at the next error check. */
+ibm_status ibm_set_contact_exclusion(ibm_ctx *ctx, int enable, double eps_sep, uint64_t seed);
+
+/* Markers left out by the last forcing step (ibm_set_contact_exclusion), as a
+ * bitmap over markers in particle-then-l order: bit (m & 31) of word m >> 5,
+ * HOST uint32[(n_markers + 31) / 32] (NULL to query the count only).
+ * *n_disabled receives the number of set bits (0 while exclusion is off).
+ * Synchronises.  Errors: INVALID_ARG, CUDA. */
+ibm_status ibm_disabled_markers(ibm_ctx *ctx, uint32_t *bits_out, int64_t *n_disabled);
+
 /* Backward pass of the last forcing step (requires requires_grad = 1 at
  * create).  For a loss L(u^{n_F}) with grad_u_out[s] = dL/du^{n_F} (DEVICE,
  * same layout/type as u), writes grad_u_in[s] = dL/du^0 (DEVICE, may alias

@@ -105,6 +105,7 @@ static void free_all(ibm_ctx *ctx) {
     for (void *p : ctx->bw_work)
         if (p) cudaFree(p);
     cluster_free(ctx);
+    contact_free(ctx);
     if (ctx->err_h) cudaFreeHost(ctx->err_h);
 }
 
@@ -324,6 +325,7 @@ static void graph_key(const ibm_ctx *ctx, void *const *u_ptrs, double tau, void 
     const long long sizes[] = {ctx->n_p, ctx->n_markers, ctx->max_nl, ctx->cap_p, ctx->tmpl_used, ctx->tuned_tpb};
     for (long long v : sizes) key.push_back((uintptr_t)v);
     if (ctx->cfg.spread_mode != IBM_SPREAD_PLAIN) cluster_graph_key(ctx, key);
+    contact_graph_key(ctx, key);
 }
 
 // Forcing step replayed from a CUDA graph: eager while the key is new, captured

@@ -112,6 +112,12 @@ struct ibm_ctx {
     // cluster-path scratch (see ibm_cluster.cu)
     void *cl = nullptr;
 
+    // marker exclusion near contact (ibm_contact.cu, Sec. 2.2.6)
+    void *ct = nullptr;
+    int ct_enable = 0;
+    double ct_eps = 0.0;
+    uint64_t ct_seed = 0;
+
     // backward
     std::vector<void *> u0_saved;            // per scene copy of u^0
     std::vector<void *> bw_work;             // per scene work field
@@ -151,6 +157,14 @@ ibm_status launch_marker_bases(ibm_ctx *ctx, int64_t *base_d);
 ibm_status launch_scan_int(ibm_ctx *ctx, const int *in, int *out_excl, int n, long long *total_d);
 
 ibm_status ensure_field_ptrs(ibm_ctx *ctx, void *const *u_ptrs, void *const *f_out);
+// marker exclusion near contact (ibm_contact.cu): per-step bitmap of the
+// markers left out of f_IBM, its pointer while enabled (else NULL), graph key
+// entries and teardown
+ibm_status contact_exclusion(ibm_ctx *ctx);
+const unsigned *contact_bits(const ibm_ctx *ctx);
+void contact_graph_key(const ibm_ctx *ctx, std::vector<uintptr_t> &key);
+void contact_free(ibm_ctx *ctx);
+
 ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
                                 bool with_f, int n_it, const int *pcl);
 

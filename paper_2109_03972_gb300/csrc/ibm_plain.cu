@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
     const PInfo *__restrict__ P, const int *__restrict__ plist, int n_list, const int *__restrict__ n_list_d,
     const double *__restrict__ t64, const float *__restrict__ t32, const double *__restrict__ up,
     const double *__restrict__ om, const int32_t *__restrict__ dims, T *const *uf, T *__restrict__ ebuf,
-    double *__restrict__ cbuf, const int *__restrict__ pcl = nullptr, unsigned *cm = nullptr) {
+    double *__restrict__ cbuf, const int *__restrict__ pcl = nullptr, unsigned *cm = nullptr,
+    const unsigned *__restrict__ dis = nullptr) {
     __shared__ double sh[6][32];
     __shared__ float shm[2][32];
     if (n_list_d) n_list = *n_list_d;
@@ -310,9 +311,12 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
                 }
             }
             T e[3];
+            // a marker left out near contact (Sec. 2.2.6) has F = 0
+            const long long mk = (long long)Pp.moff + l;
+            const bool off = dis && ((dis[mk >> 5] >> (mk & 31)) & 1u);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                e[q] = ud[q] - U[q];
+                e[q] = off ? T(0) : ud[q] - U[q];
                 ebuf[3ll * (Pp.moff + l) + q] = e[q];
                 if (FB) emax = fmaxf(emax, fabsf((float)e[q]));
             }
@@ -1008,17 +1012,20 @@ static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, co
         ctx->launches += 4;
         return IBM_OK;
     }
+    // markers left out near contact: only on the whole-particle plain path
+    const unsigned *dis = plist ? nullptr : contact_bits(ctx);
     if (ctx->cfg.kernel_width == 4) {
         k_plain_interp<T, false, 4><<<grid, kBlock, 0, ctx->stream>>>(
             ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, uf,
-            reinterpret_cast<T *>(ctx->ebuf), ctx->cbuf);
+            reinterpret_cast<T *>(ctx->ebuf), ctx->cbuf, nullptr, nullptr, dis);
         k_plain_spread<T, false, 4><<<grid, kBlock, 0, ctx->stream>>>(
             ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->dims_d,
             reinterpret_cast<const T *>(ctx->ebuf), T(1), uf, ff, T(1.0 / tau), ctx->cbuf, ctx->FD, ctx->TD);
     } else {
         k_plain_interp<T><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
                                                             ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, uf,
-                                                            reinterpret_cast<T *>(ctx->ebuf), ctx->cbuf);
+                                                            reinterpret_cast<T *>(ctx->ebuf), ctx->cbuf, nullptr,
+                                                            nullptr, dis);
         k_plain_spread<T><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64,
                                                             ctx->tmpl32, ctx->dims_d,
                                                             reinterpret_cast<const T *>(ctx->ebuf), T(1), uf, ff,
@@ -1051,6 +1058,10 @@ ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, cons
 ibm_status plain_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
     ibm_status s = ensure_field_ptrs(ctx, u_ptrs, f_out);
     if (s != IBM_OK) return s;
+    if (ctx->ct_enable) {
+        s = contact_exclusion(ctx);
+        if (s != IBM_OK) return s;
+    }
     prof_begin(ctx);
     for (int it = 0; it < ctx->cfg.n_forcing; ++it) {
         s = ctx->cfg.precision == IBM_FP64 ? plain_iteration<double>(ctx, nullptr, ctx->n_p, nullptr, tau, f_out != nullptr)

@@ -63,6 +63,8 @@ def load_library(path: str = LIB_PATH):
     L.ibm_particle_loads.argtypes = [vp, vp, vp, vp, vp, vp, i]
     L.ibm_backward.argtypes = [vp, vp, vp, vp, vp, vp]
     L.ibm_mean_force.argtypes = [vp, vp, vp, i]
+    L.ibm_set_contact_exclusion.argtypes = [vp, i, d, ctypes.c_uint64]
+    L.ibm_disabled_markers.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
     L.ibm_marker_bases.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
     L.ibm_step_stats.argtypes = [vp, vp]
     L.ibm_kernel_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i]
@@ -196,6 +198,19 @@ class Context:
         out = torch.empty((n, 3), dtype=torch.float64, device="cuda") if device else np.empty((n, 3))
         self._check(self.L.ibm_mean_force(self.h, _ptr_array(f_fields), _ptr(out), int(device)))
         return out
+
+    def set_contact_exclusion(self, enable=True, eps_sep=0.0, seed=0):
+        """Leave markers out of f_IBM near contact (Sec. 2.2.6); eps_sep = 0: the paper's value."""
+        self._check(self.L.ibm_set_contact_exclusion(self.h, int(enable), float(eps_sep),
+                                                     int(seed) & (2 ** 64 - 1)))
+
+    def disabled_markers(self):
+        """Markers left out by the last step: bool [n_markers], particle-then-l order."""
+        n = ctypes.c_int64()
+        words = np.zeros(max(1, (int(self.stats()["markers"]) + 31) // 32), dtype=np.uint32)
+        self._check(self.L.ibm_disabled_markers(self.h, _ptr(words), ctypes.byref(n)))
+        bits = np.unpackbits(words.view(np.uint8), bitorder="little").astype(bool)
+        return bits[:int(self.stats()["markers"])], int(n.value)
 
     def backward(self, grad_u_out, grad_u_in=None):
         gos = list(grad_u_out) if isinstance(grad_u_out, (list, tuple)) else [grad_u_out]
