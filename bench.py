@@ -364,6 +364,8 @@ def our_arm(args):
     if not args.quick or args.mean_force:
         line["mean_force"] = mean_force_leg(ctx, us, W, dims, stream, peaks)
     if not args.quick:
+        line["contact_exclusion"] = exclusion_leg(cfg, us, u_host, W, (x, up, om, d, rho, so), dims, stream)
+    if not args.quick:
         # end to end through the C ABI with host buffers: H2D of u and the particle
         # state, the step, D2H of u and the loads, every step
         pinned = [t.pin_memory() for t in u_host]
@@ -463,6 +465,38 @@ def mean_force_leg(ctx, us, W, dims, stream, peaks):
             "achieved_gbs": gbs, "peak": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
             "fbar_scene0": [float(v) for v in fbar[0]], "loads_identity_residual": resid,
             "l2": "field %.1f GB, larger than L2" % (nbytes / 1e9)}
+
+
+def exclusion_leg(cfg, us, u_host, W, parts, dims, stream):
+    """Marker exclusion near contact (Sec. 2.2.6) costs: the FP32 plain step of
+    the same workload with and without it (eager, CUDA events, 10 steps each)."""
+    import torch
+    from paper_2109_03972_gb300 import ibm
+    x, up, om, d, rho, so = parts
+    res = {}
+    for on in (False, True):
+        c = ibm.Context(ibm.Config(**{**cfg.__dict__, "spread_mode": ibm.IBM_SPREAD_PLAIN, "use_graph": False,
+                                      "threads_per_block": 0, "profile": False}), stream)
+        if on:
+            c.set_contact_exclusion(True, 0.0, 2109)
+        c.set_particles(x, up, om, d, rho, so if len(dims) > 1 else None)
+        for dst, src in zip(us, u_host):
+            dst.copy_(src)
+        c.forcing_step(us, W.tau)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            c.forcing_step(us, W.tau)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res["with" if on else "without"] = e0.elapsed_time(e1) / 10
+        if on:
+            res["markers_disabled"] = c.disabled_markers()[1]
+        del c
+    return {"path": "plain FP32", "ms_per_step_without": res["without"], "ms_per_step_with": res["with"],
+            "overhead_ms": res["with"] - res["without"], "markers_disabled": res["markers_disabled"],
+            "eps_sep_h": 1.5}
 
 
 def backward_leg(args, W, dims, parts, fields64, stream):
