@@ -593,6 +593,68 @@ long ora_contact_exclusion(long nx, long ny, long nz, double h, long np, const d
     return nm;
 }
 
+/* Fluid inertia inside each particle, Sec. 2.2.9 (midpoint quadrature with a
+ * level-set volume fraction):
+ *   Iu_p = sum_c alpha_c h^3 u_c,   Ir_p = sum_c alpha_c h^3 (r_c x u_c),
+ *   V_p  = sum_c alpha_c h^3,
+ * alpha_c = sum_m -phi_m H(-phi_m) / sum_m |phi_m| over the 8 corners m of cell
+ * c, H(-phi) = 1 for phi <= 0.  Reading: phi_m is the signed distance of the
+ * corner to the sphere's surface, |x_m - x_p| - d_p/2 (the printed "distance to
+ * the centre" is never negative, which would make alpha vanish).  r_c is the
+ * cell centre minus x_p, taken from the unwrapped cell index of the box around
+ * x_p; the field value at the wrapped index.  Every cell of the box
+ * floor(x_p/h - a) - 1 .. floor(x_p/h + a) + 1 per axis (a = d_p/2h) is
+ * visited, by plain loops.  Iu, Ir: [np][3]; V: [np] (any may be NULL).
+ * Pinned by: alpha = 1 / 0 deep inside / outside, V_p against the sphere
+ * volume, a uniform field, and a rigid rotation (int r x (w x r) dV =
+ * (2/5) a^2 V w). */
+void ora_particle_inertia(long nx, long ny, long nz, double h, long np, const double *x_p, const double *d_p,
+                          const double *u, double *Iu, double *Ir, double *V)
+{
+    const long ncell = nx * ny * nz;
+    const long n[3] = {nx, ny, nz};
+    for (long p = 0; p < np; ++p) {
+        const double a = 0.5 * d_p[p] / h;
+        double xi[3], su[3] = {0, 0, 0}, sr[3] = {0, 0, 0}, sv = 0.0;
+        long lo[3], hi[3];
+        for (int c = 0; c < 3; ++c) {
+            xi[c] = x_p[3 * p + c] / h;
+            lo[c] = (long)floor(xi[c] - a) - 1;
+            hi[c] = (long)floor(xi[c] + a) + 1;
+        }
+        for (long k = lo[2]; k <= hi[2]; ++k)
+            for (long j = lo[1]; j <= hi[1]; ++j)
+                for (long i = lo[0]; i <= hi[0]; ++i) {
+                    double num = 0.0, den = 0.0;
+                    for (int m = 0; m < 8; ++m) {
+                        const double cx = (double)(i + (m & 1)) - xi[0];
+                        const double cy = (double)(j + ((m >> 1) & 1)) - xi[1];
+                        const double cz = (double)(k + ((m >> 2) & 1)) - xi[2];
+                        const double phi = sqrt(cx * cx + cy * cy + cz * cz) - a;
+                        if (phi <= 0.0) num += -phi;
+                        den += fabs(phi);
+                    }
+                    const double alpha = den > 0.0 ? num / den : 0.0;
+                    if (alpha == 0.0) continue;
+                    const long idx = (iwrap(k, n[2]) * ny + iwrap(j, n[1])) * nx + iwrap(i, n[0]);
+                    const double uc[3] = {u[idx], u[ncell + idx], u[2 * ncell + idx]};
+                    const double r[3] = {((double)i + 0.5 - xi[0]) * h, ((double)j + 0.5 - xi[1]) * h,
+                                         ((double)k + 0.5 - xi[2]) * h};
+                    const double w = alpha * h * h * h;
+                    for (int c = 0; c < 3; ++c) su[c] += w * uc[c];
+                    sr[0] += w * (r[1] * uc[2] - r[2] * uc[1]);
+                    sr[1] += w * (r[2] * uc[0] - r[0] * uc[2]);
+                    sr[2] += w * (r[0] * uc[1] - r[1] * uc[0]);
+                    sv += w;
+                }
+        for (int c = 0; c < 3; ++c) {
+            if (Iu) Iu[3 * p + c] = su[c];
+            if (Ir) Ir[3 * p + c] = sr[c];
+        }
+        if (V) V[p] = sv;
+    }
+}
+
 /* Number of OpenMP threads of the oracle (1 without OpenMP); n > 0 sets it.
  * The results do not depend on it. */
 int ora_threads(int n)

@@ -66,6 +66,8 @@ def lib():
         L.ora_forcing_step_masked.argtypes = L.ora_forcing_step.argtypes + [_p]
         L.ora_contact_exclusion.restype = _l
         L.ora_contact_exclusion.argtypes = [_l, _l, _l, _d, _l, _p, _p, _d, ctypes.c_uint64, _p, _p]
+        L.ora_particle_inertia.restype = None
+        L.ora_particle_inertia.argtypes = [_l, _l, _l, _d, _l, _p, _p, _p, _p, _p, _p]
         L.ora_newton_euler.restype = None
         L.ora_newton_euler.argtypes = [_l, _p, _p, _p, _p, _p, _d, _p, _d, _p, _p]
         L.ora_backward.restype = _i
@@ -232,3 +234,15 @@ def contact_exclusion(dims, x_p, d_p, h=1.0, eps=None, seed=0, ids=None, width=3
     if got != n:
         raise MemoryError("oracle allocation failed")
     return out.astype(bool)
+
+
+def particle_inertia(u, x_p, d_p, h=1.0):
+    """Fluid inertia inside each particle, Sec. 2.2.9: dict(Iu [n,3], Ir [n,3], V [n])
+    (reading and quadrature in ora_particle_inertia)."""
+    u = _f64(u)
+    nz, ny, nx = u.shape[1:]
+    x_p, d_p = _f64(x_p, (-1, 3)), _f64(d_p, (-1,))
+    n = d_p.size
+    Iu, Ir, V = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
+    lib().ora_particle_inertia(nx, ny, nz, h, n, _ptr(x_p), _ptr(d_p), _ptr(u), _ptr(Iu), _ptr(Ir), _ptr(V))
+    return {"Iu": Iu, "Ir": Ir, "V": V}

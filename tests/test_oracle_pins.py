@@ -691,3 +691,56 @@ def test_masked_forcing_dense_recursion(oracle):
     # every marker left out: nothing happens
     allout = oracle.forcing_step(u0, x_p, u_p, om, d_p, n_forcing=nf, tau=tau, disabled=np.ones(len(Dl), bool))
     assert np.array_equal(allout["u"], u0) and not allout["F"].any()
+
+
+# ------------------------------------ fluid inertia inside a particle (Sec. 2.2.9)
+
+def test_inertia_alpha_single_cells(oracle):
+    # a unit sphere centred on a grid corner: the cell with that corner has
+    # corner distances 0, 1 (x3), sqrt 2 (x3), sqrt 3, so phi = -1, 0, 0, 0,
+    # sqrt2 - 1 (x3), sqrt3 - 1 and alpha = 1 / (1 + 3 (sqrt 2 - 1) + (sqrt 3 - 1))
+    dims = (24, 24, 24)
+    u = np.zeros((3, 24, 24, 24))
+    u[1, 10, 10, 10] = 1.0
+    r = oracle.particle_inertia(u, [[10.0, 10.0, 10.0]], [2.0])
+    alpha = 1.0 / (1.0 + 3.0 * (math.sqrt(2.0) - 1.0) + (math.sqrt(3.0) - 1.0))
+    assert r["Iu"][0] == pytest.approx([0.0, alpha, 0.0], abs=1e-15)
+    # arm r = cell centre - x_p = (1/2, 1/2, 1/2): r x (0, alpha, 0) = alpha (-1/2, 0, 1/2)
+    assert r["Ir"][0] == pytest.approx([-0.5 * alpha, 0.0, 0.5 * alpha], abs=1e-15)
+    # a cell deep inside counts whole, one outside not at all
+    u = np.zeros((3, 24, 24, 24))
+    u[2, 12, 12, 12] = 1.0
+    u[2, 12, 12, 21] = 5.0
+    r = oracle.particle_inertia(u, [[12.3, 12.6, 12.2]], [8.0], h=1.0)
+    assert r["Iu"][0] == pytest.approx([0.0, 0.0, 1.0], abs=1e-15)
+
+
+@pytest.mark.parametrize("d", [8.0, 12.0, 16.0, 24.0])
+def test_inertia_volume_and_uniform_field(oracle, d):
+    # V_p -> pi d^3 / 6 at second order in h/d; a uniform field U gives Iu = V_p U
+    # and, about a centre on a cell centre (mirror-symmetric alpha), Ir = 0
+    n = 48
+    U = np.array([0.7, -1.3, 0.4])
+    u = np.broadcast_to(U.reshape(3, 1, 1, 1), (3, n, n, n)).copy()
+    for x, sym in (([24.5, 24.5, 24.5], True), ([24.3, 23.7, 24.9], False)):
+        r = oracle.particle_inertia(u, [x], [d])
+        V = math.pi * d ** 3 / 6
+        assert abs(r["V"][0] / V - 1) <= 2.0 / d ** 2
+        assert np.allclose(r["Iu"][0], r["V"][0] * U, rtol=1e-13)
+        if sym:
+            assert np.abs(r["Ir"][0]).max() <= 1e-12 * V
+
+
+def test_inertia_rigid_rotation(oracle):
+    # u = w x (x - x_p): int r x (w x r) dV = (2/3) int |r|^2 dV w = (2/5) a^2 V w
+    n = 48
+    x = np.array([24.3, 23.7, 24.9])
+    w = np.array([0.3, -0.2, 0.5])
+    z, y, xx = np.meshgrid(*(np.arange(n) + 0.5,) * 3, indexing="ij")
+    R = np.stack([xx - x[0], y - x[1], z - x[2]])
+    u = np.cross(np.broadcast_to(w.reshape(3, 1, 1, 1), R.shape), R, axis=0)
+    for d in (12.0, 16.0):
+        r = oracle.particle_inertia(u, [x], [d])
+        V = math.pi * d ** 3 / 6
+        assert np.allclose(r["Ir"][0], 0.4 * (d / 2) ** 2 * V * w, rtol=2e-3)
+        assert np.abs(r["Iu"][0]).max() <= 2e-3 * np.linalg.norm(w) * d / 2 * V
