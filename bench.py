@@ -363,6 +363,8 @@ def our_arm(args):
 
     if not args.quick or args.mean_force:
         line["mean_force"] = mean_force_leg(ctx, us, W, dims, stream, peaks)
+    if not args.quick or args.mean_force:
+        line["particle_inertia"] = inertia_leg(ctx, us, u_host, peaks, stream)
     if not args.quick:
         line["contact_exclusion"] = exclusion_leg(cfg, us, u_host, W, (x, up, om, d, rho, so), dims, stream)
     if not args.quick:
@@ -465,6 +467,34 @@ def mean_force_leg(ctx, us, W, dims, stream, peaks):
             "achieved_gbs": gbs, "peak": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
             "fbar_scene0": [float(v) for v in fbar[0]], "loads_identity_residual": resid,
             "l2": "field %.1f GB, larger than L2" % (nbytes / 1e9)}
+
+
+def inertia_leg(ctx, us, u_host, peaks, stream):
+    """Fluid inertia inside every particle (Sec. 2.2.9): one block per particle
+    over its box, timed with CUDA events over back-to-back calls.  Algorithmic
+    bytes: the particles' cell-volume equivalent (sum V_p / h^3 cells) x 12 B of
+    FP32 velocity, plus 152 B of particle record and 56 B of sums each."""
+    import torch
+    for dst, src in zip(us, u_host):
+        dst.copy_(src)
+    for _ in range(3):
+        r = ctx.particle_inertia(us, device=True)
+    torch.cuda.synchronize()
+    n = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        r = ctx.particle_inertia(us, device=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    V = r["V"].cpu().numpy()
+    n_p = V.size
+    nbytes = float(V.sum()) * 12 + n_p * (152 + 56)
+    gbs = nbytes / (ms / 1e3) / 1e9
+    return {"kernel": "k_inertia", "ms": ms, "algorithmic_bytes": nbytes, "bound": "hbm", "achieved_gbs": gbs,
+            "peak": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"], "particles": n_p,
+            "solid_cells": float(V.sum())}
 
 
 def exclusion_leg(cfg, us, u_host, W, parts, dims, stream):

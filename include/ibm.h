@@ -182,6 +182,27 @@ ibm_status ibm_particle_loads(ibm_ctx *ctx, double *F, double *T, double *x_p, d
  * Errors: INVALID_ARG (NULL pointers), CUDA. */
 ibm_status ibm_mean_force(ibm_ctx *ctx, void *const *f_ptrs, double *fbar_out, int on_device);
 
+/* Fluid inertia inside each particle, Sec. 2.2.9 (second-order midpoint
+ * quadrature with a level-set volume fraction), for the current particles:
+ *   Iu_p = sum_c alpha_c h^3 u_c,   Ir_p = sum_c alpha_c h^3 (r_c x u_c),
+ *   V_p  = sum_c alpha_c h^3,
+ *   alpha_c = sum_m -phi_m H(-phi_m) / sum_m |phi_m|  over the 8 corners of
+ *   cell c, H(-phi) = 1 for phi <= 0, phi_m = |x_m - x_p| - d_p/2 (signed
+ *   distance of the corner to the sphere's surface; the paper's wording, the
+ *   distance to the centre, is read as this signed distance, without which
+ *   alpha would vanish); r_c = cell centre - x_p (minimum image).
+ * The rate-of-change terms d/dt int u dV and d/dt int r x u dV of the particle
+ * equations follow from two evaluations (the direct form, without the
+ * rigid-body singularity at rho_p = rho_f).
+ * u_ptrs[n_scenes]: HOST array of DEVICE pointers to the fields (the precision's
+ * type, [3][nz][ny][nx]); read only.  Iu, Ir: double [n_p][3]; V: double [n_p];
+ * any may be NULL; HOST (on_device = 0; synchronises) or DEVICE memory.
+ * FP32 fields are summed per thread in FP32 over at most a few dozen cells and
+ * per particle in FP64; the result is bit-reproducible.  With no particles set
+ * the call does nothing.  Errors: INVALID_ARG (NULL u_ptrs), CUDA. */
+ibm_status ibm_particle_inertia(ibm_ctx *ctx, void *const *u_ptrs, double *Iu, double *Ir, double *V,
+                                int on_device);
+
 /* Marker exclusion near contact, Sec. 2.2.6: from the next forcing step on,
  * markers are left out of f_IBM where two particles come within reach of each
  * other.  For every pair (p, q) of a scene whose surface gap

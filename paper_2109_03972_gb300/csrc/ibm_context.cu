@@ -97,6 +97,7 @@ static void free_all(ibm_ctx *ctx) {
                     ctx->tmpl_of_nl, ctx->FD, ctx->TD, ctx->Fout, ctx->Tout, ctx->x_new,
                     ctx->u_new, ctx->om_new, ctx->slip_acc, ctx->ebuf, ctx->e_hist, ctx->cbuf, ctx->fb_cm, ctx->fb_bits,
                     ctx->cell_off_d, ctx->fb_own, ctx->mf_seg, ctx->mf_cells, ctx->mf_part, ctx->mf_out, ctx->mf_ptr,
+                    ctx->in_ptr, ctx->in_buf,
                     ctx->gu_hist, ctx->gmk, ctx->err_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -100,6 +100,11 @@ struct ibm_ctx {
     void **mf_ptr = nullptr;
     long long mf_nseg = 0;
     std::vector<void *> mf_ptr_h;
+    // fluid inertia inside the particles (ibm_inertia.cu): field pointer table, [cap_p][7] sums
+    void **in_ptr = nullptr;
+    std::vector<void *> in_ptr_h;
+    double *in_buf = nullptr;
+    int in_cap = 0;
 
     // plain-path scratch
     void *ebuf = nullptr;     // [markers][3] real

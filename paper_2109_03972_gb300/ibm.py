@@ -63,6 +63,7 @@ def load_library(path: str = LIB_PATH):
     L.ibm_particle_loads.argtypes = [vp, vp, vp, vp, vp, vp, i]
     L.ibm_backward.argtypes = [vp, vp, vp, vp, vp, vp]
     L.ibm_mean_force.argtypes = [vp, vp, vp, i]
+    L.ibm_particle_inertia.argtypes = [vp, vp, vp, vp, vp, i]
     L.ibm_set_contact_exclusion.argtypes = [vp, i, d, ctypes.c_uint64]
     L.ibm_disabled_markers.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
     L.ibm_marker_bases.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
@@ -198,6 +199,18 @@ class Context:
         out = torch.empty((n, 3), dtype=torch.float64, device="cuda") if device else np.empty((n, 3))
         self._check(self.L.ibm_mean_force(self.h, _ptr_array(f_fields), _ptr(out), int(device)))
         return out
+
+    def particle_inertia(self, u_fields, device=False):
+        """Fluid inertia inside each particle (Sec. 2.2.9): dict(Iu [n,3], Ir [n,3], V [n]), FP64."""
+        u_fields = list(u_fields) if isinstance(u_fields, (list, tuple)) else [u_fields]
+        n = self.n_p
+        if device:
+            out = [torch.empty(s, dtype=torch.float64, device="cuda") for s in ((n, 3), (n, 3), (n,))]
+        else:
+            out = [np.empty(s) for s in ((n, 3), (n, 3), (n,))]
+        self._check(self.L.ibm_particle_inertia(self.h, _ptr_array(u_fields), *[_ptr(o) for o in out],
+                                                int(device)))
+        return dict(zip(("Iu", "Ir", "V"), out))
 
     def set_contact_exclusion(self, enable=True, eps_sep=0.0, seed=0):
         """Leave markers out of f_IBM near contact (Sec. 2.2.6); eps_sep = 0: the paper's value."""

@@ -16,7 +16,7 @@ def test_header_declares_the_boundary():
     names = _declared()
     for n in ("ibm_create", "ibm_destroy", "ibm_set_particles", "ibm_forcing_step",
               "ibm_particle_loads", "ibm_backward", "ibm_mean_force", "ibm_set_contact_exclusion",
-              "ibm_disabled_markers"):
+              "ibm_disabled_markers", "ibm_particle_inertia"):
         assert n in names
 
 
