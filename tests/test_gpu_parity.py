@@ -1,10 +1,15 @@
 """GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on
 the same seeded inputs.
 
-Tolerances (stated here, derived in the design doc):
-  FP64 path : |u - u_oracle|_inf <= 1e-12 |u0|_inf; loads <= 1e-12 sum|F|dV.
+Tolerances:
+  FP64 path : |u - u_oracle|_inf <= 1e-12 |u0|_inf; loads <= 1e-12 sum|F|dV
+              (the two differ only in the order of the additions).
   FP32 paths: |u - u_oracle|_inf <= 2e-5 |u0|_inf; force <= 1e-4 sum|F|dV,
               torque <= 1e-4 (d/2) sum|F|dV; slip RMS <= 1e-3 relative.
+              Each cell is u0 plus n_F spreads of about 30 FP32 products and
+              each interpolated velocity a 27-term FP32 sum, so the rounding
+              stays near 3 * 27 * 2^-24 ~ 5e-6 of the field scale; the loads
+              add FP32 products in 32-marker chunks before the FP64 sums.
   Stencil base cells: bit-exact.
 """
 import math
