@@ -61,3 +61,16 @@ def test_create_rejects_bad_config_without_touching_gpu():
     c.n_scenes, c.dims, c.h, c.kernel_width, c.n_forcing = 1, small, 1.0, 3, 3
     c.precision, c.spread_mode, c.max_particles = ibm.IBM_FP32, ibm.IBM_SPREAD_PLAIN, 4
     assert L.ibm_create(ctypes.byref(c), None, ctypes.byref(ctypes.c_void_p())) == 1
+
+
+def test_new_entry_points_reject_null_without_touching_gpu():
+    # NULL context or NULL required pointers return IBM_ERR_INVALID_ARG (1)
+    # before any CUDA call.
+    from paper_2109_03972_gb300 import build, ibm
+    L = ibm.load_library(build.build())
+    n = ctypes.c_int64()
+    fbar = (ctypes.c_double * 3)()
+    assert L.ibm_mean_force(None, None, fbar, 0) == 1
+    assert L.ibm_set_contact_exclusion(None, 1, 0.0, 0) == 1
+    assert L.ibm_disabled_markers(None, None, ctypes.byref(n)) == 1
+    assert L.ibm_particle_inertia(None, None, None, None, None, 0) == 1
