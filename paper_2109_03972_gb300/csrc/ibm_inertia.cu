@@ -130,10 +130,13 @@ extern "C" ibm_status ibm_particle_inertia(ibm_ctx *ctx, void *const *u_ptrs, do
         CK(cudaMalloc(&ctx->in_buf, 7ll * ctx->cap_p * sizeof(double)), "alloc inertia sums");
         ctx->in_cap = ctx->cap_p;
     }
-    // the pointer table goes through a host vector that stays alive (staged copy)
-    ctx->in_ptr_h.assign(u_ptrs, u_ptrs + ns);
-    CK(cudaMemcpyAsync(ctx->in_ptr, ctx->in_ptr_h.data(), ns * sizeof(void *), cudaMemcpyHostToDevice, ctx->stream),
-       "copy field pointers");
+    // the device pointer table is refreshed only when the pointers change (a copy
+    // from pageable memory would wait for the stream); the host vector stays alive
+    if (ctx->in_ptr_h.size() != (size_t)ns || !std::equal(ctx->in_ptr_h.begin(), ctx->in_ptr_h.end(), u_ptrs)) {
+        ctx->in_ptr_h.assign(u_ptrs, u_ptrs + ns);
+        CK(cudaMemcpyAsync(ctx->in_ptr, ctx->in_ptr_h.data(), ns * sizeof(void *), cudaMemcpyHostToDevice,
+                           ctx->stream), "copy field pointers");
+    }
     const int grid = std::min(ctx->n_p, 152 * 16);
     if (ctx->cfg.precision == IBM_FP64)
         k_inertia<double><<<grid, kInBlock, 0, ctx->stream>>>(

@@ -134,10 +134,13 @@ extern "C" ibm_status ibm_mean_force(ibm_ctx *ctx, void *const *f_ptrs, double *
         if (!f_ptrs[s]) return IBM_ERR_INVALID_ARG;
     ibm_status st = mf_prepare(ctx);
     if (st != IBM_OK) return st;
-    // the pointer table goes through a host vector kept alive until the copy is done
-    ctx->mf_ptr_h.assign(f_ptrs, f_ptrs + ns);
-    CK(cudaMemcpyAsync(ctx->mf_ptr, ctx->mf_ptr_h.data(), ns * sizeof(void *), cudaMemcpyHostToDevice, ctx->stream),
-       "copy field pointers");
+    // the device pointer table is refreshed only when the pointers change (a copy
+    // from pageable memory would wait for the stream); the host vector stays alive
+    if (ctx->mf_ptr_h.size() != (size_t)ns || !std::equal(ctx->mf_ptr_h.begin(), ctx->mf_ptr_h.end(), f_ptrs)) {
+        ctx->mf_ptr_h.assign(f_ptrs, f_ptrs + ns);
+        CK(cudaMemcpyAsync(ctx->mf_ptr, ctx->mf_ptr_h.data(), ns * sizeof(void *), cudaMemcpyHostToDevice,
+                           ctx->stream), "copy field pointers");
+    }
     const int grid = (int)std::min<long long>(std::max(1ll, ctx->mf_nseg), 152ll * 8);
     if (ctx->cfg.precision == IBM_FP64)
         k_mf_partial<double><<<grid, kMfBlock, 0, ctx->stream>>>(reinterpret_cast<const double *const *>(ctx->mf_ptr),
