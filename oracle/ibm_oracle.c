@@ -535,6 +535,10 @@ static uint64_t ora_splitmix64(uint64_t x)
     return z ^ (z >> 31);
 }
 
+/* The SplitMix64 output for state x (exported for its pin against the
+ * generator's published outputs). */
+uint64_t ora_splitmix64_out(uint64_t x) { return ora_splitmix64(x); }
+
 /* Marker exclusion near contact, Sec. 2.2.6 (reading).  For every pair p < q
  * of the scene whose surface gap zeta = |x_q - x_p| - a_p - a_q (minimum
  * image) is below 2 eps_sep, one particle of the pair is chosen at random: with

@@ -64,6 +64,7 @@ def lib():
                                        _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
         L.ora_forcing_step_masked.restype = _i
         L.ora_forcing_step_masked.argtypes = L.ora_forcing_step.argtypes + [_p]
+        L.ora_splitmix64_out.restype, L.ora_splitmix64_out.argtypes = ctypes.c_uint64, [ctypes.c_uint64]
         L.ora_contact_exclusion.restype = _l
         L.ora_contact_exclusion.argtypes = [_l, _l, _l, _d, _l, _p, _p, _d, ctypes.c_uint64, _p, _p]
         L.ora_particle_inertia.restype = None
@@ -246,3 +247,8 @@ def particle_inertia(u, x_p, d_p, h=1.0):
     Iu, Ir, V = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
     lib().ora_particle_inertia(nx, ny, nz, h, n, _ptr(x_p), _ptr(d_p), _ptr(u), _ptr(Iu), _ptr(Ir), _ptr(V))
     return {"Iu": Iu, "Ir": Ir, "V": V}
+
+
+def splitmix64(x: int) -> int:
+    """SplitMix64 output for state x (the counter-based coin of the pair choice)."""
+    return int(lib().ora_splitmix64_out(int(x) & (2**64 - 1)))

@@ -744,3 +744,33 @@ def test_inertia_rigid_rotation(oracle):
         V = math.pi * d ** 3 / 6
         assert np.allclose(r["Ir"][0], 0.4 * (d / 2) ** 2 * V * w, rtol=2e-3)
         assert np.abs(r["Iu"][0]).max() <= 2e-3 * np.linalg.norm(w) * d / 2 * V
+
+
+def test_splitmix64_published_outputs(oracle):
+    # the oracle's coin generator against the generator's published first outputs
+    g = 0x9E3779B97F4A7C15
+    rows = []
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                n, v = line.split()
+                rows.append((int(n), int(v, 16)))
+    assert len(rows) == 3
+    for n, v in rows:
+        # state (n - 1) * g, advanced once inside the output function
+        assert oracle.splitmix64(((n - 1) * g) % 2**64) == v
+
+
+def test_exclusion_choice_follows_the_coin(oracle):
+    # with ids i < j the chosen particle is j exactly when the top bit of
+    # splitmix64(seed ^ (i << 32 | j)) is set
+    rng = np.random.default_rng(66)
+    x, _ = _pair(rng, 12.0, 16.0, 1.0)
+    n1 = oracle.marker_count(12.0)
+    for seed in range(40):
+        for ids in ((0, 1), (7, 3), (123456, 99)):
+            i, j = min(ids), max(ids)
+            pick_j = oracle.splitmix64(seed ^ ((i << 32) | j)) >> 63
+            m = oracle.contact_exclusion((96, 96, 96), x, [12.0, 16.0], seed=seed, ids=list(ids))
+            first_chosen = bool(m[:n1].any())
+            assert first_chosen == (ids[0] == (j if pick_j else i))
