@@ -74,3 +74,17 @@ def test_new_entry_points_reject_null_without_touching_gpu():
     assert L.ibm_set_contact_exclusion(None, 1, 0.0, 0) == 1
     assert L.ibm_disabled_markers(None, None, ctypes.byref(n)) == 1
     assert L.ibm_particle_inertia(None, None, None, None, None, 0) == 1
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    # no CPU fallback: a missing libibm.so is an ImportError, in a fresh process
+    import subprocess
+    import sys
+    code = ("import paper_2109_03972_gb300.ibm as m\n"
+            "m._lib = None\n"
+            "try:\n"
+            "    m.load_library(%r)\n"
+            "except ImportError:\n"
+            "    print('raised')\n") % str(tmp_path / "libibm.so")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=300)
+    assert r.returncode == 0 and "raised" in r.stdout, r.stderr[-1000:]
