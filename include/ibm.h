@@ -269,12 +269,13 @@ ibm_status ibm_kernel_timing(ibm_ctx *ctx, double *total_ms, int64_t *count, int
 
 /* One FP64 forcing step that allocates nothing (no context, no cudaMalloc or
  * cudaFree, no host allocation).  For callers that cannot allocate device
- * memory: work being captured into or replayed from a CUDA graph, hosts that
- * give the library a fixed memory budget up front, applications whose own
- * allocator owns the device.  The paper has no counterpart; it is the plain
- * FP64 form of ibm_forcing_step (one thread per marker, global atomics) for a
- * single periodic nx*ny*nz grid, with the same results up to the order of
- * floating-point additions.
+ * memory: hosts that hand the library a fixed memory budget at start-up and
+ * forbid allocations afterwards, plugins inside an application whose own
+ * allocator owns the device memory, and time-critical loops that cannot afford
+ * the device-wide synchronisation of cudaFree.  The paper has no counterpart;
+ * it is the plain FP64 form of ibm_forcing_step (one thread per marker, global
+ * atomics) for a single periodic nx*ny*nz grid, with the same results up to
+ * the order of floating-point additions.
  * Inputs (DEVICE, double): x_p, u_p, omega_p [n_p][3], d_p [n_p].
  * In/out (DEVICE, double): u [3][nz][ny][nx], updated in place.
  * Outputs (DEVICE, double): F_out, T_out [n_p][3], the fluid-side loads summed
@@ -285,9 +286,15 @@ ibm_status ibm_kernel_timing(ibm_ctx *ctx, double *total_ms, int64_t *count, int
  * IBM_ERR_CAPACITY and leave u unchanged.  Every call reuses the same array,
  * so calls whose work overlaps on the GPU (other streams, other host threads
  * on the same device) race and corrupt each other.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that first
- * call outside any stream capture.  The call synchronises cuda_stream to read
- * its error word.
+ * does the set-up: it looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture begins.  The address stays valid until the device is
+ * reset: after cudaDeviceReset the entry point must not be called on that
+ * device again in the same process.  The call synchronises cuda_stream to read
+ * its error word.  On an error the particle data was rejected on the device
+ * (INVALID_ARG from the particle checks, CAPACITY from the marker total),
+ * F_out and T_out hold zeros and u is unchanged; on an error found on the host
+ * (bad sizes or pointers) nothing is written.
  * Errors: INVALID_ARG (bad sizes, NULL pointers, non-finite or oversized
  * particles: d_p/h + 4 > smallest grid edge), CAPACITY, CUDA. */
 ibm_status ibm_forcing_step_static(int nx, int ny, int nz, double h, int n_forcing, double tau, int n_p,

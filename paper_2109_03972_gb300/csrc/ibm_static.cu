@@ -1,14 +1,15 @@
 // ibm_forcing_step_static: the plain FP64 forcing step for callers that cannot
 // allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA graph
-// that is being captured or replayed (allocation is not a capturable stream
-// operation), hosts that hand the library a fixed memory budget up front, or
-// embedding applications whose allocator owns every byte of the device.  This
-// entry point needs no context and allocates nothing, on the device or on the
-// host: its scratch (per-marker slip values, per-particle marker offsets, an
-// error word) lives in one fixed-size array in this file, kStaticBytes long,
-// which every GPU that loads the library holds until the process exits.
+// Some callers cannot call cudaMalloc at all: hosts that hand the library a
+// fixed memory budget at start-up and forbid allocations afterwards, plugins
+// embedded in an application whose own allocator owns every byte of the device
+// (a cudaMalloc beside it fails or fragments its pool), and time-critical loops
+// that cannot afford the device-wide synchronisation of cudaFree.  This entry
+// point needs no context and allocates nothing, on the device or on the host:
+// its scratch (per-marker slip values, per-particle marker offsets, an error
+// word) lives in one fixed-size array in this file, kStaticBytes long, which
+// every GPU that loads the library holds until the process exits.
 //
 // The array is shared by every call: a call overwrites what the previous one
 // left there (it clears what must start at zero), and two calls whose work
@@ -16,6 +17,7 @@
 // same device) race on it and corrupt each other's results.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 
 #include "ibm_device.cuh"
@@ -61,6 +63,12 @@ __global__ void k_static_setup(unsigned char *base, int n_p, const double *x, co
     if (t == 0) bad = 0;
     __syncthreads();
     const int me = min(nx, min(ny, nz));
+    // outputs start at zero for every particle, valid or not, so that a
+    // rejected call leaves no stale rows behind
+    for (int i = t; i < 3 * n_p; i += kStaticBlock) {
+        F[i] = 0.0;
+        T[i] = 0.0;
+    }
     const int chunk = (n_p + kStaticBlock - 1) / kStaticBlock;
     const int lo = min(n_p, t * chunk), hi = min(n_p, lo + chunk);
     long long sum = 0;
@@ -75,10 +83,6 @@ __global__ void k_static_setup(unsigned char *base, int n_p, const double *x, co
         const double q = d[p] / h;
         long long n = llround(IBM_PI * q * q);
         sum += n < 1 ? 1 : n;
-        for (int c = 0; c < 3; ++c) {
-            F[3 * p + c] = 0.0;
-            T[3 * p + c] = 0.0;
-        }
     }
     part[t] = sum;
     __syncthreads();
@@ -239,23 +243,31 @@ __global__ void k_static_scale(unsigned char *base, int n_p, double s, double *F
     }
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress with that device current).
+// Device address of the scratch array on the current device, looked up at
+// set-up: the first call on a device runs cudaGetSymbolAddress with that
+// device current, later calls reuse the address.  The entries are atomic, so
+// host threads calling concurrently on different devices (or racing on the
+// first call of one device, which both resolve to the same address) are safe.
+// cudaDeviceReset unloads the library's module on that device and makes the
+// stored address stale: the entry point must not be used on a device after it
+// has been reset within the same process.
 constexpr int kMaxDevices = 64;
-unsigned char *g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<unsigned char *> g_scratch_ptr[kMaxDevices];
 
 cudaError_t static_scratch_ptr(unsigned char **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
+    unsigned char *p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void *q = nullptr;
+        e = cudaGetSymbolAddress(&q, g_static_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+        p = static_cast<unsigned char *>(q);
+        g_scratch_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

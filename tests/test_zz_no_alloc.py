@@ -1,10 +1,13 @@
 """GPU test of ibm_forcing_step_static, the entry point that allocates nothing.
 
-It is for callers that cannot allocate device memory (graph capture, fixed
-memory budgets, foreign allocators); its scratch is a fixed array inside the
-library.  Checked through the C ABI against the context-based FP64 plain path
-(ibm_forcing_step) on two calls in a row, at the FP64 tolerance of the other
-parity tests, plus the size limit.  Named so that pytest collects it last.
+It serves callers that cannot allocate device memory: a host that hands the
+library a fixed memory budget at start-up, an application whose own allocator
+owns the device, loops that cannot afford cudaFree's device-wide
+synchronisation.  Its scratch is a fixed array inside the library.  Checked
+through the C ABI against the context-based FP64 plain path (ibm_forcing_step)
+on two calls in a row, at the FP64 tolerance of the other parity tests; a call
+after the first must leave the device's free memory unchanged; sizes beyond the
+array are rejected.  Named so that pytest collects it last.
 """
 import ctypes
 
@@ -54,11 +57,17 @@ def test_static_step_matches_context_step_twice():
     F = torch.empty((sc.n_p, 3), **dev)
     T = torch.empty((sc.n_p, 3), **dev)
     scale = np.abs(u0).max()
-    for _ in range(2):
+    for call in range(2):
         ctx.forcing_step([ua], 0.01)
         ref = ctx.particle_loads()
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         assert _static_step(L, sc.dims, x, up, om, d, ub, F, T) == 0
         torch.cuda.synchronize()
+        if call > 0:
+            # after the first call (which looks up the scratch address and loads
+            # the kernels) a call takes no device memory at all
+            assert torch.cuda.mem_get_info()[0] == free0
         assert (ua - ub).abs().max().item() <= 1e-12 * scale
         Fs, Ts = F.cpu().numpy(), T.cpu().numpy()
         fs = np.abs(ref["F"]).max()
@@ -78,11 +87,13 @@ def test_static_step_rejects_sizes_beyond_its_array():
     d = torch.full((n,), 16.0, **dev)
     u = torch.randn((3, 64, 64, 64), **dev)
     u0 = u.clone()
-    F = torch.empty((n, 3), **dev)
-    T = torch.empty((n, 3), **dev)
+    F = torch.full((n, 3), 7.0, **dev)
+    T = torch.full((n, 3), 7.0, **dev)
     assert _static_step(L, dims, x, up, om, d, u, F, T) == IBM_ERR_CAPACITY
     torch.cuda.synchronize()
     assert torch.equal(u, u0)
+    # a rejected call leaves zeros in the loads, not the caller's old values
+    assert torch.count_nonzero(F).item() == 0 and torch.count_nonzero(T).item() == 0
     big = 65537
     xb = torch.zeros((big, 3), **dev)
     db = torch.full((big,), 8.0, **dev)
