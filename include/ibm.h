@@ -259,6 +259,28 @@ ibm_status ibm_marker_bases(ibm_ctx *ctx, int64_t *base_out, int64_t *n_markers)
  * particle pairs tested.  Entries [1]-[5], [7]-[9] are 0 in PLAIN mode. */
 ibm_status ibm_step_stats(ibm_ctx *ctx, int64_t *stats);
 
+/* Code paths of a particle cluster in the last forcing step, as bits of
+ * ibm_particle_clusters' path_of. */
+enum {
+    IBM_PATH_SMEM = 1,            /* shared-memory cluster kernel                 */
+    IBM_PATH_GLOBAL_RECORDS = 2,  /* ... with its marker records in global memory */
+    IBM_PATH_ONE_COMPONENT = 4,   /* ... one velocity component at a time         */
+    IBM_PATH_SPARSE_ROWS = 8,     /* ... with the sparse row table                */
+    IBM_PATH_PERIODIC = 16,       /* the cluster's box wraps around the period    */
+    IBM_PATH_FALLBACK = 32        /* the plain path (global atomics)              */
+};
+
+/* Diagnostics of the cluster modes (CLUSTER, DETERMINISTIC).  Particles whose
+ * marker stencils share a grid cell, directly or through other particles, form
+ * a cluster: the connected components of that relation are independent for
+ * all n_F iterations of Sec. 2.2.2.  For the last forcing step, cluster_of[p]
+ * receives particle p's cluster (0 .. n_clusters-1) and path_of[p] the
+ * IBM_PATH_* bits of the code path its cluster took (HOST int32 [n_p] each,
+ * either may be NULL); *n_clusters (may be NULL) the number of clusters.
+ * Synchronises.  Errors: STATE (PLAIN mode, or no step since the last
+ * ibm_set_particles), CUDA. */
+ibm_status ibm_particle_clusters(ibm_ctx *ctx, int32_t *cluster_of, int32_t *path_of, int64_t *n_clusters);
+
 /* Device time of the main forcing kernel (the shared-memory cluster kernel,
  * or the plain interpolation+spreading kernels in PLAIN mode), measured with
  * CUDA events recorded on the context's stream around each launch since the

@@ -81,6 +81,7 @@ struct ClusterScratch {
     int *cl_plist = nullptr, *cl_bkt = nullptr;
     int *bkt_cnt = nullptr, *bkt_start = nullptr, *order = nullptr, *fb_list = nullptr;
     int *nm_ord = nullptr, *cum = nullptr, *cl_scene = nullptr;
+    int *cl_path = nullptr;          // IBM_PATH_* bits of each cluster (last step)
     int2 *batches = nullptr;
     float4 *grec = nullptr;          // marker records of batches kept in global memory
     size_t grec_bytes = 0;
@@ -388,7 +389,7 @@ __global__ void k_cluster_fill(int n_p, const int *pcl, const int *cl_first, int
 __global__ void k_cluster_route(const long long *n_clust_d, const PInfo *P, const int32_t *dims, const int *cl_np,
                                 const int *cl_nm, const int *cl_first, const int *cl_plist, int *cl_box,
                                 int cap_m, int max_rows, int *cl_bkt, int *bkt_cnt, int *fb_list, int *cl_scene,
-                                int *cnt) {
+                                int *cl_path, int *cnt) {
     const int n = (int)*n_clust_d;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const int np = cl_np[c], nm = cl_nm[c];
@@ -417,6 +418,7 @@ __global__ void k_cluster_route(const long long *n_clust_d, const PInfo *P, cons
         ok = ok && (cl_box[12 * c + 4] - cl_box[12 * c + 1]) < 1023 && (cl_box[12 * c + 5] - cl_box[12 * c + 2]) < 1023 &&
              (cl_box[12 * c + 3] - cl_box[12 * c]) < 511;
         cl_scene[c] = s | (wrap << 28);   // scene, and the wrapped axes in the top bits
+        cl_path[c] = (wrap ? IBM_PATH_PERIODIC : 0) | (ok ? 0 : IBM_PATH_FALLBACK);
         if (ok) {
             const int b = min(kBuckets - 1, nm / 8);
             cl_bkt[c] = kBuckets - 1 - b;   // larger clusters first
@@ -562,6 +564,7 @@ struct KParams {
     float *const *uf;
     float *const *ff;
     const int *order, *cl_first, *cl_np, *cl_nm, *cl_box, *cl_plist, *cl_scene, *poff;
+    int *cl_path;
     const int2 *batches;
     float4 *grec;   // per CTA: 2 * TPB * KM float4 (records a, then b)
     int *cnt, *fb_list, *err;
@@ -1432,6 +1435,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                     atomicAdd(prm.cnt + C_OVERFLOW, bt.nb);
                     for (int i = 0; i < np; ++i) prm.fb_list[k0 + i] = s_ps[i].gid;
                 }
+                if (tid < bt.nb) prm.cl_path[prm.order[be.x + tid]] |= IBM_PATH_FALLBACK;
                 __syncthreads();
                 continue;
             }
@@ -1470,6 +1474,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_cluster_forcing(KParams prm) {
                 ra[m] = a;
             }
             __syncthreads();
+            if (tid < bt.nb)
+                prm.cl_path[prm.order[be.x + tid]] |= IBM_PATH_SMEM | (use_rec ? 0 : IBM_PATH_GLOBAL_RECORDS) |
+                                                      (three ? 0 : IBM_PATH_ONE_COMPONENT) |
+                                                      (bt.rix ? IBM_PATH_SPARSE_ROWS : 0);
             if (tid == 0) {
                 int touched = 0;
                 for (int j = 0; j < bt.nb; ++j) touched += s_cs[j].ncell;
@@ -1529,7 +1537,7 @@ void cluster_free(ibm_ctx *ctx) {
     int *ptrs[] = {S->scene_bin_off, S->scene_nb, S->bin_cnt, S->bin_start, S->bin_cur, S->bin_items,
                    S->parent, S->cand, S->cnt, S->root_flag, S->cid, S->pcl, S->poff, S->cl_np, S->cl_nm,
                    S->cl_first, S->cl_cur, S->cl_box, S->cl_plist, S->cl_bkt, S->bkt_cnt, S->bkt_start,
-                   S->order, S->fb_list, S->nm_ord, S->cum, S->cl_scene};
+                   S->order, S->fb_list, S->nm_ord, S->cum, S->cl_scene, S->cl_path};
     for (int *p : ptrs)
         if (p) cudaFree(p);
     if (S->batches) cudaFree(S->batches);
@@ -1587,7 +1595,7 @@ static ibm_status cluster_alloc(ibm_ctx *ctx) {
         const int cp = std::max(ctx->cap_p, np);
         int **arrs[] = {&S->bin_items, &S->parent, &S->root_flag, &S->cid, &S->pcl, &S->cl_np, &S->cl_nm,
                         &S->cl_first, &S->cl_cur, &S->cl_plist, &S->cl_bkt, &S->order, &S->fb_list,
-                        &S->nm_ord, &S->cum, &S->cl_scene};
+                        &S->nm_ord, &S->cum, &S->cl_scene, &S->cl_path};
         for (int **p : arrs) {
             if (*p) cudaFree(*p);
             CK(cudaMalloc(p, (size_t)(cp + 1) * sizeof(int)), "alloc cluster scratch");
@@ -1687,7 +1695,7 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     k_cluster_fill<<<gb, 256, 0, sm>>>(n, S->pcl, S->cl_first, S->cl_cur, S->cl_plist);
     k_cluster_route<<<gb, 256, 0, sm>>>(S->tot + 1, ctx->pinfo, ctx->dims_d, S->cl_np, S->cl_nm, S->cl_first,
                                         S->cl_plist, S->cl_box, cap_m, max_rows, S->cl_bkt, S->bkt_cnt,
-                                        S->fb_list, S->cl_scene, S->cnt);
+                                        S->fb_list, S->cl_scene, S->cl_path, S->cnt);
     k_scan1<<<1, 1024, 0, sm>>>(S->bkt_cnt, S->bkt_start, kBuckets, S->tot + 3);
     k_order_fill<<<gb, 256, 0, sm>>>(S->tot + 1, S->cl_bkt, S->bkt_start, S->bkt_start + kBuckets + 1, S->order);
     k_gather_nm<<<gb, 256, 0, sm>>>(n, S->cnt, S->order, S->cl_nm, S->nm_ord);
@@ -1709,6 +1717,7 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prm.order = S->order;
     prm.batches = S->batches;
     prm.cl_scene = S->cl_scene;
+    prm.cl_path = S->cl_path;
     prm.max_rows = max_rows;
     prm.cl_first = S->cl_first;
     prm.cl_np = S->cl_np;
@@ -1768,7 +1777,8 @@ void cluster_graph_key(const ibm_ctx *ctx, std::vector<uintptr_t> &key) {
     const void *bufs[] = {S->scene_bin_off, S->scene_nb, S->bin_cnt, S->bin_start, S->bin_cur, S->bin_items,
                           S->parent, S->cand, S->cnt, S->tot, S->root_flag, S->cid, S->pcl, S->poff, S->cl_np,
                           S->cl_nm, S->cl_first, S->cl_cur, S->cl_box, S->cl_plist, S->cl_bkt, S->bkt_cnt,
-                          S->bkt_start, S->order, S->fb_list, S->nm_ord, S->cum, S->cl_scene, S->batches, S->grec};
+                          S->bkt_start, S->order, S->fb_list, S->nm_ord, S->cum, S->cl_scene, S->cl_path,
+                          S->batches, S->grec};
     for (const void *b : bufs) key.push_back((uintptr_t)b);
     const long long sizes[] = {S->cap_p, S->cap_bins, S->cap_cand, S->nbins, S->max_nl, S->n_scenes,
                                S->smem_bytes, S->tpb, S->det, (long long)S->grec_bytes};
@@ -1791,5 +1801,25 @@ ibm_status cluster_stats(ibm_ctx *ctx, int64_t *stats) {
     stats[7] = S->tpb;
     stats[8] = c[C_ONECOMP];
     stats[9] = c[C_NCAND];
+    return IBM_OK;
+}
+
+ibm_status cluster_membership(ibm_ctx *ctx, int32_t *cluster_of, int32_t *path_of, int64_t *n_clusters) {
+    ClusterScratch *S = reinterpret_cast<ClusterScratch *>(ctx->cl);
+    if (!S) return ibm_fail(ctx, IBM_ERR_STATE, "no cluster-path forcing step yet");
+    const int n = ctx->n_p;
+    long long nclust = 0;
+    std::vector<int> pcl(std::max(n, 1)), path;
+    CK(cudaMemcpyAsync(&nclust, S->tot + 1, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream), "read clusters");
+    CK(cudaMemcpyAsync(pcl.data(), S->pcl, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+       "read clusters");
+    CK(cudaStreamSynchronize(ctx->stream), "read clusters");
+    path.resize(std::max(nclust, 1ll));
+    CK(cudaMemcpy(path.data(), S->cl_path, (size_t)nclust * sizeof(int), cudaMemcpyDeviceToHost), "read paths");
+    if (n_clusters) *n_clusters = nclust;
+    for (int p = 0; p < n; ++p) {
+        if (cluster_of) cluster_of[p] = pcl[p];
+        if (path_of) path_of[p] = (pcl[p] >= 0 && pcl[p] < nclust) ? path[pcl[p]] : 0;
+    }
     return IBM_OK;
 }

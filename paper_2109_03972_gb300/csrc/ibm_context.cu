@@ -482,4 +482,14 @@ ibm_status ibm_step_stats(ibm_ctx *ctx, int64_t *stats) {
     return s;
 }
 
+ibm_status ibm_particle_clusters(ibm_ctx *ctx, int32_t *cluster_of, int32_t *path_of, int64_t *n_clusters) {
+    if (!ctx) return IBM_ERR_INVALID_ARG;
+    if (ctx->cfg.spread_mode == IBM_SPREAD_PLAIN)
+        return ibm_fail(ctx, IBM_ERR_STATE, "PLAIN mode forms no clusters");
+    if (!ctx->have_step) return ibm_fail(ctx, IBM_ERR_STATE, "no forcing step since the last set_particles");
+    ibm_status s = ibm_check_err_word(ctx);
+    if (s != IBM_OK) return s;
+    return cluster_membership(ctx, cluster_of, path_of, n_clusters);
+}
+
 }  // extern "C"

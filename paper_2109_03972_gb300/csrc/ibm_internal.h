@@ -181,5 +181,7 @@ void prof_end(ibm_ctx *ctx);
 ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out);
 void cluster_free(ibm_ctx *ctx);
 ibm_status cluster_stats(ibm_ctx *ctx, int64_t *stats);
+// each particle's cluster and its cluster's IBM_PATH_* bits in the last step
+ibm_status cluster_membership(ibm_ctx *ctx, int32_t *cluster_of, int32_t *path_of, int64_t *n_clusters);
 // appends the cluster path's device buffers and sizes to a graph key
 void cluster_graph_key(const ibm_ctx *ctx, std::vector<uintptr_t> &key);

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libibm.so")
 
 IBM_FP64, IBM_FP32 = 0, 1
 IBM_SPREAD_CLUSTER, IBM_SPREAD_DETERMINISTIC, IBM_SPREAD_PLAIN = 0, 1, 2
+IBM_PATH_SMEM, IBM_PATH_GLOBAL_RECORDS, IBM_PATH_ONE_COMPONENT = 1, 2, 4
+IBM_PATH_SPARSE_ROWS, IBM_PATH_PERIODIC, IBM_PATH_FALLBACK = 8, 16, 32
 
 STATUS = {0: "IBM_OK", 1: "IBM_ERR_INVALID_ARG", 2: "IBM_ERR_CUDA", 3: "IBM_ERR_OOM",
           4: "IBM_ERR_CAPACITY", 5: "IBM_ERR_NONFINITE", 6: "IBM_ERR_TIMEOUT", 7: "IBM_ERR_STATE"}
@@ -68,6 +70,8 @@ def load_library(path: str = LIB_PATH):
     L.ibm_disabled_markers.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
     L.ibm_marker_bases.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
     L.ibm_step_stats.argtypes = [vp, vp]
+    L.ibm_particle_clusters.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
+    L.ibm_particle_clusters.restype = i
     L.ibm_kernel_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i]
     L.ibm_status_string.argtypes = [i]
     L.ibm_status_string.restype = ctypes.c_char_p
@@ -243,6 +247,15 @@ class Context:
         ms, n = ctypes.c_double(), ctypes.c_int64()
         self._check(self.L.ibm_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n), int(reset)))
         return ms.value, n.value
+
+    def particle_clusters(self):
+        """Each particle's cluster and its cluster's IBM_PATH_* bits in the last step."""
+        n = self.n_p
+        cl = np.zeros(max(n, 1), dtype=np.int32)
+        path = np.zeros(max(n, 1), dtype=np.int32)
+        nc = ctypes.c_int64()
+        self._check(self.L.ibm_particle_clusters(self.h, _ptr(cl), _ptr(path), ctypes.byref(nc)))
+        return cl[:n], path[:n], int(nc.value)
 
     def stats(self):
         out = np.zeros(10, dtype=np.int64)

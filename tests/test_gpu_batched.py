@@ -1,0 +1,83 @@
+"""Batched scenes against the oracle: the first 80 scenes of the batched
+workload (periodic boxes of edge 32..128, 1-40 spheres each, D ~ U[8, 20]h) run
+in one context, i.e. one persistent cluster-kernel launch per step over all
+scenes, in the benchmark's mode (FP32, deterministic spreading); 40 scenes are
+then compared with the oracle scene by scene: every 32^3 box (the densest:
+40-46% solid, clusters that wrap the period) and the densest boxes of the other
+edges.  Both kernel variants (one 1024-thread CTA per SM, two 512-thread CTAs)
+and the CUDA-graph replay of the step give the same result within the FP32
+tolerances.
+"""
+import numpy as np
+import pytest
+
+from tests._helpers import f32_round, gpu_context, load_err, rel_err_u
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2109_03972_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_2109_03972_gb300 import ibm, synth  # noqa: E402
+
+U_TOL32, LOAD_TOL32 = 2e-5, 1e-4
+N_SCENES, N_CHECK = 80, 40
+
+
+@pytest.fixture(scope="module")
+def batch():
+    from oracle import oracle as O
+    O.build()
+    W = synth.workload("batched", n_scenes=N_SCENES)
+    scenes = W.scenes
+    u0s = [f32_round(s.field()) for s in scenes]
+    solid = np.array([(np.pi / 6 * s.d_p ** 3).sum() / np.prod(s.dims) for s in scenes])
+    edge = np.array([s.dims[0] for s in scenes])
+    pick = [int(k) for k in np.nonzero(edge == 32)[0]]
+    rest = [int(k) for k in np.argsort(-solid) if edge[k] != 32 and scenes[k].n_p > 0]
+    pick += rest[:N_CHECK - len(pick)]
+    refs = {k: O.forcing_step(u0s[k], scenes[k].x_p, scenes[k].u_p, scenes[k].omega_p, scenes[k].d_p,
+                              n_forcing=3, tau=0.01) for k in pick}
+    return scenes, u0s, pick, refs
+
+
+def _run(scenes, u0s, tpb=0, graph=False, steps=1):
+    n = sum(s.n_p for s in scenes)
+    ctx = gpu_context([s.dims for s in scenes], n, ibm.IBM_FP32, ibm.IBM_SPREAD_DETERMINISTIC, tpb=tpb)
+    if graph:
+        cfg = ibm.Config(**{**ctx.cfg.__dict__, "use_graph": True})
+        ctx = ibm.Context(cfg)
+    x = np.concatenate([s.x_p for s in scenes])
+    up = np.concatenate([s.u_p for s in scenes])
+    om = np.concatenate([s.omega_p for s in scenes])
+    d = np.concatenate([s.d_p for s in scenes])
+    so = np.concatenate([np.full(s.n_p, i, dtype=np.int32) for i, s in enumerate(scenes)])
+    ctx.set_particles(x, up, om, d, scene_of=so)
+    us = [torch.from_numpy(a).float().cuda() for a in u0s]
+    for _ in range(steps):
+        for u, a in zip(us, u0s):
+            u.copy_(torch.from_numpy(a))
+        ctx.forcing_step(us, 0.01)
+    loads = ctx.particle_loads()
+    torch.cuda.synchronize()
+    return ctx, [u.double().cpu().numpy() for u in us], loads
+
+
+@pytest.mark.parametrize("tpb,graph", [(1024, False), (512, False), (1024, True)])
+def test_batched_scenes_match_oracle(batch, tpb, graph):
+    scenes, u0s, pick, refs = batch
+    assert len(pick) == N_CHECK and sum(scenes[k].dims[0] == 32 for k in pick) >= 10
+    ctx, us, loads = _run(scenes, u0s, tpb=tpb, graph=graph, steps=3 if graph else 1)
+    st = ctx.stats()
+    assert st["threads_per_block"] == tpb
+    off = np.cumsum([0] + [s.n_p for s in scenes])
+    for k in pick:
+        s, ref = scenes[k], refs[k]
+        assert rel_err_u(us[k], ref["u"], u0s[k]) <= U_TOL32, k
+        sl = slice(off[k], off[k + 1])
+        assert load_err(loads["F"][sl], ref["F"], ref["Fabs"]) <= LOAD_TOL32, k
+        assert load_err(loads["T"][sl], ref["T"], 0.5 * s.d_p * ref["Fabs"]) <= LOAD_TOL32, k

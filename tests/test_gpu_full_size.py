@@ -3,12 +3,18 @@
 (FP32, deterministic spreading, 1024-thread cluster kernel).
 
 The oracle cannot run the whole bed in seconds, so the test checks
-  * sampled outputs element by element: a particle whose centre is farther than
-    a_p + a_q + 3 sqrt 3 + 1 from every other centre is its own cluster (no
-    other stencil can reach its cells), so its loads and its cells after the
-    step depend only on u^0 around it; the oracle runs it alone on a periodic
-    sub-box cut out of u^0 around the particle, wide enough that no stencil
-    wraps;
+  * sampled outputs element by element: particles whose marker stencils share
+    no cell with any other particle's form independent clusters (Sec. 2.2.2:
+    no cell of one cluster is read or written by another), so a cluster's
+    loads and its cells after the step depend only on u^0 around it; the
+    oracle runs the cluster alone on a periodic sub-box cut out of u^0 around
+    it, wide enough that no stencil wraps.  The clusters come from the
+    library's own record of the step (ibm_particle_clusters): isolated
+    particles, the largest cluster in shared memory, multi-particle clusters of
+    assorted sizes on each shared-memory code path, and every cluster that ran
+    the plain fallback;
+  * the stencil base cell of every one of the 8.1M markers, bit for bit
+    against the oracle (the FP32 positions fall back to FP64 near a cell face);
   * a property of the whole step: the fluid's momentum change equals tau times
     the summed fluid-side loads, sum_c (u^{n_F} - u^0)_c h^3 = tau sum_p F_p
     (spreading is the D-weighted adjoint of interpolation, Sec. 2.2.2).
@@ -51,10 +57,12 @@ def bed_step():
     ctx.forcing_step([u], W.tau)
     loads = ctx.particle_loads()
     stats = ctx.stats()
+    clusters = ctx.particle_clusters()
+    bases = ctx.marker_bases()
     u1 = u.cpu().numpy()
     del u
     torch.cuda.synchronize()
-    return W, sc, u0, u1, loads, stats
+    return W, sc, u0, u1, loads, stats, clusters, bases
 
 
 def _isolated(sc, count_by_d):
@@ -75,7 +83,7 @@ def _isolated(sc, count_by_d):
 
 
 def test_full_bed_isolated_particles_match_oracle(oracle_mod, bed_step):
-    W, sc, u0, u1, loads, stats = bed_step
+    W, sc, u0, u1, loads, stats, _, _ = bed_step
     assert stats["markers"] == 8139000
     nx, ny, nz = sc.dims
     picked = _isolated(sc, {12.0: 4, 24.0: 2})
@@ -103,7 +111,7 @@ def test_full_bed_isolated_particles_match_oracle(oracle_mod, bed_step):
 
 
 def test_full_bed_momentum_balance(bed_step):
-    W, sc, u0, u1, loads, stats = bed_step
+    W, sc, u0, u1, loads, stats, _, _ = bed_step
     nz = sc.dims[2]
     du = np.zeros(3)
     for q in range(3):                                      # h = 1; summed slab by slab in FP64
@@ -113,3 +121,101 @@ def test_full_bed_momentum_balance(bed_step):
     scale = W.tau * np.abs(loads["F"]).sum()
     # FP32 storage of the touched cells (~3e-6 each, random) dominates the mismatch
     assert np.abs(du - f).max() <= 1e-5 * scale
+
+
+def _cut_out(sc, members, u, margin=4):
+    """Periodic sub-box of u around the particles `members` (unwrapped next to
+    the first by minimum image), `margin` cells beyond their stencil boxes;
+    returns (sub-box, centres in sub-box coordinates) or None if it would not
+    fit in one period."""
+    L = np.array(sc.dims)
+    x0 = sc.x_p[members[0]]
+    dv = sc.x_p[members] - x0
+    dv -= L * np.round(dv / L)
+    xu = x0 + dv
+    a = 0.5 * sc.d_p[members][:, None]
+    lo = np.floor((xu - a).min(0)).astype(int) - margin
+    hi = np.floor((xu + a).max(0)).astype(int) + margin
+    S = hi - lo + 1
+    if np.any(S > L):
+        return None
+    ix, iy, iz = ((lo[k] + np.arange(S[k])) % L[k] for k in range(3))
+    return u[:, iz][:, :, iy][:, :, :, ix].astype(np.float64), xu - lo
+
+
+def _pick_clusters(sc, cl, path):
+    """The clusters to check: every fallback cluster, the largest one in shared
+    memory, and multi-particle shared-memory clusters of assorted sizes with at
+    least one per shared-memory code path that occurs."""
+    ids, inv = np.unique(cl, return_inverse=True)
+    members = [[] for _ in ids]
+    for p, k in enumerate(inv):
+        members[k].append(p)
+    # markers per cluster, each particle's count padded to whole 32-marker chunks
+    # as the library counts them
+    from oracle import oracle as O
+    nl = {d: O.marker_count(d) for d in np.unique(sc.d_p)}
+    nm = np.array([sum((nl[sc.d_p[p]] + 31) // 32 * 32 for p in m) for m in members])
+    cpath = np.array([path[m[0]] for m in members])
+    picked = {k for k in range(len(ids)) if cpath[k] & ibm.IBM_PATH_FALLBACK}
+    smem = [k for k in range(len(ids)) if cpath[k] & ibm.IBM_PATH_SMEM]
+    multi = sorted((k for k in smem if len(members[k]) > 1), key=lambda k: nm[k])
+    picked.add(max(smem, key=lambda k: nm[k]))
+    for bit in (ibm.IBM_PATH_GLOBAL_RECORDS, ibm.IBM_PATH_ONE_COMPONENT, ibm.IBM_PATH_SPARSE_ROWS):
+        with_bit = [k for k in multi if cpath[k] & bit]
+        if with_bit:
+            picked.add(with_bit[len(with_bit) // 2])
+            picked.add(with_bit[-1])
+    for q in np.linspace(0, len(multi) - 1, 12).astype(int):
+        picked.add(multi[q])
+    return [(members[k], int(cpath[k]), int(nm[k])) for k in sorted(picked)]
+
+
+def test_full_bed_clusters_match_oracle(oracle_mod, bed_step):
+    """Multi-particle clusters of the bed, including all fallback clusters and
+    the largest shared-memory cluster, against the oracle on cut-out sub-boxes
+    (u on the cluster's stencil cells at 2e-5 max|u^0|, loads at 1e-4 sum|F|dV)."""
+    W, sc, u0, u1, loads, stats, (cl, path, n_clusters), _ = bed_step
+    assert n_clusters == stats["clusters"]
+    chosen = _pick_clusters(sc, cl, path)
+    n_fb = sum(1 for _, cp, _ in chosen if cp & ibm.IBM_PATH_FALLBACK)
+    assert n_fb == stats["clusters"] - stats["clusters_smem"]
+    assert sum(nm for _, cp, nm in chosen if cp & ibm.IBM_PATH_FALLBACK) == stats["markers_fallback"]
+    assert sum(1 for m, cp, _ in chosen if len(m) > 1 and cp & ibm.IBM_PATH_SMEM) >= 10
+    seen = 0
+    for members, cpath, nm in chosen:
+        cut = _cut_out(sc, members, u0)
+        assert cut is not None
+        sub0, x = cut
+        sub1, _ = _cut_out(sc, members, u1)
+        m = np.array(members)
+        ref = oracle_mod.forcing_step(sub0, x, sc.u_p[m], sc.omega_p[m], sc.d_p[m], n_forcing=W.n_forcing,
+                                      tau=W.tau)
+        mine = np.any(ref["u"] != sub0, axis=0)
+        scale = np.abs(sub0).max()
+        err = np.abs((sub1 - ref["u"])[:, mine]).max() / scale
+        assert err <= U_TOL32, (members, cpath, err)
+        fe = (np.abs(loads["F"][m] - ref["F"]).max(1) / ref["Fabs"]).max()
+        te = (np.abs(loads["T"][m] - ref["T"]).max(1) / (0.5 * sc.d_p[m] * ref["Fabs"])).max()
+        assert fe <= LOAD_TOL32 and te <= LOAD_TOL32, (members, cpath, fe, te)
+        seen += 1
+    assert seen >= 13
+
+
+def test_full_bed_bins_bit_exact(oracle_mod, bed_step):
+    """Stencil base cells of all 8,139,000 markers as the FP32 path computes them
+    against the oracle's floor of the FP64 positions.  The FP32 split falls back
+    to FP64 within its error bound of a face; those markers are counted to show
+    that the bed exercises that branch."""
+    W, sc, u0, u1, loads, stats, _, bases = bed_step
+    xi, base = oracle_mod.marker_positions(sc.x_p, sc.d_p)
+    assert bases.shape == base.shape == (8139000, 3)
+    frac = xi - np.floor(xi)
+    dist = np.minimum(frac, 1.0 - frac)
+    # host and device sin/cos of the marker directions may differ in the last bit
+    ties = (dist < 1e-12) & (dist > 0.0)
+    assert ties.sum() == 0
+    a = np.repeat(0.5 * sc.d_p, [oracle_mod.marker_count(d) for d in sc.d_p])
+    band = dist < 8.0 * 2.0 ** -24 * (a[:, None] + 2.0)
+    assert band.sum() > 100
+    assert np.array_equal(bases, base)
