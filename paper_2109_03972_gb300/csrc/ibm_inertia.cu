@@ -9,15 +9,22 @@
 // evaluations of these integrals (the direct form that avoids the rigid-body
 // singularity at rho_p = rho_f).
 //
-// One block per particle walks the box floor(x_p/h - a) - 1 .. floor(x_p/h + a) + 1
-// per axis, one thread per cell, x fastest, so a warp reads contiguous row
-// segments of u.  A cell
-// whose centre lies more than sqrt(3)/2 inside (outside) the surface has all
-// corners inside (outside): alpha = 1 (0, and u is not read); only the cells
-// cut by the surface evaluate the eight corners.  FP32 fields: per-thread sums
-// in FP32 (at most a few dozen cells each), the block sum in FP64; FP64 fields
-// sum in FP64 throughout.  Per particle the result is written once, without
-// atomics, so it is bit-reproducible.
+// One block per particle.  Along a grid row (fixed y, z) the cells with
+// alpha > 0, those with a corner strictly inside the sphere, lie in one x-run
+// whose ends follow in closed form from the distance of the row's nearest
+// corner line to the centre.  The block computes the run of every row of the
+// particle's box, flattens the runs with a block-wide prefix sum, and gives
+// consecutive threads consecutive cells of the flattened list, so that the
+// loads of a warp cover a few contiguous row segments of u (whole 32-byte
+// sectors) and no thread evaluates a cell that cannot contribute.  A thread
+// finds its row from a table of the row holding every 32nd cell (no integer
+// division) and keeps two cells in flight.  Each lane evaluates the four
+// corners of its cell's lower x-face; the upper face comes from the next lane,
+// which holds the next cell of the same row except at a row's end.  Boxes with
+// more rows than the shared-memory table holds are taken in chunks of whole
+// rows.  FP32 fields: per-thread sums in FP32, the block sum in FP64; FP64
+// fields sum in FP64 throughout.  Per particle the result is written once,
+// without atomics, so it is bit-reproducible.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,77 +41,217 @@
 
 namespace {
 
-constexpr int kInBlock = 256;
+constexpr int kInBlock = 128;
+constexpr int kRowCap = 768;          // rows of the run table (27 x 27 boxes of D = 24h fit)
+constexpr int kRowsPerThread = kRowCap / kInBlock;
+constexpr int kChunkCap = 512;        // 32-cell chunks with a start-row entry (16K cells)
+
+// Square root and quotient of the level-set fraction: FP64 exact; FP32 the
+// hardware approximations (relative error of order 2^-23, below the FP32
+// rounding of phi = |x| - a itself).
+__device__ __forceinline__ double lsqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float lsqrt(float v) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ double ldiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float ldiv(float a, float b) { return __fdividef(a, b); }
 
 template <typename T>
-__global__ void __launch_bounds__(kInBlock) k_inertia(int n_p, const PInfo *__restrict__ P,
-                                                     const int32_t *__restrict__ dims, const T *const *uf, double h,
-                                                     double *__restrict__ out) {
+__global__ void __launch_bounds__(kInBlock, sizeof(T) == 4 ? 10 : 4)
+    k_inertia(int n_p, const PInfo *__restrict__ P, const int32_t *__restrict__ dims, const T *const *uf, double h,
+              double *__restrict__ out) {
+    __shared__ int s_pre[kRowCap + 1];
+    __shared__ short s_x0[kRowCap], s_iy[kRowCap], s_iz[kRowCap];
+    __shared__ short s_crow[kChunkCap];
+    __shared__ int s_scan[32], s_tot;
     __shared__ double sh[7][kInBlock / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     for (int p = blockIdx.x; p < n_p; p += gridDim.x) {
         const PInfo &Pp = P[p];
         const int nx = dims[3 * Pp.scene], ny = dims[3 * Pp.scene + 1], nz = dims[3 * Pp.scene + 2];
         const long long ncell = (long long)nx * ny * nz;
-        const T *__restrict__ u = uf[Pp.scene];
+        const T *__restrict__ u0 = uf[Pp.scene];
+        const T *__restrict__ u1 = u0 + ncell;
+        const T *__restrict__ u2 = u1 + ncell;
         const double a = Pp.a;
         int lo[3], ext[3];
         for (int c = 0; c < 3; ++c) {
             lo[c] = (int)floor(Pp.xi[c] - a) - 1;
             ext[c] = (int)floor(Pp.xi[c] + a) + 1 - lo[c] + 1;
         }
-        // cell-centre offsets relative to x_p, per axis origin (grid units)
+        // the box origin taken into the period once; a box is at most one period wide
+        const int wx0 = wrapi(lo[0], nx), wy0 = wrapi(lo[1], ny), wz0 = wrapi(lo[2], nz);
+        // cell-centre offsets relative to x_p of the box's first cell (grid units)
         const T ox = (T)((double)lo[0] + 0.5 - Pp.xi[0]);
         const T oy = (T)((double)lo[1] + 0.5 - Pp.xi[1]);
         const T oz = (T)((double)lo[2] + 0.5 - Pp.xi[2]);
         const T at = (T)a;
-        const T r_in = at - (T)0.8660254037844386, r_out = at + (T)0.8660254037844386;
-        const T r_in2 = r_in > T(0) ? r_in * r_in : T(-1), r_out2 = r_out * r_out;
         T s[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-        const int ncb = ext[0] * ext[1] * ext[2];
-        for (int t = threadIdx.x; t < ncb; t += blockDim.x) {
-            const int ix = t % ext[0], iy = (t / ext[0]) % ext[1], iz = t / (ext[0] * ext[1]);
-            const T cx = ox + (T)ix, cy = oy + (T)iy, cz = oz + (T)iz;     // centre - x_p
-            const T d2 = cx * cx + cy * cy + cz * cz;
-            if (d2 > r_out2) continue;
-            T alpha = T(1);
-            if (!(d2 < r_in2)) {
-                T num = T(0), den = T(0);
+        const int nrows = ext[1] * ext[2];
+        for (int r0 = 0; r0 < nrows; r0 += kRowCap) {
+            const int nr = min(kRowCap, nrows - r0);
+            // x-run of each row: columns whose nearest corner, ||cx| - 1/2| away in
+            // x from the row's nearest corner line, can lie inside; a relative
+            // margin of 1e-4 keeps the run inclusive (the corners decide)
+            int len[kRowsPerThread], sum = 0;
 #pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    const T qx = cx + ((m & 1) ? T(0.5) : T(-0.5));
-                    const T qy = cy + ((m & 2) ? T(0.5) : T(-0.5));
-                    const T qz = cz + ((m & 4) ? T(0.5) : T(-0.5));
-                    const T phi = sqrt(qx * qx + qy * qy + qz * qz) - at;
-                    if (phi <= T(0)) num -= phi;
-                    den += fabs(phi);
+            for (int k = 0; k < kRowsPerThread; ++k) {
+                const int i = tid * kRowsPerThread + k;
+                len[k] = 0;
+                if (i < nr) {
+                    const int r = r0 + i;
+                    const int iz = r / ext[1], iy = r - iz * ext[1];   // once per row
+                    const T cy = fabs(oy + (T)iy) - T(0.5), cz = fabs(oz + (T)iz) - T(0.5);
+                    const T dn = at * at - cy * cy - cz * cz;
+                    int x0 = 0, x1 = -1;
+                    if (dn > T(-1e-4) * at * at) {
+                        const T B = sqrt(fmax(dn, T(0))) + T(0.5) + T(1e-4) * at;
+                        // columns with |ox + ix| < B
+                        x0 = max(0, (int)floor(-B - ox) + 1);
+                        x1 = min(ext[0] - 1, (int)ceil(B - ox) - 1);
+                    }
+                    len[k] = max(0, x1 - x0 + 1);
+                    s_x0[i] = (short)x0;
+                    s_iy[i] = (short)iy;
+                    s_iz[i] = (short)iz;
                 }
-                alpha = den > T(0) ? num / den : T(0);
-                if (alpha == T(0)) continue;
+                sum += len[k];
             }
-            const long long idx = ((long long)wrapi(lo[2] + iz, nz) * ny + wrapi(lo[1] + iy, ny)) * nx +
-                                  wrapi(lo[0] + ix, nx);
-            const T u0 = u[idx], u1 = u[ncell + idx], u2 = u[2 * ncell + idx];
-            s[0] += alpha * u0;
-            s[1] += alpha * u1;
-            s[2] += alpha * u2;
-            s[3] += alpha * (cy * u2 - cz * u1);
-            s[4] += alpha * (cz * u0 - cx * u2);
-            s[5] += alpha * (cx * u1 - cy * u0);
-            s[6] += alpha;
+            // block-wide exclusive prefix of the run lengths
+            int x = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_scan[wid] = x;
+            __syncthreads();
+            if (tid == 0) {
+                int acc = 0;
+                for (int w = 0; w < kInBlock / 32; ++w) {
+                    const int v = s_scan[w];
+                    s_scan[w] = acc;
+                    acc += v;
+                }
+                s_tot = acc;
+            }
+            __syncthreads();
+            {
+                int run = s_scan[wid] + x - sum;
+#pragma unroll
+                for (int k = 0; k < kRowsPerThread; ++k) {
+                    const int i = tid * kRowsPerThread + k;
+                    if (i < nr) s_pre[i] = run;
+                    run += len[k];
+                }
+            }
+            if (tid == 0) s_pre[nr] = s_tot;
+            __syncthreads();
+            const int total = s_tot;
+            // start row of every 32-cell chunk (the row holding cell 32k)
+            const bool chunked = total <= 32 * kChunkCap;
+            if (chunked)
+                for (int i = tid; i < nr; i += kInBlock) {
+                    const int c0 = s_pre[i], c1 = s_pre[i + 1];
+                    for (int k = (c0 + 31) >> 5; 32 * k < c1; ++k) s_crow[k] = (short)i;
+                }
+            __syncthreads();
+            // consecutive threads take consecutive cells of the runs (the cells of a
+            // warp are whole 32-cell chunks); the loop bound is uniform per warp
+            for (int t0 = tid; t0 < total + lane; t0 += 2 * kInBlock) {
+                T al[2], cx[2], cy[2], cz[2];
+                long long idx[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int t = t0 + j * kInBlock;
+                    const bool valid = t < total;
+                    int r = 0;
+                    if (valid) {
+                        if (chunked) {
+                            r = s_crow[t >> 5];
+                            while (s_pre[r + 1] <= t) ++r;
+                        } else {
+                            int lo_r = 0, hi_r = nr - 1;   // last row with s_pre <= t
+                            while (lo_r < hi_r) {
+                                const int mid = (lo_r + hi_r + 1) >> 1;
+                                if (s_pre[mid] <= t) lo_r = mid;
+                                else hi_r = mid - 1;
+                            }
+                            r = lo_r;
+                        }
+                    }
+                    const int ix = valid ? s_x0[r] + (t - s_pre[r]) : 0;
+                    const int iy = valid ? s_iy[r] : 0, iz = valid ? s_iz[r] : 0;
+                    cx[j] = ox + (T)ix;
+                    cy[j] = oy + (T)iy;
+                    cz[j] = oz + (T)iz;
+                    // signed distances of the four corners of the lower x-face
+                    const T xl = cx[j] - T(0.5);
+                    const T ym = cy[j] - T(0.5), yp = cy[j] + T(0.5), zm = cz[j] - T(0.5), zp = cz[j] + T(0.5);
+                    const T yz[4] = {ym * ym + zm * zm, yp * yp + zm * zm, ym * ym + zp * zp, yp * yp + zp * zp};
+                    T ph[8];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) ph[k] = lsqrt(xl * xl + yz[k]) - at;
+                    // upper x-face: from the next lane when it holds the next cell of this row
+                    const int rn = __shfl_down_sync(0xffffffffu, valid ? r : -1, 1);
+                    const bool own = !(lane < 31 && rn == r && valid);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) ph[4 + k] = __shfl_down_sync(0xffffffffu, ph[k], 1);
+                    if (own) {
+                        const T xu = cx[j] + T(0.5);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) ph[4 + k] = lsqrt(xu * xu + yz[k]) - at;
+                    }
+                    T num = T(0), den = T(0);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (ph[k] <= T(0)) num -= ph[k];
+                        den += fabs(ph[k]);
+                    }
+                    // alpha = 1 exactly when every corner is inside (num == den)
+                    al[j] = !valid || !(num > T(0)) ? T(0) : (num == den ? T(1) : ldiv(num, den));
+                    int gx = wx0 + ix, gy = wy0 + iy, gz = wz0 + iz;
+                    if (gx >= nx) gx -= nx;
+                    if (gy >= ny) gy -= ny;
+                    if (gz >= nz) gz -= nz;
+                    idx[j] = ((long long)gz * ny + gy) * nx + gx;
+                }
+                T v[2][3];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const bool ld = al[j] != T(0);
+                    v[j][0] = ld ? u0[idx[j]] : T(0);
+                    v[j][1] = ld ? u1[idx[j]] : T(0);
+                    v[j][2] = ld ? u2[idx[j]] : T(0);
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const T w = al[j];
+                    s[0] += w * v[j][0];
+                    s[1] += w * v[j][1];
+                    s[2] += w * v[j][2];
+                    s[3] += w * (cy[j] * v[j][2] - cz[j] * v[j][1]);
+                    s[4] += w * (cz[j] * v[j][0] - cx[j] * v[j][2]);
+                    s[5] += w * (cx[j] * v[j][1] - cy[j] * v[j][0]);
+                    s[6] += w;
+                }
+            }
+            __syncthreads();
         }
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
             const double v = warp_sum((double)s[k]);
             if (lane == 0) sh[k][wid] = v;
         }
         __syncthreads();
-        if (threadIdx.x < 7) {
+        if (tid < 7) {
             double v = 0.0;
-            for (int w = 0; w < kInBlock / 32; ++w) v += sh[threadIdx.x][w];
+            for (int w = 0; w < kInBlock / 32; ++w) v += sh[tid][w];
             const double h3 = h * h * h;
             // arms are in grid units: r x u carries one more factor h
-            out[7ll * p + threadIdx.x] = v * (threadIdx.x >= 3 && threadIdx.x < 6 ? h3 * h : h3);
+            out[7ll * p + tid] = v * (tid >= 3 && tid < 6 ? h3 * h : h3);
         }
         __syncthreads();
     }
@@ -137,7 +284,7 @@ extern "C" ibm_status ibm_particle_inertia(ibm_ctx *ctx, void *const *u_ptrs, do
         CK(cudaMemcpyAsync(ctx->in_ptr, ctx->in_ptr_h.data(), ns * sizeof(void *), cudaMemcpyHostToDevice,
                            ctx->stream), "copy field pointers");
     }
-    const int grid = std::min(ctx->n_p, 152 * 16);
+    const int grid = std::min(ctx->n_p, 152 * 16);   // grid-stride over particles
     if (ctx->cfg.precision == IBM_FP64)
         k_inertia<double><<<grid, kInBlock, 0, ctx->stream>>>(
             ctx->n_p, ctx->pinfo, ctx->dims_d, reinterpret_cast<const double *const *>(ctx->in_ptr), ctx->cfg.h,
