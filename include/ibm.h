@@ -67,6 +67,11 @@ enum { IBM_FP64 = 0, IBM_FP32 = 1 };
  *                            fixed point (per group and iteration a power-of-
  *                            two scale), in shared memory and on the plain
  *                            path alike, so results are bit-reproducible.
+ *                            The scale assumes that no cell collects more
+ *                            than 64 unit weights (far above what non-
+ *                            overlapping spheres give); heavily overlapping
+ *                            particles that break it make the step report
+ *                            IBM_ERR_CAPACITY at its next synchronising call.
  *  IBM_SPREAD_PLAIN          One thread per marker, global atomics into u, two
  *                            kernels per iteration.  The only mode for FP64
  *                            ("plain FP64 form"). */
@@ -323,6 +328,25 @@ ibm_status ibm_forcing_step_static(int nx, int ny, int nz, double h, int n_forci
                                    const double *x_p, const double *u_p, const double *omega_p,
                                    const double *d_p, double *u, double *F_out, double *T_out,
                                    void *cuda_stream);
+
+/* Bound of the device-side retry loops of the cluster modes (the lock-free
+ * union-find that joins particles into clusters retries a compare-and-swap
+ * until it succeeds; every retry loop gives up after this many iterations and
+ * the step reports IBM_ERR_TIMEOUT at its next synchronising call instead of
+ * spinning on).  0 restores the default, 2^22.  Applies to the following
+ * forcing steps of ctx; a step that gave up leaves its velocity field invalid,
+ * the context itself stays usable.  The paper has no counterpart: it is a
+ * safeguard of this library, exposed so that the give-up path can be tested.
+ * Errors: INVALID_ARG (NULL ctx, iterations < 0 or > INT32_MAX). */
+ibm_status ibm_set_wait_limit(ibm_ctx *ctx, int64_t iterations);
+
+/* Test hook, process-wide: the n-th device allocation the library makes after
+ * this call fails as if the device were out of memory (the call that makes it
+ * returns IBM_ERR_OOM and releases what it had allocated so far); n = 0 turns
+ * the hook off.  No GPU fault is involved: the allocation is refused on the
+ * host before cudaMalloc.  The paper has no counterpart.
+ * Errors: INVALID_ARG (n < 0). */
+ibm_status ibm_debug_fail_allocation(int64_t n);
 
 /* Human-readable status name; never NULL. */
 const char *ibm_status_string(ibm_status s);

@@ -50,7 +50,7 @@ constexpr int kCapP = 32;        // particles per shared-memory batch
 constexpr int kBuckets = 1024;   // work-order buckets
 constexpr int kPairThreads = 128;
 constexpr int kPairCap = 1024;   // near-marker list in the exact pair test
-constexpr int kUnionSpin = 1 << 22;
+constexpr int kUnionSpin = 1 << 22;   // default bound of the union-find retries
 constexpr int kSparseRows = 32768;   // box rows (y, z) of a cluster with a sparse row table
 
 enum {
@@ -92,8 +92,8 @@ struct ClusterScratch {
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *((const volatile int *)p); }
 
-__device__ int uf_find(int *parent, int x) {
-    for (int it = 0; it < kUnionSpin; ++it) {
+__device__ int uf_find(int *parent, int x, int spin) {
+    for (int it = 0; it < spin; ++it) {
         const int p = ld_volatile(parent + x);
         if (p == x) return x;
         const int gp = ld_volatile(parent + p);
@@ -103,10 +103,10 @@ __device__ int uf_find(int *parent, int x) {
     return -1;
 }
 
-__device__ bool uf_unite(int *parent, int a, int b) {
-    for (int it = 0; it < kUnionSpin; ++it) {
-        a = uf_find(parent, a);
-        b = uf_find(parent, b);
+__device__ bool uf_unite(int *parent, int a, int b, int spin) {
+    for (int it = 0; it < spin; ++it) {
+        a = uf_find(parent, a, spin);
+        b = uf_find(parent, b, spin);
         if (a < 0 || b < 0) return false;
         if (a == b) return true;
         if (a > b) { const int t = a; a = b; b = t; }
@@ -217,7 +217,7 @@ __global__ void k_candidates(int n_p, const PInfo *P, const int *scene_nb, const
 // comparing the two lists pair by pair.
 __global__ void __launch_bounds__(kPairThreads) k_pair_test(const PInfo *P, const float *t32, const double *t64,
                                                             const int32_t *dims, const int *cand, const int *cnt,
-                                                            int cap_cand, int *parent, int *err) {
+                                                            int cap_cand, int *parent, int spin, int *err) {
     __shared__ int3 qb[kPairCap];
     __shared__ unsigned vol[2][32 * 32];   // [z][y] rows of 32 x-bits
     __shared__ int nq, found, over, lo[3], hi[3];
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_test(const PInfo *P, cons
         __syncthreads();
         const int n = nq;
         if (over) {
-            if (threadIdx.x == 0 && !uf_unite(parent, p, q)) set_err(err, IBM_EBIT_TIMEOUT);
+            if (threadIdx.x == 0 && !uf_unite(parent, p, q, spin)) set_err(err, IBM_EBIT_TIMEOUT);
             __syncthreads();
             continue;
         }
@@ -325,14 +325,14 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_test(const PInfo *P, cons
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0 && found && !uf_unite(parent, p, q)) set_err(err, IBM_EBIT_TIMEOUT);
+        if (threadIdx.x == 0 && found && !uf_unite(parent, p, q, spin)) set_err(err, IBM_EBIT_TIMEOUT);
         __syncthreads();
     }
 }
 
-__global__ void k_roots(int n_p, int *parent, int *root_flag, int *err) {
+__global__ void k_roots(int n_p, int *parent, int *root_flag, int spin, int *err) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_p; p += gridDim.x * blockDim.x) {
-        const int r = uf_find(parent, p);
+        const int r = uf_find(parent, p, spin);
         if (r < 0) { set_err(err, IBM_EBIT_TIMEOUT); root_flag[p] = 0; continue; }
         root_flag[p] = (r == p);
     }
@@ -355,9 +355,9 @@ __global__ void k_cluster_init(int n, int *cl_np, int *cl_nm, int *cl_cur, int *
 // Per particle: its cluster, the whole-period shift that unwraps it next to
 // the cluster's root, and the cluster's stencil box (floor(xi -+ a) -+ 1).
 __global__ void k_cluster_stats(int n_p, const PInfo *P, const int32_t *dims, int *parent, const int *cid,
-                                int *pcl, int *poff, int *cl_np, int *cl_nm, int *cl_box) {
+                                int *pcl, int *poff, int *cl_np, int *cl_nm, int *cl_box, int spin) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_p; p += gridDim.x * blockDim.x) {
-        const int r = uf_find(parent, p);
+        const int r = uf_find(parent, p, spin);
         const int c = cid[r < 0 ? p : r];
         pcl[p] = c;
         const PInfo &Pp = P[p];
@@ -834,9 +834,14 @@ __device__ __forceinline__ void ghost_pass(const Batch &bt, const CS *s_cs, cons
 // scale per cluster and iteration.  The scale comes from a running bound B on
 // |u| over the cluster's cells: B_0 = max |u^0| (one scan after the gather),
 // and before the spreading of iteration m, B_m = B_{m-1} + 64 Dmax max|e^m|,
-// which bounds |u^m| because no cell collects more than 64 unit weights
+// which bounds |u^m| as long as no cell collects more than 64 unit weights
 // (Sec. 2.2.2: u^m = u^{m-1} + W^T D e^m).  2^k is the largest power of two
-// with B_m 2^k < 2^30, so every cell value and every partial sum fits.  The
+// with B_m 2^k < 2^28.  Integer addition wraps modulo 2^32 and is associative,
+// so partial sums may wrap harmlessly; a final cell value above 2^28 in
+// magnitude means the weight bound was broken (particles overlapping far more
+// than non-overlapping spheres can) and sets IBM_EBIT_FIXEDPOINT on the way
+// back to floating point; only a violation by more than a factor of about 15
+// can wrap back into range unseen.  The
 // scale depends only on the cluster, never on how clusters are batched or on
 // the order of the atomic additions, so the result is bit-reproducible.
 // The per-cluster slot ranges start at multiples of 4 and their padding is
@@ -872,7 +877,7 @@ __device__ __forceinline__ void det_scale(const Batch &bt, CS *s_cs) {
     for (int j = threadIdx.x; j < bt.nb; j += TPB) {
         const float range = __uint_as_float(s_cs[j].umax) + 64.f * s_cs[j].dmax * __uint_as_float(s_cs[j].emax);
         int ex = 100;
-        if (range > 0.f) ex = min(100, max(-100, 29 - (int)ceilf(log2f(range))));
+        if (range > 0.f) ex = min(100, max(-100, 27 - (int)ceilf(log2f(range))));
         s_cs[j].S = ldexpf(1.f, ex);
         s_cs[j].invS = ldexpf(1.f, -ex);
         s_cs[j].umax = __float_as_uint(range);
@@ -882,9 +887,10 @@ __device__ __forceinline__ void det_scale(const Batch &bt, CS *s_cs) {
 
 // u -> round(u S) (TO) or back, components 0..NC-1 of every cluster.
 template <int TPB, int NC, bool TO>
-__device__ __forceinline__ void det_convert(const Batch &bt, const CS *s_cs, float *s_u) {
+__device__ __forceinline__ void det_convert(const Batch &bt, const CS *s_cs, float *s_u, int *err) {
     const int C = bt.C;
     const int tid = threadIdx.x;
+    bool out_of_range = false;
     for (int j = 0; j < bt.nb; ++j) {
         const int n4 = (s_cs[j].ncell + 3) >> 2;
         const float S = TO ? s_cs[j].S : s_cs[j].invS;
@@ -900,11 +906,14 @@ __device__ __forceinline__ void det_convert(const Batch &bt, const CS *s_cs, flo
                     reinterpret_cast<int4 *>(p)[i] = r;
                 } else {
                     const int4 r = reinterpret_cast<const int4 *>(p)[i];
+                    constexpr int kLim = 1 << 28;
+                    out_of_range |= abs(r.x) > kLim || abs(r.y) > kLim || abs(r.z) > kLim || abs(r.w) > kLim;
                     p[i] = make_float4((float)r.x * S, (float)r.y * S, (float)r.z * S, (float)r.w * S);
                 }
             }
         }
     }
+    if (!TO && out_of_range) set_err(err, IBM_EBIT_FIXEDPOINT);
 }
 
 // Zero the padding slots of every cluster (components 0..NC-1).
@@ -1040,7 +1049,7 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
         if (DET) {
             det_scale<TPB>(bt, s_cs);
             __syncthreads();
-            det_convert<TPB, NC, true>(bt, s_cs, s_u);
+            det_convert<TPB, NC, true>(bt, s_cs, s_u, prm.err);
             __syncthreads();
         }
         if (bt.gx) {
@@ -1087,7 +1096,7 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
             __syncthreads();
         }
         if (DET) {
-            det_convert<TPB, NC, false>(bt, s_cs, s_u);
+            det_convert<TPB, NC, false>(bt, s_cs, s_u, prm.err);
             __syncthreads();
         }
     }
@@ -1547,6 +1556,15 @@ void cluster_free(ibm_ctx *ctx) {
     ctx->cl = nullptr;
 }
 
+// Replaces *p by a new device allocation of `bytes` (the old one released
+// first, so that a failure leaves *p NULL rather than dangling).
+template <typename T>
+static cudaError_t dev_realloc(T **p, size_t bytes) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    return ibm_malloc(p, bytes);
+}
+
 static ibm_status cluster_alloc(ibm_ctx *ctx) {
     ClusterScratch *S = reinterpret_cast<ClusterScratch *>(ctx->cl);
     const int np = std::max(ctx->n_p, 1);
@@ -1572,18 +1590,14 @@ static ibm_status cluster_alloc(ibm_ctx *ctx) {
         }
         off[ctx->cfg.n_scenes] = (int)total;
         if (total > (1 << 28)) return ibm_fail(ctx, IBM_ERR_CAPACITY, "too many particle bins");
-        if (S->scene_bin_off) cudaFree(S->scene_bin_off);
-        if (S->scene_nb) cudaFree(S->scene_nb);
-        CK(cudaMalloc(&S->scene_bin_off, off.size() * sizeof(int)), "alloc bins");
-        CK(cudaMalloc(&S->scene_nb, nb.size() * sizeof(int)), "alloc bins");
+        CK(dev_realloc(&S->scene_bin_off, off.size() * sizeof(int)), "alloc bins");
+        CK(dev_realloc(&S->scene_nb, nb.size() * sizeof(int)), "alloc bins");
         CK(cudaMemcpy(S->scene_bin_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice), "copy");
         CK(cudaMemcpy(S->scene_nb, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice), "copy");
         if ((int)total > S->cap_bins) {
-            for (int **p : {&S->bin_cnt, &S->bin_start, &S->bin_cur})
-                if (*p) cudaFree(*p);
-            CK(cudaMalloc(&S->bin_cnt, (total + 1) * sizeof(int)), "alloc bins");
-            CK(cudaMalloc(&S->bin_start, (total + 1) * sizeof(int)), "alloc bins");
-            CK(cudaMalloc(&S->bin_cur, (total + 1) * sizeof(int)), "alloc bins");
+            CK(dev_realloc(&S->bin_cnt, (total + 1) * sizeof(int)), "alloc bins");
+            CK(dev_realloc(&S->bin_start, (total + 1) * sizeof(int)), "alloc bins");
+            CK(dev_realloc(&S->bin_cur, (total + 1) * sizeof(int)), "alloc bins");
             S->cap_bins = (int)total;
         }
         S->nbins = (int)total;
@@ -1596,23 +1610,16 @@ static ibm_status cluster_alloc(ibm_ctx *ctx) {
         int **arrs[] = {&S->bin_items, &S->parent, &S->root_flag, &S->cid, &S->pcl, &S->cl_np, &S->cl_nm,
                         &S->cl_first, &S->cl_cur, &S->cl_plist, &S->cl_bkt, &S->order, &S->fb_list,
                         &S->nm_ord, &S->cum, &S->cl_scene, &S->cl_path};
-        for (int **p : arrs) {
-            if (*p) cudaFree(*p);
-            CK(cudaMalloc(p, (size_t)(cp + 1) * sizeof(int)), "alloc cluster scratch");
-        }
-        if (S->poff) cudaFree(S->poff);
-        if (S->cl_box) cudaFree(S->cl_box);
-        if (S->batches) cudaFree(S->batches);
-        CK(cudaMalloc(&S->batches, (size_t)(cp + 1) * sizeof(int2)), "alloc batch list");
-        CK(cudaMalloc(&S->poff, 3 * (size_t)cp * sizeof(int)), "alloc cluster scratch");
-        CK(cudaMalloc(&S->cl_box, 12 * (size_t)cp * sizeof(int)), "alloc cluster scratch");
+        for (int **p : arrs) CK(dev_realloc(p, (size_t)(cp + 1) * sizeof(int)), "alloc cluster scratch");
+        CK(dev_realloc(&S->batches, (size_t)(cp + 1) * sizeof(int2)), "alloc batch list");
+        CK(dev_realloc(&S->poff, 3 * (size_t)cp * sizeof(int)), "alloc cluster scratch");
+        CK(dev_realloc(&S->cl_box, 12 * (size_t)cp * sizeof(int)), "alloc cluster scratch");
         S->cap_cand = std::max(1 << 16, 16 * cp);
-        if (S->cand) cudaFree(S->cand);
-        CK(cudaMalloc(&S->cand, 2 * (size_t)S->cap_cand * sizeof(int)), "alloc candidates");
-        if (!S->cnt) CK(cudaMalloc(&S->cnt, C_COUNT * sizeof(int)), "alloc counters");
-        if (!S->tot) CK(cudaMalloc(&S->tot, 4 * sizeof(long long)), "alloc totals");
-        if (!S->bkt_cnt) CK(cudaMalloc(&S->bkt_cnt, (kBuckets + 1) * sizeof(int)), "alloc buckets");
-        if (!S->bkt_start) CK(cudaMalloc(&S->bkt_start, (kBuckets + 1) * sizeof(int) * 2), "alloc buckets");
+        CK(dev_realloc(&S->cand, 2 * (size_t)S->cap_cand * sizeof(int)), "alloc candidates");
+        if (!S->cnt) CK(ibm_malloc(&S->cnt, C_COUNT * sizeof(int)), "alloc counters");
+        if (!S->tot) CK(ibm_malloc(&S->tot, 4 * sizeof(long long)), "alloc totals");
+        if (!S->bkt_cnt) CK(ibm_malloc(&S->bkt_cnt, (kBuckets + 1) * sizeof(int)), "alloc buckets");
+        if (!S->bkt_start) CK(ibm_malloc(&S->bkt_start, (kBuckets + 1) * sizeof(int) * 2), "alloc buckets");
         S->cap_p = cp;
     }
     return IBM_OK;
@@ -1641,7 +1648,7 @@ static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams
         if (S->grec) cudaFree(S->grec);
         S->grec = nullptr;
         S->grec_bytes = 0;
-        CK(cudaMalloc(&S->grec, grec), "alloc marker records");
+        CK(ibm_malloc(&S->grec, grec), "alloc marker records");
         S->grec_bytes = grec;
     }
     prm.grec = S->grec;
@@ -1668,6 +1675,7 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     const bool tuning = req < 0 && ctx->tune_step < 3;
     const int tpb = req > 0 ? req : (req == 0 ? 1024 : (tuning ? (ctx->tune_step == 2 ? 512 : 1024) : ctx->tuned_tpb));
     const int cap_m = tpb * markers_per_thread(tpb);
+    const int spin = ctx->wait_limit > 0 ? ctx->wait_limit : kUnionSpin;
     // row table may take at most half of the dynamic shared memory
     const int max_rows = (max_dyn_smem(ctas_per_sm(tpb)) - fixed_smem_bytes<1024, 12>()) / 16;
 
@@ -1685,12 +1693,12 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     k_candidates<<<grid_for(27ll * n, 256), 256, 0, sm>>>(n, ctx->pinfo, S->scene_nb, S->scene_bin_off, ctx->dims_d,
                                                          S->bin_start, S->bin_items, S->cand, S->cap_cand, S->cnt);
     k_pair_test<<<std::min(S->cap_cand, 152 * 16), kPairThreads, 0, sm>>>(
-        ctx->pinfo, ctx->tmpl32, ctx->tmpl64, ctx->dims_d, S->cand, S->cnt, S->cap_cand, S->parent, ctx->err_d);
-    k_roots<<<gb, 256, 0, sm>>>(n, S->parent, S->root_flag, ctx->err_d);
+        ctx->pinfo, ctx->tmpl32, ctx->tmpl64, ctx->dims_d, S->cand, S->cnt, S->cap_cand, S->parent, spin, ctx->err_d);
+    k_roots<<<gb, 256, 0, sm>>>(n, S->parent, S->root_flag, spin, ctx->err_d);
     k_scan1<<<1, 1024, 0, sm>>>(S->root_flag, S->cid, n, S->tot + 1);
     k_cluster_init<<<gb, 256, 0, sm>>>(n, S->cl_np, S->cl_nm, S->cl_cur, S->cl_box);
     k_cluster_stats<<<gb, 256, 0, sm>>>(n, ctx->pinfo, ctx->dims_d, S->parent, S->cid, S->pcl, S->poff,
-                                        S->cl_np, S->cl_nm, S->cl_box);
+                                        S->cl_np, S->cl_nm, S->cl_box, spin);
     k_scan1<<<1, 1024, 0, sm>>>(S->cl_np, S->cl_first, n, S->tot + 2);
     k_cluster_fill<<<gb, 256, 0, sm>>>(n, S->pcl, S->cl_first, S->cl_cur, S->cl_plist);
     k_cluster_route<<<gb, 256, 0, sm>>>(S->tot + 1, ctx->pinfo, ctx->dims_d, S->cl_np, S->cl_nm, S->cl_first,

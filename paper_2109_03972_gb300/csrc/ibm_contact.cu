@@ -247,11 +247,11 @@ ibm_status ct_alloc(ibm_ctx *ctx, CtScratch *S) {
             *p = nullptr;
         }
         S->n_scenes = 0;
-        CK(cudaMalloc(&S->scene_nb, nb.size() * sizeof(int)), "alloc contact bins");
-        CK(cudaMalloc(&S->scene_off, off.size() * sizeof(int)), "alloc contact bins");
-        CK(cudaMalloc(&S->bin_cnt, (total + 1) * sizeof(int)), "alloc contact bins");
-        CK(cudaMalloc(&S->bin_start, (total + 1) * sizeof(int)), "alloc contact bins");
-        CK(cudaMalloc(&S->bin_cur, (total + 1) * sizeof(int)), "alloc contact bins");
+        CK(ibm_malloc(&S->scene_nb, nb.size() * sizeof(int)), "alloc contact bins");
+        CK(ibm_malloc(&S->scene_off, off.size() * sizeof(int)), "alloc contact bins");
+        CK(ibm_malloc(&S->bin_cnt, (total + 1) * sizeof(int)), "alloc contact bins");
+        CK(ibm_malloc(&S->bin_start, (total + 1) * sizeof(int)), "alloc contact bins");
+        CK(ibm_malloc(&S->bin_cur, (total + 1) * sizeof(int)), "alloc contact bins");
         CK(cudaMemcpy(S->scene_nb, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice), "copy bins");
         CK(cudaMemcpy(S->scene_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice), "copy bins");
         S->nbins = (int)total;
@@ -265,10 +265,10 @@ ibm_status ct_alloc(ibm_ctx *ctx, CtScratch *S) {
         }
         S->cap_p = 0;
         const int cap_pairs = 32 * ctx->cap_p + 64;
-        CK(cudaMalloc(&S->bin_of, ctx->cap_p * sizeof(int)), "alloc contact lists");
-        CK(cudaMalloc(&S->items, ctx->cap_p * sizeof(int)), "alloc contact lists");
-        CK(cudaMalloc(&S->pairs, 2ll * cap_pairs * sizeof(int)), "alloc contact pairs");
-        CK(cudaMalloc(&S->cnt, sizeof(int)), "alloc contact count");
+        CK(ibm_malloc(&S->bin_of, ctx->cap_p * sizeof(int)), "alloc contact lists");
+        CK(ibm_malloc(&S->items, ctx->cap_p * sizeof(int)), "alloc contact lists");
+        CK(ibm_malloc(&S->pairs, 2ll * cap_pairs * sizeof(int)), "alloc contact pairs");
+        CK(ibm_malloc(&S->cnt, sizeof(int)), "alloc contact count");
         S->cap_pairs = cap_pairs;
         S->cap_p = ctx->cap_p;
     }
@@ -277,7 +277,7 @@ ibm_status ct_alloc(ibm_ctx *ctx, CtScratch *S) {
         if (S->bits) cudaFree(S->bits);
         S->bits = nullptr;
         S->words = 0;
-        CK(cudaMalloc(&S->bits, words * sizeof(unsigned)), "alloc marker bitmap");
+        CK(ibm_malloc(&S->bits, words * sizeof(unsigned)), "alloc marker bitmap");
         S->words = words;
     }
     return IBM_OK;

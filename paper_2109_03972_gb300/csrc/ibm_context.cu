@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -10,6 +11,24 @@
 #include <string>
 
 #include "ibm_internal.h"
+
+// Allocation-failure injection (ibm_debug_fail_allocation): the n-th device
+// allocation after the call fails as if the device were out of memory.
+static std::atomic<long long> g_fail_countdown{0};
+
+cudaError_t ibm_dev_malloc(void **p, size_t bytes) {
+    long long c = g_fail_countdown.load();
+    while (c > 0) {
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) {
+            if (c == 1) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
 
 ibm_status ibm_fail(ibm_ctx *ctx, ibm_status s, const std::string &msg) {
     if (ctx) ctx->last_error = msg;
@@ -46,6 +65,10 @@ ibm_status ibm_check_err_word(ibm_ctx *ctx) {
                         "rho_p == rho_f: the rigid-body Newton-Euler form is singular");
     if (e & IBM_EBIT_TIMEOUT) return ibm_fail(ctx, IBM_ERR_TIMEOUT, "a device-side wait timed out");
     if (e & IBM_EBIT_OVERFLOW) return ibm_fail(ctx, IBM_ERR_CAPACITY, "internal scratch capacity exceeded");
+    if (e & IBM_EBIT_FIXEDPOINT)
+        return ibm_fail(ctx, IBM_ERR_CAPACITY,
+                        "deterministic spreading left its fixed-point range (particles overlap far more than "
+                        "the range allows); the velocity field of this step is not valid");
     return ibm_fail(ctx, IBM_ERR_CUDA, "internal device error");
 }
 
@@ -54,7 +77,7 @@ static ibm_status dev_alloc(ibm_ctx *ctx, T **p, size_t n) {
     if (*p) cudaFree(*p);
     *p = nullptr;
     if (n == 0) n = 1;
-    return ibm_cuda_check(ctx, cudaMalloc((void **)p, n * sizeof(T)), "cudaMalloc");
+    return ibm_cuda_check(ctx, ibm_malloc((void **)p, n * sizeof(T)), "cudaMalloc");
 }
 
 static const int kProfPairs = 512;
@@ -97,7 +120,7 @@ static void free_all(ibm_ctx *ctx) {
                     ctx->tmpl_of_nl, ctx->FD, ctx->TD, ctx->Fout, ctx->Tout, ctx->x_new,
                     ctx->u_new, ctx->om_new, ctx->slip_acc, ctx->ebuf, ctx->e_hist, ctx->cbuf, ctx->fb_cm, ctx->fb_bits,
                     ctx->cell_off_d, ctx->fb_own, ctx->mf_seg, ctx->mf_cells, ctx->mf_part, ctx->mf_out, ctx->mf_ptr,
-                    ctx->in_ptr, ctx->in_buf,
+                    ctx->in_ptr, ctx->in_buf, ctx->uptr_d, ctx->fptr_d,
                     ctx->gu_hist, ctx->gmk, ctx->err_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -254,7 +277,10 @@ ibm_status ibm_set_particles(ibm_ctx *ctx, int n_p, const double *x_p, const dou
         else CK(cudaMemsetAsync(ctx->scene, 0, (size_t)n_p * sizeof(int32_t), ctx->stream), "zero scene");
     }
     ibm_status s = launch_setup_particles(ctx);   // validation + marker counts + offsets
-    if (s != IBM_OK) return s;
+    if (s != IBM_OK) {
+        ctx->n_p = 0;   // no step may run on a half-prepared particle set
+        return s;
+    }
     s = ibm_check_err_word(ctx);
     if (s != IBM_OK) {
         ctx->n_p = 0;
@@ -276,7 +302,7 @@ static ibm_status forcing_body(ibm_ctx *ctx, void *const *u_ptrs, double tau, vo
         ctx->u0_saved.resize(ctx->cfg.n_scenes, nullptr);
         for (int s = 0; s < ctx->cfg.n_scenes; ++s) {
             const size_t n = 3ull * ctx->dims_h[3 * s] * ctx->dims_h[3 * s + 1] * ctx->dims_h[3 * s + 2];
-            if (!ctx->u0_saved[s]) CK(cudaMalloc(&ctx->u0_saved[s], n * esz), "alloc u0 copy");
+            if (!ctx->u0_saved[s]) CK(ibm_malloc(&ctx->u0_saved[s], n * esz), "alloc u0 copy");
             CK(cudaMemcpyAsync(ctx->u0_saved[s], u_ptrs[s], n * esz, cudaMemcpyDeviceToDevice, ctx->stream),
                "save u0");
         }
@@ -323,7 +349,8 @@ static void graph_key(const ibm_ctx *ctx, void *const *u_ptrs, double tau, void 
                           ctx->uptr_d, ctx->fptr_d, ctx->err_d, ctx->fb_cm, ctx->fb_bits, ctx->cell_off_d,
                           ctx->fb_own};
     for (const void *b : bufs) key.push_back((uintptr_t)b);
-    const long long sizes[] = {ctx->n_p, ctx->n_markers, ctx->max_nl, ctx->cap_p, ctx->tmpl_used, ctx->tuned_tpb};
+    const long long sizes[] = {ctx->n_p, ctx->n_markers, ctx->max_nl, ctx->cap_p, ctx->tmpl_used, ctx->tuned_tpb,
+                               ctx->wait_limit};
     for (long long v : sizes) key.push_back((uintptr_t)v);
     if (ctx->cfg.spread_mode != IBM_SPREAD_PLAIN) cluster_graph_key(ctx, key);
     contact_graph_key(ctx, key);
@@ -448,7 +475,7 @@ ibm_status ibm_marker_bases(ibm_ctx *ctx, int64_t *base_out, int64_t *n_markers)
     *n_markers = ctx->n_markers;
     if (!base_out || ctx->n_markers == 0) return IBM_OK;
     int64_t *dev = nullptr;
-    CK(cudaMalloc(&dev, 3 * (size_t)ctx->n_markers * sizeof(int64_t)), "alloc bases");
+    CK(ibm_malloc(&dev, 3 * (size_t)ctx->n_markers * sizeof(int64_t)), "alloc bases");
     ibm_status s = launch_pinfo(ctx);
     if (s == IBM_OK) s = launch_marker_bases(ctx, dev);
     if (s == IBM_OK)
@@ -490,6 +517,19 @@ ibm_status ibm_particle_clusters(ibm_ctx *ctx, int32_t *cluster_of, int32_t *pat
     ibm_status s = ibm_check_err_word(ctx);
     if (s != IBM_OK) return s;
     return cluster_membership(ctx, cluster_of, path_of, n_clusters);
+}
+
+ibm_status ibm_set_wait_limit(ibm_ctx *ctx, int64_t iterations) {
+    if (!ctx) return IBM_ERR_INVALID_ARG;
+    if (iterations < 0 || iterations > INT32_MAX) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "wait limit out of range");
+    ctx->wait_limit = (int)iterations;
+    return IBM_OK;
+}
+
+ibm_status ibm_debug_fail_allocation(int64_t n) {
+    if (n < 0) return IBM_ERR_INVALID_ARG;
+    g_fail_countdown.store(n);
+    return IBM_OK;
 }
 
 }  // extern "C"

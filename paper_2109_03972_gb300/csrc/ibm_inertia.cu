@@ -269,12 +269,12 @@ extern "C" ibm_status ibm_particle_inertia(ibm_ctx *ctx, void *const *u_ptrs, do
     // particle records (centres in grid units, radii) of the current particles
     ibm_status st = launch_pinfo(ctx);
     if (st != IBM_OK) return st;
-    if (!ctx->in_ptr) CK(cudaMalloc(&ctx->in_ptr, ns * sizeof(void *)), "alloc field pointers");
+    if (!ctx->in_ptr) CK(ibm_malloc(&ctx->in_ptr, ns * sizeof(void *)), "alloc field pointers");
     if (ctx->in_cap < ctx->cap_p) {
         if (ctx->in_buf) cudaFree(ctx->in_buf);
         ctx->in_buf = nullptr;
         ctx->in_cap = 0;
-        CK(cudaMalloc(&ctx->in_buf, 7ll * ctx->cap_p * sizeof(double)), "alloc inertia sums");
+        CK(ibm_malloc(&ctx->in_buf, 7ll * ctx->cap_p * sizeof(double)), "alloc inertia sums");
         ctx->in_cap = ctx->cap_p;
     }
     // the device pointer table is refreshed only when the pointers change (a copy

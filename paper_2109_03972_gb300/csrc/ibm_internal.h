@@ -18,6 +18,7 @@ enum : int {
     IBM_EBIT_TIMEOUT = 16,
     IBM_EBIT_OVERFLOW = 32,   // a scratch capacity was exceeded (work skipped)
     IBM_EBIT_INTERNAL = 64,
+    IBM_EBIT_FIXEDPOINT = 128,  // a deterministic-mode cell left its fixed-point range
 };
 
 // Per-particle record derived from the FP64 state at every step (device).
@@ -137,12 +138,24 @@ struct ibm_ctx {
     double prof_ms = 0.0;     // folded-in time of pairs already read
     long long prof_count = 0;
 
+    // bound of the device-side retry loops (lock-free union-find of the
+    // clustering); ibm_set_wait_limit, 0 = the default
+    int wait_limit = 0;
+
     int *err_d = nullptr;
     int *err_h = nullptr;     // pinned
     bool have_step = false;
     int64_t stats[8] = {0};
     std::string last_error;
 };
+
+// Device allocations of the library all go through ibm_malloc, so that a test
+// can make one of them fail on the host (ibm_debug_fail_allocation).
+cudaError_t ibm_dev_malloc(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t ibm_malloc(T **p, size_t bytes) {
+    return ibm_dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
 
 // helpers (ibm_context.cu)
 ibm_status ibm_fail(ibm_ctx *ctx, ibm_status s, const std::string &msg);

@@ -105,10 +105,10 @@ ibm_status mf_prepare(ibm_ctx *ctx) {
     long long *seg = nullptr, *cl = nullptr;
     double *part = nullptr, *out = nullptr;
     void **ptr = nullptr;
-    if (cudaMalloc(&seg, prefix.size() * sizeof(long long)) != cudaSuccess ||
-        cudaMalloc(&cl, cells.size() * sizeof(long long)) != cudaSuccess ||
-        cudaMalloc(&part, std::max(1ll, prefix[n_arr]) * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&out, n_arr * sizeof(double)) != cudaSuccess || cudaMalloc(&ptr, ns * sizeof(void *)) != cudaSuccess) {
+    if (ibm_malloc(&seg, prefix.size() * sizeof(long long)) != cudaSuccess ||
+        ibm_malloc(&cl, cells.size() * sizeof(long long)) != cudaSuccess ||
+        ibm_malloc(&part, std::max(1ll, prefix[n_arr]) * sizeof(double)) != cudaSuccess ||
+        ibm_malloc(&out, n_arr * sizeof(double)) != cudaSuccess || ibm_malloc(&ptr, ns * sizeof(void *)) != cudaSuccess) {
         cudaGetLastError();
         for (void *p : {(void *)seg, (void *)cl, (void *)part, (void *)out, (void *)ptr})
             if (p) cudaFree(p);

@@ -355,12 +355,13 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
 }
 
 // Fixed-point scale of a fallback cluster (deterministic mode): the largest
-// power of two 2^k with (max|u| + 64 Dmax max|e|) 2^k < 2^30, as in the
-// shared-memory kernel.
+// power of two 2^k with (max|u| + 64 Dmax max|e|) 2^k < 2^28, as in the
+// shared-memory kernel (a converted-back cell above 2^28 in magnitude sets
+// IBM_EBIT_FIXEDPOINT).
 __device__ __forceinline__ float fb_scale(const unsigned *cm, int c, float *inv) {
     const float range = __uint_as_float(cm[3 * c]) + 64.f * __uint_as_float(cm[3 * c + 2]) * __uint_as_float(cm[3 * c + 1]);
     int ex = 100;
-    if (range > 0.f) ex = min(100, max(-100, 29 - (int)ceilf(log2f(range))));
+    if (range > 0.f) ex = min(100, max(-100, 27 - (int)ceilf(log2f(range))));
     *inv = ldexpf(1.f, -ex);
     return ldexpf(1.f, ex);
 }
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(kBlock) k_fb_convert(const PInfo *__restrict__
                                                       const float *__restrict__ t32, const int32_t *__restrict__ dims,
                                                       const long long *__restrict__ cell_off, float *const *uf,
                                                       const int *__restrict__ pcl, const unsigned *__restrict__ cm,
-                                                      const unsigned *__restrict__ own, unsigned *clear) {
+                                                      const unsigned *__restrict__ own, unsigned *clear, int *err) {
     const int n_list = *n_list_d;
     for (int k = blockIdx.y; k < n_list; k += gridDim.y) {
         const int p = plist[k];
@@ -431,8 +432,13 @@ __global__ void __launch_bounds__(kBlock) k_fb_convert(const PInfo *__restrict__
                 if (clear) clear[(cell_off[Pp.scene] + idx) >> 5] = 0u;
                 for (int q = 0; q < 3; ++q) {
                     float *c = u + q * g.ncell + idx;
-                    if (TO) *reinterpret_cast<int *>(c) = __float2int_rn(*c * S);
-                    else *c = (float)*reinterpret_cast<const int *>(c) * inv;
+                    if (TO) {
+                        *reinterpret_cast<int *>(c) = __float2int_rn(*c * S);
+                    } else {
+                        const int v = *reinterpret_cast<const int *>(c);
+                        if (abs(v) > (1 << 28)) set_err(err, IBM_EBIT_FIXEDPOINT);
+                        *c = (float)v * inv;
+                    }
                 }
             }
         }
@@ -772,9 +778,19 @@ int blocks_for_particles(int n) { return std::max(1, std::min(n, 152 * 16)); }
 
 ibm_status ensure_field_ptrs(ibm_ctx *ctx, void *const *u_ptrs, void *const *f_out) {
     const int ns = ctx->cfg.n_scenes;
-    if (!ctx->uptr_d) {
-        CK(cudaMalloc(&ctx->uptr_d, ns * sizeof(void *)), "alloc field pointers");
-        CK(cudaMalloc(&ctx->fptr_d, ns * sizeof(void *)), "alloc field pointers");
+    if (!ctx->uptr_d || !ctx->fptr_d) {
+        // both tables or neither: a failed second allocation releases the first
+        void **ud = nullptr, **fd = nullptr;
+        CK(ibm_malloc(&ud, ns * sizeof(void *)), "alloc field pointers");
+        const cudaError_t e = ibm_malloc(&fd, ns * sizeof(void *));
+        if (e != cudaSuccess) {
+            cudaFree(ud);
+            return ibm_cuda_check(ctx, e, "alloc field pointers");
+        }
+        if (ctx->uptr_d) cudaFree(ctx->uptr_d);
+        if (ctx->fptr_d) cudaFree(ctx->fptr_d);
+        ctx->uptr_d = ud;
+        ctx->fptr_d = fd;
         ctx->uptr_h.assign(ns, nullptr);
         ctx->fptr_h.assign(ns, nullptr);
     }
@@ -802,7 +818,7 @@ static ibm_status ensure_ebuf(ibm_ctx *ctx) {
     if (ctx->ebuf_cap < need) {
         if (ctx->ebuf) cudaFree(ctx->ebuf);
         ctx->ebuf = nullptr;
-        CK(cudaMalloc(&ctx->ebuf, need), "alloc marker buffer");
+        CK(ibm_malloc(&ctx->ebuf, need), "alloc marker buffer");
         ctx->ebuf_cap = need;
     }
     return IBM_OK;
@@ -812,7 +828,7 @@ ibm_status launch_setup_particles(ibm_ctx *ctx) {
     const int n = ctx->n_p;
     int *max_d = nullptr;
     long long *tot_d = nullptr;
-    CK(cudaMalloc(&max_d, sizeof(int) + sizeof(long long) * 2), "alloc");
+    CK(ibm_malloc(&max_d, sizeof(int) + sizeof(long long) * 2), "alloc");
     tot_d = reinterpret_cast<long long *>(max_d + 2);
     CK(cudaMemsetAsync(max_d, 0, sizeof(int) + sizeof(long long) * 2, ctx->stream), "memset");
     if (n > 0)
@@ -837,7 +853,7 @@ ibm_status launch_setup_particles(ibm_ctx *ctx) {
     if (maxnl >= ctx->nl_cap) {
         int cap = std::max(maxnl + 1, 2 * ctx->nl_cap);
         int *nd = nullptr;
-        CK(cudaMalloc(&nd, cap * sizeof(int)), "alloc template index");
+        CK(ibm_malloc(&nd, cap * sizeof(int)), "alloc template index");
         ctx->tmpl_of_nl_h.resize(cap, -1);
         CK(cudaMemcpyAsync(nd, ctx->tmpl_of_nl_h.data(), cap * sizeof(int), cudaMemcpyHostToDevice, ctx->stream),
            "copy template index");
@@ -846,7 +862,7 @@ ibm_status launch_setup_particles(ibm_ctx *ctx) {
         ctx->nl_cap = cap;
     }
     int *flag = nullptr;
-    CK(cudaMalloc(&flag, ctx->nl_cap * sizeof(int)), "alloc flags");
+    CK(ibm_malloc(&flag, ctx->nl_cap * sizeof(int)), "alloc flags");
     CK(cudaMemsetAsync(flag, 0, ctx->nl_cap * sizeof(int), ctx->stream), "memset flags");
     k_flag_new_nl<<<grid_for(n, kBlock), kBlock, 0, ctx->stream>>>(n, ctx->nl, ctx->tmpl_of_nl, flag);
     std::vector<int> fl(ctx->nl_cap);
@@ -867,8 +883,12 @@ ibm_status launch_setup_particles(ibm_ctx *ctx) {
             long long cap = std::max(used, 2 * ctx->tmpl_cap);
             double *n64 = nullptr;
             float *n32 = nullptr;
-            CK(cudaMalloc(&n64, 3 * cap * sizeof(double)), "alloc templates");
-            CK(cudaMalloc(&n32, 3 * cap * sizeof(float)), "alloc templates");
+            CK(ibm_malloc(&n64, 3 * cap * sizeof(double)), "alloc templates");
+            const cudaError_t e32 = ibm_malloc(&n32, 3 * cap * sizeof(float));
+            if (e32 != cudaSuccess) {
+                cudaFree(n64);
+                return ibm_cuda_check(ctx, e32, "alloc templates");
+            }
             if (ctx->tmpl_used) {
                 CK(cudaMemcpyAsync(n64, ctx->tmpl64, 3 * ctx->tmpl_used * sizeof(double), cudaMemcpyDeviceToDevice,
                                    ctx->stream), "copy templates");
@@ -884,7 +904,7 @@ ibm_status launch_setup_particles(ibm_ctx *ctx) {
         }
         int *ld = nullptr;
         const int nlst = (int)lst_nl.size();
-        CK(cudaMalloc(&ld, 2 * nlst * sizeof(int)), "alloc list");
+        CK(ibm_malloc(&ld, 2 * nlst * sizeof(int)), "alloc list");
         CK(cudaMemcpyAsync(ld, lst_nl.data(), nlst * sizeof(int), cudaMemcpyHostToDevice, ctx->stream), "copy");
         CK(cudaMemcpyAsync(ld + nlst, lst_off.data(), nlst * sizeof(int), cudaMemcpyHostToDevice, ctx->stream),
            "copy");
@@ -950,24 +970,26 @@ static ibm_status fb_prepare(ibm_ctx *ctx) {
             off += (long long)ctx->dims_h[3 * s] * ctx->dims_h[3 * s + 1] * ctx->dims_h[3 * s + 2];
         }
         const size_t words = (size_t)(off + 31) / 32 + 1;
-        CK(cudaMalloc(&ctx->cell_off_d, offs.size() * sizeof(long long)), "alloc scene offsets");
+        if (ctx->cell_off_d) cudaFree(ctx->cell_off_d);   // left by an earlier failed attempt
+        ctx->cell_off_d = nullptr;
+        CK(ibm_malloc(&ctx->cell_off_d, offs.size() * sizeof(long long)), "alloc scene offsets");
         CK(cudaMemcpy(ctx->cell_off_d, offs.data(), offs.size() * sizeof(long long), cudaMemcpyHostToDevice),
            "copy scene offsets");
-        CK(cudaMalloc(&ctx->fb_bits, words * sizeof(unsigned)), "alloc cell bitmap");
+        CK(ibm_malloc(&ctx->fb_bits, words * sizeof(unsigned)), "alloc cell bitmap");
         CK(cudaMemset(ctx->fb_bits, 0, words * sizeof(unsigned)), "zero cell bitmap");
     }
     if (ctx->fb_cm_cap < ctx->cap_p) {
         if (ctx->fb_cm) cudaFree(ctx->fb_cm);
         ctx->fb_cm = nullptr;
         ctx->fb_cm_cap = 0;
-        CK(cudaMalloc(&ctx->fb_cm, 3 * (size_t)ctx->cap_p * sizeof(unsigned)), "alloc cluster maxima");
+        CK(ibm_malloc(&ctx->fb_cm, 3 * (size_t)ctx->cap_p * sizeof(unsigned)), "alloc cluster maxima");
         ctx->fb_cm_cap = ctx->cap_p;
     }
     if (ctx->fb_own_cap < ctx->n_markers) {
         if (ctx->fb_own) cudaFree(ctx->fb_own);
         ctx->fb_own = nullptr;
         ctx->fb_own_cap = 0;
-        CK(cudaMalloc(&ctx->fb_own, (size_t)ctx->n_markers * sizeof(unsigned)), "alloc owned-cell masks");
+        CK(ibm_malloc(&ctx->fb_own, (size_t)ctx->n_markers * sizeof(unsigned)), "alloc owned-cell masks");
         ctx->fb_own_cap = ctx->n_markers;
     }
     return IBM_OK;
@@ -978,18 +1000,26 @@ static ibm_status fb_prepare(ibm_ctx *ctx) {
 // deterministic fixed point of the cluster (interpolate with the maxima,
 // convert the cells claimed by k_fb_claim, integer spreading, convert back);
 // first: the first iteration of the step, whose conversion clears the bitmap.
-template <typename T>
-static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
-                                  bool with_f, const int *pcl = nullptr, bool first = false) {
-    const dim3 grid = chunk_grid(ctx, n_list, n_list_d != nullptr);
+// Per-(particle, chunk) load sums of the plain kernels for a list of n_list.
+static ibm_status ensure_cbuf(ibm_ctx *ctx, int n_list, bool count_on_device) {
+    const dim3 grid = chunk_grid(ctx, n_list, count_on_device);
     const size_t need = (size_t)std::max(1, n_list) * grid.x * 6 * sizeof(double);
     if (ctx->cbuf_cap < need) {
         if (ctx->cbuf) cudaFree(ctx->cbuf);
         ctx->cbuf = nullptr;
         ctx->cbuf_cap = 0;
-        CK(cudaMalloc(&ctx->cbuf, need), "alloc chunk sums");
+        CK(ibm_malloc(&ctx->cbuf, need), "alloc chunk sums");
         ctx->cbuf_cap = need;
     }
+    return IBM_OK;
+}
+
+template <typename T>
+static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
+                                  bool with_f, const int *pcl = nullptr, bool first = false) {
+    const dim3 grid = chunk_grid(ctx, n_list, n_list_d != nullptr);
+    ibm_status cs = ensure_cbuf(ctx, n_list, n_list_d != nullptr);
+    if (cs != IBM_OK) return cs;
     T *const *uf = reinterpret_cast<T *const *>(ctx->uptr_d);
     T *const *ff = with_f ? reinterpret_cast<T *const *>(ctx->fptr_d) : nullptr;
     if (pcl && sizeof(T) == 4) {
@@ -1001,14 +1031,14 @@ static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, co
             reinterpret_cast<float *>(ctx->ebuf), ctx->cbuf, pcl, ctx->fb_cm);
         k_fb_convert<true><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list_d, ctx->tmpl64, ctx->tmpl32,
                                                              ctx->dims_d, ctx->cell_off_d, u32, pcl, ctx->fb_cm,
-                                                             ctx->fb_own, first ? ctx->fb_bits : nullptr);
+                                                             ctx->fb_own, first ? ctx->fb_bits : nullptr, ctx->err_d);
         k_plain_spread<float, true><<<grid, kBlock, 0, ctx->stream>>>(
             ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->dims_d,
             reinterpret_cast<const float *>(ctx->ebuf), 1.f, u32, f32, (float)(1.0 / tau), ctx->cbuf, ctx->FD,
             ctx->TD, pcl, ctx->fb_cm);
         k_fb_convert<false><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list_d, ctx->tmpl64, ctx->tmpl32,
                                                               ctx->dims_d, ctx->cell_off_d, u32, pcl, ctx->fb_cm,
-                                                              ctx->fb_own, nullptr);
+                                                              ctx->fb_own, nullptr, ctx->err_d);
         ctx->launches += 4;
         return IBM_OK;
     }
@@ -1041,7 +1071,11 @@ static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, co
 ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
                                 bool with_f, int n_it, const int *pcl) {
     if (pcl && n_it > 0) {
-        const ibm_status st = fb_prepare(ctx);
+        // every allocation of the iterations happens before the claim: the claim
+        // leaves cell bits set that only the first conversion clears, so no
+        // error may return between the two
+        ibm_status st = fb_prepare(ctx);
+        if (st == IBM_OK) st = ensure_cbuf(ctx, n_list, n_list_d != nullptr);
         if (st != IBM_OK) return st;
         k_fb_claim<<<chunk_grid(ctx, n_list, true), kBlock, 0, ctx->stream>>>(
             ctx->pinfo, plist, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->dims_d, ctx->cell_off_d, ctx->fb_bits,
@@ -1120,16 +1154,16 @@ static ibm_status backward_impl(ibm_ctx *ctx, void *const *grad_u_out, void *con
         if (ctx->gu_hist) cudaFree(ctx->gu_hist);
         if (ctx->gmk) cudaFree(ctx->gmk);
         ctx->e_hist = ctx->gu_hist = ctx->gmk = nullptr;
-        CK(cudaMalloc(&ctx->e_hist, 3 * need * sizeof(double)), "alloc adjoint history");
-        CK(cudaMalloc(&ctx->gu_hist, 9 * need * sizeof(double)), "alloc adjoint history");
-        CK(cudaMalloc(&ctx->gmk, 6 * nm * sizeof(double)), "alloc adjoint accumulators");
+        CK(ibm_malloc(&ctx->e_hist, 3 * need * sizeof(double)), "alloc adjoint history");
+        CK(ibm_malloc(&ctx->gu_hist, 9 * need * sizeof(double)), "alloc adjoint history");
+        CK(ibm_malloc(&ctx->gmk, 6 * nm * sizeof(double)), "alloc adjoint accumulators");
         ctx->hist_cap = need;
     }
     ctx->bw_work.resize(ns, nullptr);
     std::vector<void *> work(ns);
     for (int s = 0; s < ns; ++s) {
         const size_t n = 3ull * ctx->dims_h[3 * s] * ctx->dims_h[3 * s + 1] * ctx->dims_h[3 * s + 2];
-        if (!ctx->bw_work[s]) CK(cudaMalloc(&ctx->bw_work[s], n * sizeof(T)), "alloc adjoint work field");
+        if (!ctx->bw_work[s]) CK(ibm_malloc(&ctx->bw_work[s], n * sizeof(T)), "alloc adjoint work field");
         CK(cudaMemcpyAsync(ctx->bw_work[s], ctx->u0_saved[s], n * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream),
            "copy u0");
         work[s] = ctx->bw_work[s];

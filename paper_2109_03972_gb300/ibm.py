@@ -72,6 +72,10 @@ def load_library(path: str = LIB_PATH):
     L.ibm_step_stats.argtypes = [vp, vp]
     L.ibm_particle_clusters.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
     L.ibm_particle_clusters.restype = i
+    L.ibm_set_wait_limit.argtypes = [vp, ctypes.c_int64]
+    L.ibm_set_wait_limit.restype = i
+    L.ibm_debug_fail_allocation.argtypes = [ctypes.c_int64]
+    L.ibm_debug_fail_allocation.restype = i
     L.ibm_kernel_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i]
     L.ibm_status_string.argtypes = [i]
     L.ibm_status_string.restype = ctypes.c_char_p
@@ -248,6 +252,10 @@ class Context:
         self._check(self.L.ibm_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n), int(reset)))
         return ms.value, n.value
 
+    def set_wait_limit(self, iterations=0):
+        """Bound of the device-side retry loops of the cluster modes (0 = default)."""
+        self._check(self.L.ibm_set_wait_limit(self.h, int(iterations)))
+
     def particle_clusters(self):
         """Each particle's cluster and its cluster's IBM_PATH_* bits in the last step."""
         n = self.n_p
@@ -263,6 +271,13 @@ class Context:
         keys = ("markers", "clusters", "clusters_smem", "markers_fallback", "largest_cluster_cells",
                 "touched_cells", "launches", "threads_per_block", "clusters_one_component", "candidate_pairs")
         return dict(zip(keys, (int(v) for v in out)))
+
+
+def debug_fail_allocation(n):
+    """Test hook: the n-th device allocation of the library from now on fails (0 = off)."""
+    st = load_library().ibm_debug_fail_allocation(int(n))
+    if st != 0:
+        raise IBMError(st, "ibm_debug_fail_allocation")
 
 
 class IBMForcing(torch.autograd.Function):
