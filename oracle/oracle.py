@@ -17,6 +17,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "ibm_oracle.c")
+SRC_COLLISION = os.path.join(HERE, "ibm_collision_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -30,11 +31,12 @@ _p = ctypes.c_void_p
 def build(force: bool = False) -> str:
     """Compile liboracle.so if missing or older than its source."""
     with _lock:
-        if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        newest = max(os.path.getmtime(SRC), os.path.getmtime(SRC_COLLISION))
+        if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
             tmp = LIB + f".{os.getpid()}.tmp"
             cc = os.environ.get("CC", "cc")
             subprocess.check_call([cc, "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-                                   "-o", tmp, SRC, "-lm"])
+                                   "-o", tmp, SRC, SRC_COLLISION, "-lm"])
             os.replace(tmp, LIB)
     return LIB
 
@@ -71,6 +73,15 @@ def lib():
         L.ora_particle_inertia.argtypes = [_l, _l, _l, _d, _l, _p, _p, _p, _p, _p, _p]
         L.ora_newton_euler.restype = None
         L.ora_newton_euler.argtypes = [_l, _p, _p, _p, _p, _p, _d, _p, _d, _p, _p]
+        L.orc_tstar.restype, L.orc_tstar.argtypes = _d, [_d]
+        L.orc_kn.restype, L.orc_kn.argtypes = _d, [_p, _d, _d, _d, _d, _d, _d, _d, _d]
+        L.orc_pair.restype = _d
+        L.orc_pair.argtypes = [_p, _p, _p, _p, _p, _p, _d, _d, _d, _d, _p, _d, _p, _p]
+        L.orc_collision_forces.restype = None
+        L.orc_collision_forces.argtypes = [_l, _p, _p, _p, _p, _p, _p, _p, _p, _l, _p, _p, _p, _p, _p, _p]
+        L.orc_particle_substeps.restype = _i
+        L.orc_particle_substeps.argtypes = [_l, _p, _p, _p, _d, _i, _p, _p, _p, _p, _p, _p, _p, _l, _p, _p, _p,
+                                            _p, _p]
         L.ora_backward.restype = _i
         L.ora_backward.argtypes = [_i, _l, _l, _l, _d, _i, _l, _p, _p, _p, _p,
                                    _p, _p, _p, _p, _p, _p]
@@ -252,3 +263,87 @@ def particle_inertia(u, x_p, d_p, h=1.0):
 def splitmix64(x: int) -> int:
     """SplitMix64 output for state x (the counter-based coin of the pair choice)."""
     return int(lib().ora_splitmix64_out(int(x) & (2**64 - 1)))
+
+
+# ---------------------------------------------------------------- collisions
+
+COLLISION_DEFAULTS = dict(rho_f=1.0, nu_f=0.01, e_dry=0.97, mu_s=0.4, mu_k=0.3, nu_poisson=0.3, t_c=0.1,
+                          st_crit=5.0, eps_sep=None, zeta_min=None, lub_c=5.5, g=(0.0, 0.0, 0.0))
+
+
+def collision_params(h=1.0, **kw):
+    """Parameter vector of the collision oracle (ibm_collision_oracle.c):
+    eps_sep defaults to 1.5 h, zeta_min to 0.01 h."""
+    c = {**COLLISION_DEFAULTS, **kw}
+    eps = 1.5 * h if c["eps_sep"] is None else c["eps_sep"]
+    zmin = 0.01 * h if c["zeta_min"] is None else c["zeta_min"]
+    g = list(c["g"])
+    return np.array([c["rho_f"], c["nu_f"], c["e_dry"], c["mu_s"], c["mu_k"], c["nu_poisson"], c["t_c"],
+                     c["st_crit"], eps, zmin, c["lub_c"], g[0], g[1], g[2], h], dtype=np.float64)
+
+
+def collision_tstar(t_c):
+    return float(lib().orc_tstar(float(t_c)))
+
+
+def pair_force(P, dv, u_s, u_o, w_s, w_o, d_s, d_o, rho_s, rho_o, zt=(0.0, 0.0, 0.0), uin=-1.0):
+    """Force and torque on `self` from one pair (dv = x_other - x_self); returns (F, T, zeta_n)."""
+    F, T = np.zeros(3), np.zeros(3)
+    args = [_f64(a, (3,)) for a in (dv, u_s, u_o, w_s, w_o)]
+    zt = _f64(zt, (3,))
+    z = lib().orc_pair(_ptr(P), *[_ptr(a) for a in args], float(d_s), float(d_o), float(rho_s), float(rho_o),
+                       _ptr(zt), float(uin), _ptr(F), _ptr(T))
+    return F, T, z
+
+
+class PairHistory:
+    """Contact history of the oracle: canonical pairs p < q with the tangential
+    spring (in p's frame) and the impact speed."""
+
+    def __init__(self, cap=100000):
+        self.cap = cap
+        self.n = ctypes.c_long(0)
+        self.p = np.zeros(cap, dtype=np.int64)
+        self.q = np.zeros(cap, dtype=np.int64)
+        self.z = np.zeros((cap, 3))
+        self.u = np.zeros(cap)
+
+    def arrays(self):
+        return self.p, self.q, self.z, self.u
+
+
+def _scene_arrays(dims, scene, n):
+    dims = np.ascontiguousarray(np.asarray(dims, dtype=np.int64).reshape(-1, 3))
+    sc = np.zeros(n, dtype=np.int32) if scene is None else np.ascontiguousarray(scene, dtype=np.int32)
+    return dims, sc
+
+
+def collision_forces(P, dims, x, u, om, d, rho, hist=None, scene=None):
+    """F_c,p and T_c,p of every particle (Eq. f_int), history as given."""
+    x, u, om = (_f64(a, (-1, 3)) for a in (x, u, om))
+    d, rho = _f64(d, (-1,)), _f64(rho, (-1,))
+    n = d.size
+    dims, sc = _scene_arrays(dims, scene, n)
+    hist = hist or PairHistory(1)
+    Fc, Tc = np.zeros((n, 3)), np.zeros((n, 3))
+    lib().orc_collision_forces(n, _ptr(dims), _ptr(sc), _ptr(P), _ptr(x), _ptr(u), _ptr(om), _ptr(d), _ptr(rho),
+                               hist.n.value, *[_ptr(a) for a in hist.arrays()], _ptr(Fc), _ptr(Tc))
+    return Fc, Tc
+
+
+def particle_substeps(P, dims, x, u, om, d, rho, dt, n_sub=15, F_h=None, T_h=None, hist=None, scene=None):
+    """RK3 predictor-corrector sub-steps of Sec. 2.2.10 (oracle); returns
+    (x, u, om, hist) with the state advanced by dt."""
+    x, u, om = (_f64(a, (-1, 3)).copy() for a in (x, u, om))
+    d, rho = _f64(d, (-1,)), _f64(rho, (-1,))
+    n = d.size
+    dims, sc = _scene_arrays(dims, scene, n)
+    hist = hist or PairHistory()
+    Fh = None if F_h is None else _f64(F_h, (-1, 3))
+    Th = None if T_h is None else _f64(T_h, (-1, 3))
+    rc = lib().orc_particle_substeps(n, _ptr(dims), _ptr(sc), _ptr(P), float(dt), int(n_sub), _ptr(Fh), _ptr(Th),
+                                     _ptr(x), _ptr(u), _ptr(om), _ptr(d), _ptr(rho), hist.cap,
+                                     ctypes.byref(hist.n), *[_ptr(a) for a in hist.arrays()])
+    if rc != 0:
+        raise MemoryError("oracle collision history full")
+    return x, u, om, hist
