@@ -248,6 +248,75 @@ ibm_status ibm_disabled_markers(ibm_ctx *ctx, uint32_t *bits_out, int64_t *n_dis
 ibm_status ibm_backward(ibm_ctx *ctx, void *const *grad_u_out, void *const *grad_u_in,
                         double *gU, double *gOmega, double *gX);
 
+/* Parameters of the collision models (Sec. 2.2.6-2.2.8) for
+ * ibm_particle_substeps and ibm_collision_forces, in the length and time units
+ * of h and the particle state.  0 in eps_sep, zeta_min, lub_c or pair_margin
+ * takes the default given. */
+typedef struct {
+    double rho_f;        /* fluid density (> 0)                                */
+    double nu_f;         /* kinematic viscosity (>= 0; 0 turns lubrication off)*/
+    double e_dry;        /* dry restitution coefficient, 0 < e_dry < 1         */
+    double mu_s, mu_k;   /* static and kinetic friction coefficients           */
+    double nu_poisson;   /* Poisson's ratio of the particle material           */
+    double t_c;          /* collision time T_c (the paper uses 10 dt)          */
+    double st_crit;      /* critical Stokes number (the paper uses 5)          */
+    double eps_sep;      /* threshold separation; 0: 1.5 h (3-point), 2 h      */
+    double zeta_min;     /* floor of the lubrication gap; 0: 0.01 h            */
+    double lub_c;        /* C of the erf blend; 0: 5.5 (3-point), 4 (4-point)  */
+    double g[3];         /* gravity                                            */
+    double pair_margin;  /* neighbour-list margin beyond eps_sep; 0: 1.5 h     */
+} ibm_collision_params;
+
+/* Advance the particle state of ctx (x_p, u_p, w_p of ibm_set_particles, with
+ * rho_p given) by dt under the collision models of Sec. 2.2.6-2.2.8 and
+ * constant hydrodynamic loads, in n_sub sub-steps of dt/n_sub, each the
+ * three-stage predictor-corrector Runge-Kutta update of Sec. 2.2.10 (the paper
+ * uses 15 sub-steps).  Collision force on p (Eq. f_int), summed over its pairs
+ * in the same scene, each with n from p to q (minimum image) and surface gap
+ * zeta_n: for 0 < zeta_n < eps_sep the lubrication force
+ * -6 pi rho_f nu_f R_eff^2 psi / max(zeta_min, zeta_n) g_n, psi =
+ * erf(6 - C max(zeta_min, zeta_n)/h)/2 + 1/2; for zeta_n <= 0 the Hertz
+ * contact -k_n |zeta_n|^{3/2} n - d_n g_n plus the tangential spring-dashpot
+ * force capped by mu |F_n| (stick/slip), with torque R_p,cp n x F_t.  Stiffness
+ * and damping follow the adaptive collision time model; where the paper cites
+ * closed forms it does not print, this library's reading is used: k_n =
+ * m_eff/sqrt(u_in t*^5) with t* = T_c (4/5)^{2/5}/(2 I_H), the stiffness for
+ * which an undamped Hertz impact at speed u_in lasts T_c (I_H = sqrt(pi)
+ * Gamma(7/5)/Gamma(9/10)), below the critical impact speed of St_crit
+ * max(k_n(u_in,crit), k_n,grav); d_n = -2 m_eff ln(e_dry)/T_c; k_t =
+ * 2(1-nu)/(2-nu) k_n.  No walls (periodic boxes).
+ * F_h, T_h: the hydrodynamic force and torque on each particle ([n_p][3],
+ * host or device per on_device, held constant over the call; NULL = 0), e.g.
+ * -rho_f times the fluid-side loads of ibm_particle_loads.  The state is
+ * updated in place (read it with ibm_particle_state; the next forcing step
+ * uses it); the tangential springs and impact speeds of the pairs in contact
+ * are kept for the next call while the particle count stays the same.
+ * FP64; every sum in a fixed order (bit-reproducible).  Synchronises.
+ * Errors: INVALID_ARG (parameters, dt <= 0, n_sub < 1, densities not
+ * positive), CAPACITY (a particle moved more than half of pair_margin in the
+ * call, so that pairs could have been missed), OOM, CUDA. */
+ibm_status ibm_particle_substeps(ibm_ctx *ctx, const ibm_collision_params *prm, double dt, int n_sub,
+                                 const double *F_h, const double *T_h, int on_device);
+
+/* Collision force F_c,p and torque T_c,p of every particle (Eq. f_int) at the
+ * current state with the kept contact history ([n_p][3] each, host or device;
+ * either may be NULL).  Synchronises for host outputs.
+ * Errors: INVALID_ARG, CAPACITY, OOM, CUDA. */
+ibm_status ibm_collision_forces(ibm_ctx *ctx, const ibm_collision_params *prm, double *F_c, double *T_c,
+                                int on_device);
+
+/* Current particle state of ctx (x_p, u_p, w_p, [n_p][3] each, host or device;
+ * any may be NULL).  Synchronises for host outputs.  Errors: CUDA. */
+ibm_status ibm_particle_state(ibm_ctx *ctx, double *x_p, double *u_p, double *omega_p, int on_device);
+
+/* Contact history kept by the last ibm_particle_substeps: the pairs (p, q),
+ * p < q, in contact at its end, ordered by p, with the tangential spring
+ * (in p's frame, double [n][3]) and the impact speed.  HOST arrays of
+ * *n_pairs entries; pass NULL arrays to query the count.  Synchronises.
+ * Errors: INVALID_ARG, CUDA. */
+ibm_status ibm_contact_history(ibm_ctx *ctx, int64_t *n_pairs, int32_t *p, int32_t *q, double *zeta_t,
+                               double *u_in);
+
 /* Diagnostics.  Stencil base cell of every marker, in particle-then-l order,
  * as the active precision path computes it: floor(X_l/h) per axis
  * (floor(X_l/h - 1/2) for kernel_width 4), NOT wrapped

@@ -64,6 +64,9 @@ ibm_status ibm_check_err_word(ibm_ctx *ctx) {
         return ibm_fail(ctx, IBM_ERR_INVALID_ARG,
                         "rho_p == rho_f: the rigid-body Newton-Euler form is singular");
     if (e & IBM_EBIT_TIMEOUT) return ibm_fail(ctx, IBM_ERR_TIMEOUT, "a device-side wait timed out");
+    if (e & IBM_EBIT_MASS)
+        return ibm_fail(ctx, IBM_ERR_INVALID_ARG,
+                        "particle sub-steps need positive densities (rho_p given to ibm_set_particles)");
     if (e & IBM_EBIT_OVERFLOW) return ibm_fail(ctx, IBM_ERR_CAPACITY, "internal scratch capacity exceeded");
     if (e & IBM_EBIT_FIXEDPOINT)
         return ibm_fail(ctx, IBM_ERR_CAPACITY,
@@ -130,6 +133,7 @@ static void free_all(ibm_ctx *ctx) {
         if (p) cudaFree(p);
     cluster_free(ctx);
     contact_free(ctx);
+    collision_free(ctx);
     if (ctx->err_h) cudaFreeHost(ctx->err_h);
 }
 

@@ -19,6 +19,7 @@ enum : int {
     IBM_EBIT_OVERFLOW = 32,   // a scratch capacity was exceeded (work skipped)
     IBM_EBIT_INTERNAL = 64,
     IBM_EBIT_FIXEDPOINT = 128,  // a deterministic-mode cell left its fixed-point range
+    IBM_EBIT_MASS = 256,        // a particle without positive mass (rho_p) in the particle sub-steps
 };
 
 // Per-particle record derived from the FP64 state at every step (device).
@@ -118,6 +119,9 @@ struct ibm_ctx {
     // cluster-path scratch (see ibm_cluster.cu)
     void *cl = nullptr;
 
+    // collision models and particle sub-steps (ibm_collision.cu)
+    void *col = nullptr;
+
     // marker exclusion near contact (ibm_contact.cu, Sec. 2.2.6)
     void *ct = nullptr;
     int ct_enable = 0;
@@ -172,7 +176,6 @@ ibm_status launch_setup_particles(ibm_ctx *ctx);      // nl, validation
 ibm_status launch_templates(ibm_ctx *ctx, int lo_nl, int hi_nl);
 ibm_status launch_pinfo(ibm_ctx *ctx);
 ibm_status launch_marker_bases(ibm_ctx *ctx, int64_t *base_d);
-ibm_status launch_scan_int(ibm_ctx *ctx, const int *in, int *out_excl, int n, long long *total_d);
 
 ibm_status ensure_field_ptrs(ibm_ctx *ctx, void *const *u_ptrs, void *const *f_out);
 // marker exclusion near contact (ibm_contact.cu): per-step bitmap of the
@@ -182,6 +185,8 @@ ibm_status contact_exclusion(ibm_ctx *ctx);
 const unsigned *contact_bits(const ibm_ctx *ctx);
 void contact_graph_key(const ibm_ctx *ctx, std::vector<uintptr_t> &key);
 void contact_free(ibm_ctx *ctx);
+// collision models and particle sub-steps (ibm_collision.cu): teardown
+void collision_free(ibm_ctx *ctx);
 
 ibm_status plain_iterations_f32(ibm_ctx *ctx, const int *plist, int n_list, const int *n_list_d, double tau,
                                 bool with_f, int n_it, const int *pcl);

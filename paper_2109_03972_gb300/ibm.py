@@ -45,6 +45,41 @@ class _Config(ctypes.Structure):
                 ("profile", ctypes.c_int), ("use_graph", ctypes.c_int)]
 
 
+class _CollisionParams(ctypes.Structure):
+    _fields_ = [("rho_f", ctypes.c_double), ("nu_f", ctypes.c_double), ("e_dry", ctypes.c_double),
+                ("mu_s", ctypes.c_double), ("mu_k", ctypes.c_double), ("nu_poisson", ctypes.c_double),
+                ("t_c", ctypes.c_double), ("st_crit", ctypes.c_double), ("eps_sep", ctypes.c_double),
+                ("zeta_min", ctypes.c_double), ("lub_c", ctypes.c_double), ("g", ctypes.c_double * 3),
+                ("pair_margin", ctypes.c_double)]
+
+
+@dataclass
+class CollisionParams:
+    """Collision models of Sec. 2.2.6-2.2.8 (0 in eps_sep, zeta_min, lub_c,
+    pair_margin takes the library's default)."""
+    rho_f: float = 1.0
+    nu_f: float = 0.01
+    e_dry: float = 0.97
+    mu_s: float = 0.4
+    mu_k: float = 0.3
+    nu_poisson: float = 0.3
+    t_c: float = 0.1
+    st_crit: float = 5.0
+    eps_sep: float = 0.0
+    zeta_min: float = 0.0
+    lub_c: float = 0.0
+    g: tuple = (0.0, 0.0, 0.0)
+    pair_margin: float = 0.0
+
+    def _c(self):
+        c = _CollisionParams()
+        for k in ("rho_f", "nu_f", "e_dry", "mu_s", "mu_k", "nu_poisson", "t_c", "st_crit", "eps_sep",
+                  "zeta_min", "lub_c", "pair_margin"):
+            setattr(c, k, float(getattr(self, k)))
+        c.g = (ctypes.c_double * 3)(*[float(v) for v in self.g])
+        return c
+
+
 _lib = None
 
 
@@ -72,6 +107,14 @@ def load_library(path: str = LIB_PATH):
     L.ibm_step_stats.argtypes = [vp, vp]
     L.ibm_particle_clusters.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
     L.ibm_particle_clusters.restype = i
+    L.ibm_particle_substeps.argtypes = [vp, ctypes.POINTER(_CollisionParams), d, i, vp, vp, i]
+    L.ibm_particle_substeps.restype = i
+    L.ibm_collision_forces.argtypes = [vp, ctypes.POINTER(_CollisionParams), vp, vp, i]
+    L.ibm_collision_forces.restype = i
+    L.ibm_particle_state.argtypes = [vp, vp, vp, vp, i]
+    L.ibm_particle_state.restype = i
+    L.ibm_contact_history.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), vp, vp, vp, vp]
+    L.ibm_contact_history.restype = i
     L.ibm_set_wait_limit.argtypes = [vp, ctypes.c_int64]
     L.ibm_set_wait_limit.restype = i
     L.ibm_debug_fail_allocation.argtypes = [ctypes.c_int64]
@@ -251,6 +294,40 @@ class Context:
         ms, n = ctypes.c_double(), ctypes.c_int64()
         self._check(self.L.ibm_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n), int(reset)))
         return ms.value, n.value
+
+    def particle_substeps(self, prm, dt, n_sub=15, F_h=None, T_h=None):
+        """Advance the particle state by dt under the collision models and the
+        constant hydrodynamic loads F_h, T_h (numpy [n_p, 3] or device tensors)."""
+        on_dev = isinstance(F_h, torch.Tensor) or isinstance(T_h, torch.Tensor)
+        conv = (lambda a: a.contiguous()) if on_dev else (
+            lambda a: np.ascontiguousarray(a, dtype=np.float64))
+        Fh = None if F_h is None else conv(F_h)
+        Th = None if T_h is None else conv(T_h)
+        c = prm._c()
+        self._check(self.L.ibm_particle_substeps(self.h, ctypes.byref(c), float(dt), int(n_sub), _ptr(Fh),
+                                                 _ptr(Th), int(on_dev)))
+
+    def collision_forces(self, prm):
+        n = self.n_p
+        F, T = np.zeros((n, 3)), np.zeros((n, 3))
+        c = prm._c()
+        self._check(self.L.ibm_collision_forces(self.h, ctypes.byref(c), _ptr(F), _ptr(T), 0))
+        return F, T
+
+    def particle_state(self):
+        n = self.n_p
+        x, u, w = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+        self._check(self.L.ibm_particle_state(self.h, _ptr(x), _ptr(u), _ptr(w), 0))
+        return x, u, w
+
+    def contact_history(self):
+        nc = ctypes.c_int64()
+        self._check(self.L.ibm_contact_history(self.h, ctypes.byref(nc), None, None, None, None))
+        m = int(nc.value)
+        p, q = np.zeros(max(m, 1), dtype=np.int32), np.zeros(max(m, 1), dtype=np.int32)
+        z, u = np.zeros((max(m, 1), 3)), np.zeros(max(m, 1))
+        self._check(self.L.ibm_contact_history(self.h, ctypes.byref(nc), _ptr(p), _ptr(q), _ptr(z), _ptr(u)))
+        return p[:m], q[:m], z[:m], u[:m]
 
     def set_wait_limit(self, iterations=0):
         """Bound of the device-side retry loops of the cluster modes (0 = default)."""
