@@ -185,3 +185,13 @@ def test_missing_densities_are_rejected():
     with pytest.raises(ibm.IBMError) as e:
         ctx.particle_substeps(_gpu_params(), 0.1, 3)
     assert e.value.status == 1
+
+
+def test_larger_dense_box_matches_oracle(oracle_mod):
+    # 400 spheres in a 64^3 box (about 30% solid), one call of 15 sub-steps
+    dims = (64, 64, 64)
+    parts = _packed(dims, 400, 51)
+    got = _run_gpu([dims], parts, None, 0.1, 15, 1)
+    ref = _run_oracle(oracle_mod, [dims], parts, None, 0.1, 15, 1)
+    assert got[3][0].size >= 5
+    _compare(got, ref, parts)
