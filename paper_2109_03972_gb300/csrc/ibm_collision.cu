@@ -79,7 +79,7 @@ struct ColScratch {
     int *nbr = nullptr, *canon = nullptr;       // [cap_e] neighbour, canonical entry of the pair
     double *zt = nullptr, *uin = nullptr;       // [cap_e][3], [cap_e] pair state (lower index's entry)
     int *has = nullptr;                         // [cap_e] pair in contact (state valid)
-    double *F0 = nullptr, *T0 = nullptr, *F1 = nullptr, *T1 = nullptr, *F2 = nullptr, *T2 = nullptr;
+    double *F0 = nullptr, *T0 = nullptr, *F1 = nullptr, *T1 = nullptr;
     double *xt = nullptr, *ut = nullptr, *wt = nullptr, *xb = nullptr, *fh = nullptr, *th = nullptr;
     long long *tot = nullptr;
     // contact history kept between calls: per particle p, its pairs (p, q > p)
@@ -285,10 +285,12 @@ __device__ void col_pair(const ColPrm &P, const double *dv, const double *us, co
                          const double *wo, double ds, double dd_o, double rs, double ro, const double *zt,
                          double uin, double *F, double *T) {
     const double Rs = 0.5 * ds, Ro = 0.5 * dd_o;
+    for (int c = 0; c < 3; ++c) F[c] = T[c] = 0.0;
+    // most list entries lie beyond eps_sep: decide on the gap before the rest
+    // of the geometry (the same FP64 expression as col_geo)
+    if (sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]) - Rs - Ro >= P.eps) return;
     PairGeo G;
     col_geo(dv, us, uo, ws, wo, Rs, Ro, G);
-    for (int c = 0; c < 3; ++c) F[c] = T[c] = 0.0;
-    if (G.zeta >= P.eps) return;
     const double ms = mass(ds, rs), mo = mass(dd_o, ro);
     const double m_eff = ms * mo / (ms + mo);
     if (G.zeta > 0.0) {
@@ -324,7 +326,34 @@ __device__ void col_pair(const ColPrm &P, const double *dv, const double *us, co
     T[2] = as[0] * Ft[1] - as[1] * Ft[0];
 }
 
-// Collision loads of every particle over its neighbour list, in list order.
+// Collision loads of particle p over its neighbour list, in list order.
+__device__ __forceinline__ void col_loads(int p, const ColPrm &P, const double *x, const double *u,
+                                          const double *om, const double *d, const double *rho,
+                                          const int32_t *scene, const int32_t *dims, const int *nstart,
+                                          const int *nbr, const int *canon, const double *zt, const double *uin,
+                                          const int *has, double Fs[3], double Ts[3]) {
+    const int s = scene[p];
+    const double L[3] = {dims[3 * s] * P.h, dims[3 * s + 1] * P.h, dims[3 * s + 2] * P.h};
+    for (int k = 0; k < 3; ++k) Fs[k] = Ts[k] = 0.0;
+    for (int j = nstart[p]; j < nstart[p + 1]; ++j) {
+        const int q = nbr[j], c = canon[j];
+        double dv[3], z[3] = {0, 0, 0}, ui = -1.0;
+        for (int k = 0; k < 3; ++k) dv[k] = min_img(x[3 * q + k] - x[3 * p + k], L[k]);
+        if (c >= 0 && has[c]) {
+            const double sgn = p < q ? 1.0 : -1.0;   // the state is stored in the lower index's frame
+            for (int k = 0; k < 3; ++k) z[k] = sgn * zt[3 * c + k];
+            ui = uin[c];
+        }
+        double F[3], T[3];
+        col_pair(P, dv, u + 3 * p, u + 3 * q, om + 3 * p, om + 3 * q, d[p], d[q], rho[p], rho[q], z, ui, F, T);
+        for (int k = 0; k < 3; ++k) {
+            Fs[k] += F[k];
+            Ts[k] += T[k];
+        }
+    }
+}
+
+// Collision loads of every particle at (x, u, om).
 __global__ void __launch_bounds__(kColBlock) k_col_force(int n, ColPrm P, const double *x, const double *u,
                                                          const double *om, const double *d, const double *rho,
                                                          const int32_t *scene, const int32_t *dims,
@@ -332,25 +361,8 @@ __global__ void __launch_bounds__(kColBlock) k_col_force(int n, ColPrm P, const 
                                                          const double *zt, const double *uin, const int *has,
                                                          double *Fc, double *Tc) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int s = scene[p];
-        const double L[3] = {dims[3 * s] * P.h, dims[3 * s + 1] * P.h, dims[3 * s + 2] * P.h};
-        double Fs[3] = {0, 0, 0}, Ts[3] = {0, 0, 0};
-        for (int j = nstart[p]; j < nstart[p + 1]; ++j) {
-            const int q = nbr[j], c = canon[j];
-            double dv[3], z[3] = {0, 0, 0}, ui = -1.0;
-            for (int k = 0; k < 3; ++k) dv[k] = min_img(x[3 * q + k] - x[3 * p + k], L[k]);
-            if (c >= 0 && has[c]) {
-                const double sgn = p < q ? 1.0 : -1.0;   // the state is stored in the lower index's frame
-                for (int k = 0; k < 3; ++k) z[k] = sgn * zt[3 * c + k];
-                ui = uin[c];
-            }
-            double F[3], T[3];
-            col_pair(P, dv, u + 3 * p, u + 3 * q, om + 3 * p, om + 3 * q, d[p], d[q], rho[p], rho[q], z, ui, F, T);
-            for (int k = 0; k < 3; ++k) {
-                Fs[k] += F[k];
-                Ts[k] += T[k];
-            }
-        }
+        double Fs[3], Ts[3];
+        col_loads(p, P, x, u, om, d, rho, scene, dims, nstart, nbr, canon, zt, uin, has, Fs, Ts);
         for (int k = 0; k < 3; ++k) {
             Fc[3 * p + k] = Fs[k];
             Tc[3 * p + k] = Ts[k];
@@ -358,16 +370,27 @@ __global__ void __launch_bounds__(kColBlock) k_col_force(int n, ColPrm P, const 
     }
 }
 
-// One half of an RK stage (Sec. 2.2.10): CORRECT = false writes the predictor
-// (xo, uo, wo) from the loads Fa = F_c(x^{k-1}), Fb = F_c(x^{k-2});
-// CORRECT = true advances (x, u, w) in place with Fa = F_c(predicted),
-// Fb = F_c(x^{k-1}).
+// Half of an RK stage (Sec. 2.2.10) for every particle: the collision loads
+// at (xs, us, ws) -- the state at the start of the stage for the predictor,
+// the predicted state for the corrector -- then the update
+//   u' = u^{k-1} + ds/m (2 alpha F_h + gamma F + zeta Fb) + 2 alpha ds g'
+//   w' = w^{k-1} + ds/I (2 alpha T_h + gamma T + zeta Tb)
+//   x' = x^{k-1} + alpha ds (u' + u^{k-1})
+// with Fb = F_c(x^{k-2}) for the predictor and F_c(x^{k-1}) for the
+// corrector.  The predictor (CORRECT = false) keeps its loads in Fa, Ta (the
+// corrector's Fb) and writes (xo, uo, wo); the corrector advances (x, u, w)
+// in place, which no thread of its launch reads (its loads are taken at the
+// predicted state).
 template <bool CORRECT>
-__global__ void k_col_update(int n, ColPrm P, double a, double g, double z, double ds, const double *d,
-                             const double *rho, const double *Fh, const double *Th, const double *Fa,
-                             const double *Ta, const double *Fb, const double *Tb, double *x, double *u, double *w,
-                             double *xo, double *uo, double *wo, int *err) {
+__global__ void __launch_bounds__(kColBlock) k_col_stage(
+    int n, ColPrm P, double a, double g, double z, double ds, const double *xs, const double *us, const double *ws,
+    const double *d, const double *rho, const int32_t *scene, const int32_t *dims, const int *nstart,
+    const int *nbr, const int *canon, const double *zt, const double *uin, const int *has, const double *Fh,
+    const double *Th, double *Fa, double *Ta, const double *Fb, const double *Tb, double *x, double *u, double *w,
+    double *xo, double *uo, double *wo, int *err) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        double Fs[3], Ts[3];
+        col_loads(p, P, xs, us, ws, d, rho, scene, dims, nstart, nbr, canon, zt, uin, has, Fs, Ts);
         const double m = mass(d[p], rho[p]);
         if (!(m > 0.0)) {
             set_err(err, IBM_EBIT_MASS);
@@ -377,9 +400,13 @@ __global__ void k_col_update(int n, ColPrm P, double a, double g, double z, doub
         const double gr = 1.0 - P.rho_f / rho[p];
         for (int c = 0; c < 3; ++c) {
             const int i = 3 * p + c;
+            if (!CORRECT) {
+                Fa[i] = Fs[c];
+                Ta[i] = Ts[c];
+            }
             const double fh = Fh ? Fh[i] : 0.0, th = Th ? Th[i] : 0.0;
-            const double un = u[i] + ds / m * (2.0 * a * fh + g * Fa[i] + z * Fb[i]) + 2.0 * a * ds * gr * P.g[c];
-            const double wn = w[i] + ds / I * (2.0 * a * th + g * Ta[i] + z * Tb[i]);
+            const double un = u[i] + ds / m * (2.0 * a * fh + g * Fs[c] + z * Fb[i]) + 2.0 * a * ds * gr * P.g[c];
+            const double wn = w[i] + ds / I * (2.0 * a * th + g * Ts[c] + z * Tb[i]);
             const double xn = x[i] + a * ds * (un + u[i]);
             if (CORRECT) {
                 x[i] = xn;
@@ -408,6 +435,15 @@ __global__ void k_col_history(int n, ColPrm P, double dts, const double *x, cons
             if (q < p) continue;
             double dv[3];
             for (int k = 0; k < 3; ++k) dv[k] = min_img(x[3 * q + k] - x[3 * p + k], L[k]);
+            const bool apart = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]) - 0.5 * d[p] - 0.5 * d[q] > 0.0;
+            if (apart) {
+                if (has[j]) {
+                    has[j] = 0;
+                    uin[j] = -1.0;
+                    zt[3 * j] = zt[3 * j + 1] = zt[3 * j + 2] = 0.0;
+                }
+                continue;
+            }
             PairGeo G;
             col_geo(dv, u + 3 * p, u + 3 * q, om + 3 * p, om + 3 * q, 0.5 * d[p], 0.5 * d[q], G);
             if (G.zeta > 0.0) {
@@ -534,7 +570,7 @@ ibm_status col_build(ibm_ctx *ctx, ColScratch *S, const ColPrm &P, long long *n_
         CK(dev_realloc(&S->items, c * sizeof(int)), "alloc collision scratch");
         CK(dev_realloc(&S->hoff, c * sizeof(int)), "alloc collision scratch");
         CK(dev_realloc(&S->hcnt, c * sizeof(int)), "alloc collision scratch");
-        double **v3[] = {&S->F0, &S->T0, &S->F1, &S->T1, &S->F2, &S->T2, &S->xt, &S->ut, &S->wt, &S->xb,
+        double **v3[] = {&S->F0, &S->T0, &S->F1, &S->T1, &S->xt, &S->ut, &S->wt, &S->xb,
                          &S->fh, &S->th};
         for (double **p : v3) CK(dev_realloc(p, 3 * c * sizeof(double)), "alloc collision scratch");
         if (!S->tot) CK(ibm_malloc(&S->tot, 4 * sizeof(long long)), "alloc collision scratch");
@@ -655,7 +691,7 @@ void collision_free(ibm_ctx *ctx) {
     ColScratch *S = reinterpret_cast<ColScratch *>(ctx->col);
     if (!S) return;
     void *ptrs[] = {S->scene_nb, S->scene_off, S->bin_of, S->bin_cnt, S->bin_start, S->bin_cur, S->items, S->ncnt,
-                    S->nstart, S->nbr, S->canon, S->zt, S->uin, S->has, S->F0, S->T0, S->F1, S->T1, S->F2, S->T2,
+                    S->nstart, S->nbr, S->canon, S->zt, S->uin, S->has, S->F0, S->T0, S->F1, S->T1,
                     S->xt, S->ut, S->wt, S->xb, S->fh, S->th, S->tot, S->hoff, S->hcnt, S->hq, S->hz, S->hu};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -694,28 +730,26 @@ extern "C" ibm_status ibm_particle_substeps(ibm_ctx *ctx, const ibm_collision_pa
     double *F0 = S->F0, *T0 = S->T0, *F1 = S->F1, *T1 = S->T1;
     for (int s = 0; s < n_sub; ++s) {
         for (int k = 0; k < 3; ++k) {
-            k_col_force<<<gb, kColBlock, 0, sm>>>(n, P, ctx->x, ctx->up, ctx->om, ctx->d, ctx->rho, ctx->scene,
-                                                  ctx->dims_d, S->nstart, S->nbr, S->canon, S->zt, S->uin, S->has,
-                                                  F1, T1);
             if (k == 0) {
                 CK(cudaMemsetAsync(F0, 0, 3 * (size_t)n * sizeof(double), sm), "zero loads");
                 CK(cudaMemsetAsync(T0, 0, 3 * (size_t)n * sizeof(double), sm), "zero loads");
             }
-            k_col_update<false><<<gb, kColBlock, 0, sm>>>(n, P, A[k], G[k], Z[k], ds, ctx->d, ctx->rho, Fh, Th, F1,
-                                                          T1, F0, T0, ctx->x, ctx->up, ctx->om, S->xt, S->ut, S->wt,
-                                                          ctx->err_d);
-            k_col_force<<<gb, kColBlock, 0, sm>>>(n, P, S->xt, S->ut, S->wt, ctx->d, ctx->rho, ctx->scene,
-                                                  ctx->dims_d, S->nstart, S->nbr, S->canon, S->zt, S->uin, S->has,
-                                                  S->F2, S->T2);
-            k_col_update<true><<<gb, kColBlock, 0, sm>>>(n, P, A[k], G[k], Z[k], ds, ctx->d, ctx->rho, Fh, Th,
-                                                         S->F2, S->T2, F1, T1, ctx->x, ctx->up, ctx->om, nullptr,
-                                                         nullptr, nullptr, ctx->err_d);
+            // predictor: loads at the stage's start state, kept in F1 for the corrector
+            k_col_stage<false><<<gb, kColBlock, 0, sm>>>(
+                n, P, A[k], G[k], Z[k], ds, ctx->x, ctx->up, ctx->om, ctx->d, ctx->rho, ctx->scene, ctx->dims_d,
+                S->nstart, S->nbr, S->canon, S->zt, S->uin, S->has, Fh, Th, F1, T1, F0, T0, ctx->x, ctx->up,
+                ctx->om, S->xt, S->ut, S->wt, ctx->err_d);
+            // corrector: loads at the predicted state
+            k_col_stage<true><<<gb, kColBlock, 0, sm>>>(
+                n, P, A[k], G[k], Z[k], ds, S->xt, S->ut, S->wt, ctx->d, ctx->rho, ctx->scene, ctx->dims_d,
+                S->nstart, S->nbr, S->canon, S->zt, S->uin, S->has, Fh, Th, nullptr, nullptr, F1, T1, ctx->x,
+                ctx->up, ctx->om, nullptr, nullptr, nullptr, ctx->err_d);
             k_col_history<<<gb, kColBlock, 0, sm>>>(n, P, 2.0 * A[k] * ds, ctx->x, ctx->up, ctx->om, ctx->d,
                                                     ctx->rho, ctx->scene, ctx->dims_d, S->nstart, S->nbr, S->zt,
                                                     S->uin, S->has);
             std::swap(F0, F1);   // F_c(x^{k-1}) of this stage is F_c(x^{k-2}) of the next
             std::swap(T0, T1);
-            ctx->launches += 5;
+            ctx->launches += 3;
         }
     }
     k_col_margin<<<gb, kColBlock, 0, sm>>>(n, ctx->x, S->xb, ctx->scene, ctx->dims_d, ctx->cfg.h, 0.5 * margin,
