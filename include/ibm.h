@@ -96,9 +96,11 @@ typedef struct {
     int threads_per_block;   /* cluster kernel (CLUSTER, DETERMINISTIC): 0 =
                                 1024 threads, one CTA per SM; 512 = two
                                 512-thread CTAs per SM; -1 = autotune: the
-                                first step warms up, the next two time the
-                                two variants (with a host sync each), the
-                                faster is kept for the context's lifetime   */
+                                first two steps run each variant once, the
+                                next two time each variant's whole step
+                                (kernel and the fallback work its routing
+                                leaves, with a host sync each); the faster
+                                is kept for the context's lifetime          */
     int profile;             /* 1: time the main forcing kernel with CUDA events */
     int use_graph;           /* 1: ibm_forcing_step calls without slip_out (and
                                 without requires_grad) are replayed from a CUDA

@@ -1661,6 +1661,7 @@ static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams
 static int markers_per_thread(int) { return 12; }
 static int records_per_thread(int) { return 2; }
 static int ctas_per_sm(int tpb) { return tpb == 512 ? 2 : 1; }
+static constexpr int kTuneSteps = 4;
 
 ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
     ibm_status st = ensure_field_ptrs(ctx, u_ptrs, f_out);
@@ -1672,8 +1673,10 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     cudaStream_t sm = ctx->stream;
     // kernel variant: fixed, or autotuned over the first steps (see ibm_config)
     const int req = ctx->cfg.threads_per_block;
-    const bool tuning = req < 0 && ctx->tune_step < 3;
-    const int tpb = req > 0 ? req : (req == 0 ? 1024 : (tuning ? (ctx->tune_step == 2 ? 512 : 1024) : ctx->tuned_tpb));
+    // tuning steps 0 and 1 run each variant once untimed (module load, first-use allocations of the
+    // fallback buffers), steps 2 and 3 time them
+    const bool tuning = req < 0 && ctx->tune_step < kTuneSteps;
+    const int tpb = req > 0 ? req : (req == 0 ? 1024 : (tuning ? ((ctx->tune_step & 1) ? 512 : 1024) : ctx->tuned_tpb));
     const int cap_m = tpb * markers_per_thread(tpb);
     const int spin = ctx->wait_limit > 0 ? ctx->wait_limit : kUnionSpin;
     // row table may take at most half of the dynamic shared memory
@@ -1742,7 +1745,7 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prm.finv = (float)(1.0 / tau);
     prof_begin(ctx);
     cudaEvent_t tev[2] = {nullptr, nullptr};
-    if (tuning && ctx->tune_step > 0) {
+    if (tuning && ctx->tune_step >= 2) {
         CK(cudaEventCreate(&tev[0]), "tuning event");
         CK(cudaEventCreate(&tev[1]), "tuning event");
         CK(cudaEventRecord(tev[0], sm), "tuning event");
@@ -1755,25 +1758,28 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
         st = det ? launch_cluster_kernel<512, 12, 2, true, 2>(ctx, S, prm)
                  : launch_cluster_kernel<512, 12, 2, false, 2>(ctx, S, prm);
     prof_end(ctx);
+    if (st == IBM_OK) {
+        ctx->launches += 1;
+        // clusters that did not fit: plain FP32 iterations over their particles
+        st = plain_iterations_f32(ctx, S->fb_list, n, S->cnt + C_NFB, tau, f_out != nullptr, ctx->cfg.n_forcing,
+                                  det ? S->pcl : nullptr);
+    }
     if (tev[0]) {
-        // tuning step: time this variant (host sync), keep the faster after both
+        // tuning step: time this variant together with the fallback work its routing leaves (host sync);
+        // keep the faster after both
         float ms = 0.f;
-        cudaEventRecord(tev[1], sm);
-        cudaEventSynchronize(tev[1]);
-        cudaEventElapsedTime(&ms, tev[0], tev[1]);
+        if (st == IBM_OK) {
+            cudaEventRecord(tev[1], sm);
+            cudaEventSynchronize(tev[1]);
+            cudaEventElapsedTime(&ms, tev[0], tev[1]);
+        }
         cudaEventDestroy(tev[0]);
         cudaEventDestroy(tev[1]);
-        ctx->tune_ms[ctx->tune_step - 1] = ms;
-        if (ctx->tune_step == 2) ctx->tuned_tpb = ctx->tune_ms[0] <= ctx->tune_ms[1] ? 1024 : 512;
+        ctx->tune_ms[ctx->tune_step - 2] = ms;
+        if (ctx->tune_step == 3) ctx->tuned_tpb = ctx->tune_ms[0] <= ctx->tune_ms[1] ? 1024 : 512;
     }
-    if (tuning) ctx->tune_step += 1;
-    if (st != IBM_OK) return st;
-    ctx->launches += 1;
-    // clusters that did not fit: plain FP32 iterations over their particles
-    st = plain_iterations_f32(ctx, S->fb_list, n, S->cnt + C_NFB, tau, f_out != nullptr, ctx->cfg.n_forcing,
-                              det ? S->pcl : nullptr);
-    if (st != IBM_OK) return st;
-    return IBM_OK;
+    if (tuning && st == IBM_OK) ctx->tune_step += 1;
+    return st;
 }
 
 void cluster_graph_key(const ibm_ctx *ctx, std::vector<uintptr_t> &key) {

@@ -422,7 +422,7 @@ ibm_status ibm_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void 
             if (!f_out[s]) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "NULL f_out field");
     if (!(tau > 0.0) || !std::isfinite(tau)) return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "tau must be > 0");
     if (ctx->cfg.use_graph && !slip_out && !ctx->cfg.requires_grad && ctx->n_p > 0 &&
-        (ctx->cfg.threads_per_block >= 0 || ctx->cfg.spread_mode == IBM_SPREAD_PLAIN || ctx->tune_step >= 3))
+        (ctx->cfg.threads_per_block >= 0 || ctx->cfg.spread_mode == IBM_SPREAD_PLAIN || ctx->tune_step >= 4))
         return graph_step(ctx, u_ptrs, tau, f_out);
     ibm_status st = forcing_body(ctx, u_ptrs, tau, f_out);
     if (st != IBM_OK) return st;
