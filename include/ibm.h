@@ -49,7 +49,8 @@ typedef enum {
     IBM_ERR_CAPACITY = 4,     /* more particles than max_particles            */
     IBM_ERR_NONFINITE = 5,    /* NaN/Inf in particle state                    */
     IBM_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up           */
-    IBM_ERR_STATE = 7         /* call out of order (e.g. backward w/o forward)*/
+    IBM_ERR_STATE = 7,        /* call out of order (e.g. backward w/o forward)*/
+    IBM_ERR_NOCONVERGE = 8    /* an iterative solve missed its tolerance      */
 } ibm_status;
 
 /* precision */
@@ -418,6 +419,101 @@ ibm_status ibm_set_wait_limit(ibm_ctx *ctx, int64_t iterations);
  * host before cudaMalloc.  The paper has no counterpart.
  * Errors: INVALID_ARG (n < 0). */
 ibm_status ibm_debug_fail_allocation(int64_t n);
+
+/* ------------------------------------------------------------------------
+ * Collocated fractional-step fluid solver (Sec. 2.2.3 "Pressure-momentum
+ * coupling on a collocated grid" and Sec. 2.2.5, the modified solver
+ * Eq. fluid-solver (a)-(i)) on one triply periodic grid, FP64.  One RK3 stage
+ * k (alpha_k, gamma_k, zeta_k of Rai and Moin, Sec. 2.2.1) is
+ *   (a)  u~ = u + dt (2 alpha nu lap u - 2 alpha grad P - gamma N(u) - zeta N_old),
+ *        N(u) = (u . grad) u (advective form, central differences), kept as
+ *        the next stage's N_old;
+ *   (b)-(d) the IBM forcing loop on u~ (ibm_forcing_step with tau = 2 alpha dt,
+ *        which leaves u~ + 2 alpha dt f_IBM in place);
+ *   (e)  (1 - alpha dt nu lap) u* = u~ - 2 alpha dt f_mean - alpha dt nu lap u
+ *                                  + 2 alpha theta dt grad P     (Crank-Nicolson),
+ *        f_mean the volume average of f_IBM (compatibility, Sec. 2.2.4);
+ *   (f)  u_f* = I(u*): the mean of the two cells at each face;
+ *   (g)  lap phi = div u_f* / (2 alpha dt)  (compact 7-point operator);
+ *   (h)  u = u* - 2 alpha dt grad phi (central), u_f = u_f* - 2 alpha dt
+ *        (grad phi)_f (difference across the face);
+ *   (i)  P = (1 - theta) P + theta (phi - alpha dt nu lap phi).
+ * The equations of (e) and (g) are solved by multigrid V-cycles (red-black
+ * Gauss-Seidel smoothing, averaging restriction, trilinear prolongation,
+ * a one-CTA conjugate-gradient solve on the coarsest level) to the relative
+ * residual rtol (max norm).  The Poisson right-hand side is made mean-free
+ * and phi leaves each stage with zero mean.  Everything is deterministic.
+ *
+ * Fields are caller-owned DEVICE arrays of doubles, x fastest:
+ *   u, ut, uf  [3][nz][ny][nx]; p, phi [nz][ny][nx].
+ * uf[d] holds the face between cell i and cell i+1 along axis d.
+ * ---------------------------------------------------------------------- */
+typedef struct ibm_fluid ibm_fluid;
+
+typedef struct {
+    int nx, ny, nz;          /* periodic grid, each >= 2; halving every even
+                                extent down to at most 32768 cells must be
+                                possible (the coarsest multigrid level)       */
+    double h;                /* grid spacing (> 0)                             */
+    double nu;               /* kinematic viscosity (>= 0)                     */
+    double theta;            /* 0: pressure projection, 1: pressure correction
+                                (step (i)); any value in [0, 1]               */
+    double rtol;             /* relative max-norm residual of each solve;
+                                0 = 1e-12                                     */
+    int max_cycles;          /* V-cycles per solve before IBM_ERR_NOCONVERGE;
+                                0 = 60                                        */
+} ibm_fluid_config;
+
+typedef struct {
+    double *u;      /* u^{k-1} in, u^k out                                    */
+    double *ut;     /* out: u~ after ibm_fluid_predict; in: the forced u~ to
+                       ibm_fluid_correct, which leaves u* in it               */
+    double *uf;     /* out: face velocities u_f^k                             */
+    double *p;      /* P^{k-1} in, P^k out                                    */
+    double *phi;    /* in: initial guess of the Poisson solve; out: phi       */
+} ibm_fluid_fields;
+
+/* Create a solver on cuda_stream (NULL = legacy default stream).  It owns
+ * the scratch: N_old (zero at creation), the multigrid levels, the Poisson
+ * and Helmholtz right-hand sides, about 5.3 doubles per cell in all.
+ * Errors: INVALID_ARG (sizes, h, nu, theta, coarsest level too large),
+ * OOM, CUDA. */
+ibm_status ibm_fluid_create(const ibm_fluid_config *cfg, void *cuda_stream, ibm_fluid **out);
+ibm_status ibm_fluid_destroy(ibm_fluid *fl);
+
+/* Step (a) of RK3 stage k (0, 1, 2) with time step dt: writes ut and the
+ * stage's convective term (kept inside fl for stage k+1; stage 0 ignores it).
+ * Errors: INVALID_ARG (k, dt, NULL field), CUDA. */
+ibm_status ibm_fluid_predict(ibm_fluid *fl, int k, double dt, const ibm_fluid_fields *F);
+
+/* Steps (e)-(i) of stage k from the forced field in ut.  mean_f: NULL (no
+ * IBM force), or the volume average of f_IBM per component, [3] doubles,
+ * HOST memory (on_device = 0) or DEVICE memory (1).  Note that
+ * ibm_mean_force returns its negation (Eq. fe_IBM).  Synchronises the stream
+ * once per V-cycle (convergence test).
+ * Errors: INVALID_ARG, NOCONVERGE (a solve missed rtol in max_cycles; the
+ * fields then hold the last iterate), CUDA. */
+ibm_status ibm_fluid_correct(ibm_fluid *fl, int k, double dt, const ibm_fluid_fields *F, const double *mean_f,
+                             int on_device);
+
+/* One whole RK3 stage k: ibm_fluid_predict, the forcing loop of ctx on ut
+ * (tau = 2 alpha_k dt; ctx FP64, one scene of the same dims and h; NULL ctx
+ * or no particles: no forcing), the grid-pass mean of f_IBM (ibm_mean_force),
+ * and ibm_fluid_correct.  f_out: NULL (scratch inside fl), or a DEVICE
+ * [3][nz][ny][nx] array that receives f_IBM.  The particle loads of the stage
+ * are then available from ibm_particle_loads(ctx, ...).  ctx's stream is
+ * ordered after fl's and back by events.
+ * Errors: as the calls it makes (messages copied to fl). */
+ibm_status ibm_fluid_stage(ibm_fluid *fl, ibm_ctx *ctx, int k, double dt, const ibm_fluid_fields *F,
+                           double *f_out);
+
+/* Solver report of the last ibm_fluid_correct: cycles[4] and resid[4] (V-cycles
+ * and final relative max-norm residual of the three Helmholtz solves and the
+ * Poisson solve), levels = multigrid levels.  Any pointer may be NULL. */
+ibm_status ibm_fluid_stats(ibm_fluid *fl, int64_t *cycles, double *resid, int *levels);
+
+/* Description of the last error on fl (empty string if none); never NULL. */
+const char *ibm_fluid_last_error(const ibm_fluid *fl);
 
 /* Human-readable status name; never NULL. */
 const char *ibm_status_string(ibm_status s);

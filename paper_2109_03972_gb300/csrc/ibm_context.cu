@@ -149,6 +149,7 @@ const char *ibm_status_string(ibm_status s) {
         case IBM_ERR_NONFINITE: return "IBM_ERR_NONFINITE";
         case IBM_ERR_TIMEOUT: return "IBM_ERR_TIMEOUT";
         case IBM_ERR_STATE: return "IBM_ERR_STATE";
+        case IBM_ERR_NOCONVERGE: return "IBM_ERR_NOCONVERGE";
     }
     return "IBM_ERR_UNKNOWN";
 }

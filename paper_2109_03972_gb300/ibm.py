@@ -22,7 +22,8 @@ IBM_PATH_SMEM, IBM_PATH_GLOBAL_RECORDS, IBM_PATH_ONE_COMPONENT = 1, 2, 4
 IBM_PATH_SPARSE_ROWS, IBM_PATH_PERIODIC, IBM_PATH_FALLBACK = 8, 16, 32
 
 STATUS = {0: "IBM_OK", 1: "IBM_ERR_INVALID_ARG", 2: "IBM_ERR_CUDA", 3: "IBM_ERR_OOM",
-          4: "IBM_ERR_CAPACITY", 5: "IBM_ERR_NONFINITE", 6: "IBM_ERR_TIMEOUT", 7: "IBM_ERR_STATE"}
+          4: "IBM_ERR_CAPACITY", 5: "IBM_ERR_NONFINITE", 6: "IBM_ERR_TIMEOUT", 7: "IBM_ERR_STATE",
+          8: "IBM_ERR_NOCONVERGE"}
 
 EXPORTED = ["ibm_create", "ibm_destroy", "ibm_set_particles", "ibm_forcing_step",
             "ibm_particle_loads", "ibm_backward", "ibm_marker_bases", "ibm_step_stats",
@@ -51,6 +52,17 @@ class _CollisionParams(ctypes.Structure):
                 ("t_c", ctypes.c_double), ("st_crit", ctypes.c_double), ("eps_sep", ctypes.c_double),
                 ("zeta_min", ctypes.c_double), ("lub_c", ctypes.c_double), ("g", ctypes.c_double * 3),
                 ("pair_margin", ctypes.c_double)]
+
+
+class _FluidConfig(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double),
+                ("nu", ctypes.c_double), ("theta", ctypes.c_double), ("rtol", ctypes.c_double),
+                ("max_cycles", ctypes.c_int)]
+
+
+class _FluidFields(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("ut", ctypes.c_void_p), ("uf", ctypes.c_void_p), ("p", ctypes.c_void_p),
+                ("phi", ctypes.c_void_p)]
 
 
 @dataclass
@@ -120,6 +132,20 @@ def load_library(path: str = LIB_PATH):
     L.ibm_debug_fail_allocation.argtypes = [ctypes.c_int64]
     L.ibm_debug_fail_allocation.restype = i
     L.ibm_kernel_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i]
+    L.ibm_fluid_create.argtypes = [ctypes.POINTER(_FluidConfig), vp, ctypes.POINTER(vp)]
+    L.ibm_fluid_create.restype = i
+    L.ibm_fluid_destroy.argtypes = [vp]
+    L.ibm_fluid_destroy.restype = i
+    L.ibm_fluid_predict.argtypes = [vp, i, d, ctypes.POINTER(_FluidFields)]
+    L.ibm_fluid_predict.restype = i
+    L.ibm_fluid_correct.argtypes = [vp, i, d, ctypes.POINTER(_FluidFields), vp, i]
+    L.ibm_fluid_correct.restype = i
+    L.ibm_fluid_stage.argtypes = [vp, vp, i, d, ctypes.POINTER(_FluidFields), vp]
+    L.ibm_fluid_stage.restype = i
+    L.ibm_fluid_stats.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
+    L.ibm_fluid_stats.restype = i
+    L.ibm_fluid_last_error.argtypes = [vp]
+    L.ibm_fluid_last_error.restype = ctypes.c_char_p
     L.ibm_status_string.argtypes = [i]
     L.ibm_status_string.restype = ctypes.c_char_p
     L.ibm_last_error.argtypes = [vp]
@@ -348,6 +374,88 @@ class Context:
         keys = ("markers", "clusters", "clusters_smem", "markers_fallback", "largest_cluster_cells",
                 "touched_cells", "launches", "threads_per_block", "clusters_one_component", "candidate_pairs")
         return dict(zip(keys, (int(v) for v in out)))
+
+
+class FluidFields:
+    """Device state of one periodic grid: u, ut, uf [3, nz, ny, nx], p, phi [nz, ny, nx], float64."""
+
+    def __init__(self, dims, u=None, p=None, device="cuda"):
+        nx, ny, nz = dims
+        z = lambda *s: torch.zeros(s, dtype=torch.float64, device=device)
+        self.u = z(3, nz, ny, nx) if u is None else torch.as_tensor(u, dtype=torch.float64, device=device).clone()
+        self.ut = z(3, nz, ny, nx)
+        self.uf = z(3, nz, ny, nx)
+        self.p = z(nz, ny, nx) if p is None else torch.as_tensor(p, dtype=torch.float64, device=device).clone()
+        self.phi = z(nz, ny, nx)
+        for t in (self.u, self.ut, self.uf, self.p, self.phi):
+            assert t.is_contiguous()
+
+    def _c(self):
+        return _FluidFields(*[t.data_ptr() for t in (self.u, self.ut, self.uf, self.p, self.phi)])
+
+
+class Fluid:
+    """ibm_fluid: the collocated fractional-step solver of Sec. 2.2.3-2.2.5 on
+    one periodic grid (FP64), on a CUDA stream (torch's current by default)."""
+
+    def __init__(self, dims, h=1.0, nu=0.01, theta=1.0, rtol=0.0, max_cycles=0, stream=None):
+        self.L = load_library()
+        self.dims = tuple(int(v) for v in dims)
+        self.stream = stream or torch.cuda.current_stream()
+        c = _FluidConfig(*self.dims, float(h), float(nu), float(theta), float(rtol), int(max_cycles))
+        hnd = ctypes.c_void_p()
+        st = self.L.ibm_fluid_create(ctypes.byref(c), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(hnd))
+        if st != 0:
+            raise IBMError(st, "ibm_fluid_create rejected the configuration")
+        self.h = hnd
+
+    def _check(self, st):
+        if st != 0:
+            raise IBMError(st, self.L.ibm_fluid_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ibm_fluid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def predict(self, k, dt, F: FluidFields):
+        c = F._c()
+        self._check(self.L.ibm_fluid_predict(self.h, int(k), float(dt), ctypes.byref(c)))
+
+    def correct(self, k, dt, F: FluidFields, mean_f=None):
+        """mean_f: None, a host sequence of 3 floats, or a device float64 tensor of 3."""
+        c = F._c()
+        if mean_f is None:
+            ptr, dev = None, 0
+        elif isinstance(mean_f, torch.Tensor) and mean_f.is_cuda:
+            keep = mean_f.contiguous()
+            ptr, dev = ctypes.c_void_p(keep.data_ptr()), 1
+        else:
+            keep = (ctypes.c_double * 3)(*[float(v) for v in mean_f])
+            ptr, dev = ctypes.cast(keep, ctypes.c_void_p), 0
+        self._check(self.L.ibm_fluid_correct(self.h, int(k), float(dt), ctypes.byref(c), ptr, dev))
+
+    def stage(self, k, dt, F: FluidFields, ctx: "Context | None" = None, f_out=None):
+        c = F._c()
+        self._check(self.L.ibm_fluid_stage(self.h, ctx.h if ctx is not None else None, int(k), float(dt),
+                                           ctypes.byref(c), _ptr(f_out)))
+
+    def step(self, dt, F: FluidFields, ctx: "Context | None" = None):
+        for k in range(3):
+            self.stage(k, dt, F, ctx)
+
+    def stats(self):
+        cyc = (ctypes.c_int64 * 4)()
+        res = (ctypes.c_double * 4)()
+        lv = ctypes.c_int()
+        self._check(self.L.ibm_fluid_stats(self.h, cyc, res, ctypes.byref(lv)))
+        return {"cycles": list(cyc), "resid": list(res), "levels": lv.value}
 
 
 def debug_fail_allocation(n):

@@ -76,6 +76,27 @@ def test_new_entry_points_reject_null_without_touching_gpu():
     assert L.ibm_particle_inertia(None, None, None, None, None, 0) == 1
 
 
+def test_fluid_solver_rejects_bad_config_without_touching_gpu():
+    # the fluid solver checks sizes, h, nu, theta and the coarsest multigrid level before any CUDA call
+    from paper_2109_03972_gb300 import build, ibm
+    L = ibm.load_library(build.build())
+    good = dict(nx=32, ny=32, nz=64, h=1.0, nu=0.01, theta=1.0, rtol=0.0, max_cycles=0)
+    for bad in ({"nx": 1}, {"h": 0.0}, {"nu": -1.0}, {"theta": 1.5}, {"rtol": -1.0}, {"max_cycles": -1},
+                {"nx": 33, "ny": 33, "nz": 33},        # odd: one level of 35937 cells > 32768
+                {"nx": 2 ** 14, "ny": 2 ** 14, "nz": 4}):  # beyond the index range
+        c = ibm._FluidConfig(**{**good, **bad})
+        out = ctypes.c_void_p()
+        assert L.ibm_fluid_create(ctypes.byref(c), None, ctypes.byref(out)) == 1, bad
+        assert not out.value
+    assert L.ibm_fluid_predict(None, 0, 0.1, None) == 1
+    assert L.ibm_fluid_correct(None, 0, 0.1, None, None, 0) == 1
+    assert L.ibm_fluid_stage(None, None, 0, 0.1, None, None) == 1
+    assert L.ibm_fluid_stats(None, None, None, None) == 1
+    assert L.ibm_fluid_destroy(None) == 1
+    assert L.ibm_fluid_last_error(None) == b""
+    assert L.ibm_status_string(8) == b"IBM_ERR_NOCONVERGE"
+
+
 def test_binding_fails_loudly_without_the_library(tmp_path):
     # no CPU fallback: a missing libibm.so is an ImportError, in a fresh process
     import subprocess
