@@ -56,6 +56,8 @@ def parse():
                     help="also time forward + adjoint (ibm_backward) steps, FP32 and FP64")
     ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--fluid", action="store_true",
+                    help="run the fluid-solver leg also with --quick")
     ap.add_argument("--mean-force", action="store_true",
                     help="time the grid-pass mean force even with --quick")
     return ap.parse_args()
@@ -369,6 +371,8 @@ def our_arm(args):
         line["contact_exclusion"] = exclusion_leg(cfg, us, u_host, W, (x, up, om, d, rho, so), dims, stream)
     if not args.quick:
         line["particle_substeps"] = collision_leg(W, (x, up, om, d, rho, so), dims, stream, ctx, peaks)
+    if (not args.quick or args.fluid) and len(dims) == 1:
+        line["fluid_stage"] = fluid_leg(W, (x, up, om, d, rho, so), dims[0], fields64[0], stream, peaks)
     if not args.quick:
         # end to end through the C ABI with host buffers: H2D of u and the particle
         # state, the step, D2H of u and the loads, every step
@@ -536,6 +540,64 @@ def collision_leg(W, parts, dims, stream, fctx, peaks):
     return {"what": "one particle time step tau: 15 sub-steps x 3 RK stages, collision loads at the stage start "
                     "and the predicted state, FP64", "ms_per_call": ms, "wall_ms_per_call": wall,
             "particles": len(d), "pairs_in_contact": contacts, "kernel_launches_per_call": launches}
+
+
+def fluid_leg(W, parts, dims, u0, stream, peaks):
+    """One time step (three RK3 stages) of the collocated fractional-step solver
+    of Sec. 2.2.3-2.2.5 on the workload's grid, FP64, with the IBM forcing loop
+    of the workload's particles (plain FP64 path) inside every stage: step (a),
+    n_F forcing iterations, the grid-pass mean force, the Crank-Nicolson
+    Helmholtz solves and the Poisson solve (multigrid to 1e-12), the corrector.
+    nu = 0.01, dt = tau, starting from the workload's velocity field.  CUDA
+    events over one warm and one timed step; the finest-level smoothing launches
+    (the dominant kernel) are timed one by one."""
+    import torch
+    from paper_2109_03972_gb300 import ibm
+    x, up, om, d, rho, so = parts
+    c = ibm.Context(ibm.Config(dims=[dims], n_forcing=W.n_forcing, precision=ibm.IBM_FP64,
+                               spread_mode=ibm.IBM_SPREAD_PLAIN, max_particles=len(d)), stream)
+    c.set_particles(x, up, om, d)
+    fl = ibm.Fluid(dims, h=1.0, nu=0.01, theta=1.0, profile=True, stream=stream)
+    F = ibm.FluidFields(dims)
+    F.u.copy_(torch.from_numpy(u0))
+    dt = W.tau
+    fl.step(dt, F, ctx=c)                      # warm-up step (also first-call allocations)
+    torch.cuda.synchronize()
+    fl.kernel_timing(reset=True)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    cyc, res = [], []
+    e[0].record(stream)
+    for k in range(3):
+        fl.stage(k, dt, F, ctx=c)
+        e[k + 1].record(stream)
+        s = fl.stats()
+        cyc.append(s["cycles"])
+        res.append(max(s["resid"]))
+    torch.cuda.synchronize()
+    stage_ms = [e[k].elapsed_time(e[k + 1]) for k in range(3)]
+    k_ms, k_n = fl.kernel_timing(reset=True)
+    nx, ny, nz = dims
+    cells = nx * ny * nz
+    k_avg = k_ms / max(1, k_n)
+    alg = 16 * cells                            # one colour pass: x read (8 B/cell), b and x for half the cells
+    achieved = alg / (k_avg / 1e3) / 1e9 if k_avg > 0 else None
+    uf = F.uf
+    div = ((uf[0] - torch.roll(uf[0], 1, 2)) + (uf[1] - torch.roll(uf[1], 1, 1)) +
+           (uf[2] - torch.roll(uf[2], 1, 0))).abs().max().item()
+    levels = fl.stats()["levels"]
+    del F, fl, c
+    torch.cuda.empty_cache()
+    return {"what": "one RK3 time step of the collocated fractional-step solver with the IBM loop in each stage, "
+                    "FP64, multigrid to relative residual 1e-12",
+            "grid": list(dims), "cells": cells, "particles": len(d), "ms_per_step": sum(stage_ms),
+            "ms_per_stage": stage_ms, "cells_per_s": cells / (sum(stage_ms) / 1e3),
+            "v_cycles_per_stage": cyc, "max_rel_residual": max(res), "multigrid_levels": levels,
+            "max_abs_div_uf": div,
+            "roofline": {"bound": "hbm", "kernel": "k_mg_smooth (finest level, one colour)",
+                         "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"] if achieved else None, "kernel_ms": k_avg,
+                         "launches_timed": k_n, "share_of_step": k_ms / sum(stage_ms),
+                         "algorithmic_bytes_per_launch": alg}}
 
 
 def exclusion_leg(cfg, us, u_host, W, parts, dims, stream):

@@ -438,11 +438,13 @@ ibm_status ibm_debug_fail_allocation(int64_t n);
  *   (h)  u = u* - 2 alpha dt grad phi (central), u_f = u_f* - 2 alpha dt
  *        (grad phi)_f (difference across the face);
  *   (i)  P = (1 - theta) P + theta (phi - alpha dt nu lap phi).
- * The equations of (e) and (g) are solved by multigrid V-cycles (red-black
- * Gauss-Seidel smoothing, averaging restriction, trilinear prolongation,
- * a one-CTA conjugate-gradient solve on the coarsest level) to the relative
- * residual rtol (max norm).  The Poisson right-hand side is made mean-free
- * and phi leaves each stage with zero mean.  Everything is deterministic.
+ * The equations of (e) and (g) are solved to the relative FP64 residual rtol
+ * (max norm) by iterative refinement: FP64 residual, one FP32 multigrid
+ * V-cycle for the correction (two red-black Gauss-Seidel sweeps before and
+ * after each coarse correction, averaging restriction, trilinear
+ * prolongation, a one-CTA conjugate-gradient solve on the coarsest level),
+ * FP64 update.  The Poisson right-hand side is made mean-free and phi leaves
+ * each stage with zero mean.  Everything is deterministic.
  *
  * Fields are caller-owned DEVICE arrays of doubles, x fastest:
  *   u, ut, uf  [3][nz][ny][nx]; p, phi [nz][ny][nx].
@@ -460,8 +462,14 @@ typedef struct {
                                 (step (i)); any value in [0, 1]               */
     double rtol;             /* relative max-norm residual of each solve;
                                 0 = 1e-12                                     */
-    int max_cycles;          /* V-cycles per solve before IBM_ERR_NOCONVERGE;
-                                0 = 60                                        */
+    int max_cycles;          /* V-cycles (refinement steps) per solve before
+                                IBM_ERR_NOCONVERGE; 0 = 60                    */
+    int profile;             /* 1: time every finest-level smoothing sweep
+                                with CUDA events (ibm_fluid_kernel_timing)    */
+    int two_pass_smoother;   /* 1: smooth every level by two half sweeps (red,
+                                then black) instead of the fused one-pass
+                                sweep; the results are the same bit for bit
+                                (a cross-check)                               */
 } ibm_fluid_config;
 
 typedef struct {
@@ -474,8 +482,9 @@ typedef struct {
 } ibm_fluid_fields;
 
 /* Create a solver on cuda_stream (NULL = legacy default stream).  It owns
- * the scratch: N_old (zero at creation), the multigrid levels, the Poisson
- * and Helmholtz right-hand sides, about 5.3 doubles per cell in all.
+ * the scratch: N_old (zero at creation), the FP64 right-hand side of the
+ * solves and the FP32 multigrid levels, about 46 bytes per cell (70 once
+ * ibm_fluid_stage keeps an f_IBM of its own).
  * Errors: INVALID_ARG (sizes, h, nu, theta, coarsest level too large),
  * OOM, CUDA. */
 ibm_status ibm_fluid_create(const ibm_fluid_config *cfg, void *cuda_stream, ibm_fluid **out);
@@ -511,6 +520,11 @@ ibm_status ibm_fluid_stage(ibm_fluid *fl, ibm_ctx *ctx, int k, double dt, const 
  * and final relative max-norm residual of the three Helmholtz solves and the
  * Poisson solve), levels = multigrid levels.  Any pointer may be NULL. */
 ibm_status ibm_fluid_stats(ibm_fluid *fl, int64_t *cycles, double *resid, int *levels);
+
+/* With cfg.profile: total device time (ms) and count of the finest-level
+ * red-black sweeps since the last reset (synchronises the stream).  Without
+ * it both are 0.  Errors: INVALID_ARG, CUDA. */
+ibm_status ibm_fluid_kernel_timing(ibm_fluid *fl, double *total_ms, int64_t *count, int reset);
 
 /* Description of the last error on fl (empty string if none); never NULL. */
 const char *ibm_fluid_last_error(const ibm_fluid *fl);

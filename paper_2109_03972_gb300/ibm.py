@@ -57,7 +57,7 @@ class _CollisionParams(ctypes.Structure):
 class _FluidConfig(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double),
                 ("nu", ctypes.c_double), ("theta", ctypes.c_double), ("rtol", ctypes.c_double),
-                ("max_cycles", ctypes.c_int)]
+                ("max_cycles", ctypes.c_int), ("profile", ctypes.c_int), ("two_pass_smoother", ctypes.c_int)]
 
 
 class _FluidFields(ctypes.Structure):
@@ -144,6 +144,8 @@ def load_library(path: str = LIB_PATH):
     L.ibm_fluid_stage.restype = i
     L.ibm_fluid_stats.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     L.ibm_fluid_stats.restype = i
+    L.ibm_fluid_kernel_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i]
+    L.ibm_fluid_kernel_timing.restype = i
     L.ibm_fluid_last_error.argtypes = [vp]
     L.ibm_fluid_last_error.restype = ctypes.c_char_p
     L.ibm_status_string.argtypes = [i]
@@ -398,11 +400,13 @@ class Fluid:
     """ibm_fluid: the collocated fractional-step solver of Sec. 2.2.3-2.2.5 on
     one periodic grid (FP64), on a CUDA stream (torch's current by default)."""
 
-    def __init__(self, dims, h=1.0, nu=0.01, theta=1.0, rtol=0.0, max_cycles=0, stream=None):
+    def __init__(self, dims, h=1.0, nu=0.01, theta=1.0, rtol=0.0, max_cycles=0, profile=False,
+                 two_pass_smoother=False, stream=None):
         self.L = load_library()
         self.dims = tuple(int(v) for v in dims)
         self.stream = stream or torch.cuda.current_stream()
-        c = _FluidConfig(*self.dims, float(h), float(nu), float(theta), float(rtol), int(max_cycles))
+        c = _FluidConfig(*self.dims, float(h), float(nu), float(theta), float(rtol), int(max_cycles), int(profile),
+                         int(two_pass_smoother))
         hnd = ctypes.c_void_p()
         st = self.L.ibm_fluid_create(ctypes.byref(c), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(hnd))
         if st != 0:
@@ -449,6 +453,12 @@ class Fluid:
     def step(self, dt, F: FluidFields, ctx: "Context | None" = None):
         for k in range(3):
             self.stage(k, dt, F, ctx)
+
+    def kernel_timing(self, reset=True):
+        """(total ms, launches) of the finest-level smoothing launches (profile=True)."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        self._check(self.L.ibm_fluid_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n), int(reset)))
+        return ms.value, n.value
 
     def stats(self):
         cyc = (ctypes.c_int64 * 4)()

@@ -80,7 +80,7 @@ def test_fluid_solver_rejects_bad_config_without_touching_gpu():
     # the fluid solver checks sizes, h, nu, theta and the coarsest multigrid level before any CUDA call
     from paper_2109_03972_gb300 import build, ibm
     L = ibm.load_library(build.build())
-    good = dict(nx=32, ny=32, nz=64, h=1.0, nu=0.01, theta=1.0, rtol=0.0, max_cycles=0)
+    good = dict(nx=32, ny=32, nz=64, h=1.0, nu=0.01, theta=1.0, rtol=0.0, max_cycles=0, profile=0, two_pass_smoother=0)
     for bad in ({"nx": 1}, {"h": 0.0}, {"nu": -1.0}, {"theta": 1.5}, {"rtol": -1.0}, {"max_cycles": -1},
                 {"nx": 33, "ny": 33, "nz": 33},        # odd: one level of 35937 cells > 32768
                 {"nx": 2 ** 14, "ny": 2 ** 14, "nz": 4}):  # beyond the index range
@@ -92,6 +92,7 @@ def test_fluid_solver_rejects_bad_config_without_touching_gpu():
     assert L.ibm_fluid_correct(None, 0, 0.1, None, None, 0) == 1
     assert L.ibm_fluid_stage(None, None, 0, 0.1, None, None) == 1
     assert L.ibm_fluid_stats(None, None, None, None) == 1
+    assert L.ibm_fluid_kernel_timing(None, None, None, 0) == 1
     assert L.ibm_fluid_destroy(None) == 1
     assert L.ibm_fluid_last_error(None) == b""
     assert L.ibm_status_string(8) == b"IBM_ERR_NOCONVERGE"

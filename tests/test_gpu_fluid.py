@@ -108,8 +108,10 @@ def test_predict_and_correct_separately_with_a_mean_force(F_or):
         st.u, st.uf, st.P, st.phi, st.N_old = r["u"], r["uf"], r["P"], r["phi"], N
         fl.predict(k, dt, Fd)
         torch.cuda.synchronize()
-        # step (a) alone: only rounding (FMA contraction, summation order) separates the two
-        assert np.abs(Fd.ut.cpu().numpy() - ut).max() <= 1e-12 * np.abs(ut).max()
+        # step (a): in the first stage only rounding (FMA contraction, summation order) separates the two;
+        # later stages start from u that carries the solves' tolerance
+        tol = 1e-12 if k == 0 else TOL
+        assert np.abs(Fd.ut.cpu().numpy() - ut).max() <= tol * np.abs(ut).max()
         fl.correct(k, dt, Fd, mean_f=mf if k != 1 else torch.tensor(mf, device="cuda"))
         torch.cuda.synchronize()
         _compare(Fd, st, f"stage {k}")
@@ -161,6 +163,24 @@ def test_stage_is_bit_reproducible():
         out.append([t.cpu().numpy() for t in (Fd.u, Fd.uf, Fd.p, Fd.phi)])
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dims", [(64, 48, 40), (96, 40, 66)])
+def test_fused_sweeps_equal_two_half_sweeps(dims):
+    # the one-pass red-black sweep (tiles with a 2-cell halo, 32-plane chunks; ragged tiles and chunks here)
+    # gives the two half sweeps' results bit for bit
+    nx, ny, nz = dims
+    u0 = _smooth_random((nz, ny, nx), 11)
+    out = []
+    for two in (False, True):
+        fl = ibm.Fluid(dims, h=1.0, nu=0.3, two_pass_smoother=two)
+        Fd = ibm.FluidFields(dims, u0)
+        for k in range(3):
+            fl.stage(k, 0.2, Fd)
+        torch.cuda.synchronize()
+        out.append([t.cpu().numpy() for t in (Fd.u, Fd.uf, Fd.p, Fd.phi)] + [fl.stats()["cycles"]])
+    for a, b in zip(*out):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
 
 
 def test_cycle_limit_reports_noconvergence():
