@@ -547,7 +547,8 @@ def fluid_leg(W, parts, dims, u0, stream, peaks):
     of Sec. 2.2.3-2.2.5 on the workload's grid, FP64, with the IBM forcing loop
     of the workload's particles (plain FP64 path) inside every stage: step (a),
     n_F forcing iterations, the grid-pass mean force, the Crank-Nicolson
-    Helmholtz solves and the Poisson solve (multigrid to 1e-12), the corrector.
+    Helmholtz solves and the Poisson solve (FP64 residuals around FP32 multigrid
+    V-cycles, to 1e-12), the corrector.
     nu = 0.01, dt = tau, starting from the workload's velocity field.  CUDA
     events over one warm and one timed step; the finest-level smoothing launches
     (the dominant kernel) are timed one by one."""
@@ -579,7 +580,7 @@ def fluid_leg(W, parts, dims, u0, stream, peaks):
     nx, ny, nz = dims
     cells = nx * ny * nz
     k_avg = k_ms / max(1, k_n)
-    alg = 16 * cells                            # one colour pass: x read (8 B/cell), b and x for half the cells
+    alg = 12 * cells                            # one FP32 sweep: x and b read, x written (4 B each per cell)
     achieved = alg / (k_avg / 1e3) / 1e9 if k_avg > 0 else None
     uf = F.uf
     div = ((uf[0] - torch.roll(uf[0], 1, 2)) + (uf[1] - torch.roll(uf[1], 1, 1)) +
@@ -588,12 +589,12 @@ def fluid_leg(W, parts, dims, u0, stream, peaks):
     del F, fl, c
     torch.cuda.empty_cache()
     return {"what": "one RK3 time step of the collocated fractional-step solver with the IBM loop in each stage, "
-                    "FP64, multigrid to relative residual 1e-12",
+                    "FP64 state, solves by FP64 refinement around FP32 multigrid V-cycles to relative residual 1e-12",
             "grid": list(dims), "cells": cells, "particles": len(d), "ms_per_step": sum(stage_ms),
             "ms_per_stage": stage_ms, "cells_per_s": cells / (sum(stage_ms) / 1e3),
             "v_cycles_per_stage": cyc, "max_rel_residual": max(res), "multigrid_levels": levels,
             "max_abs_div_uf": div,
-            "roofline": {"bound": "hbm", "kernel": "k_mg_smooth (finest level, one colour)",
+            "roofline": {"bound": "hbm", "kernel": "k_mg_rbgs<float> (finest-level red-black sweep)",
                          "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"] if achieved else None, "kernel_ms": k_avg,
                          "launches_timed": k_n, "share_of_step": k_ms / sum(stage_ms),

@@ -366,58 +366,75 @@ template <typename T>
 __global__ void __launch_bounds__(kFlThreads) k_mg_rbgs(int nx, int ny, int nz, T a0, T beta,
                                                         const T *__restrict__ xin, T *__restrict__ xout,
                                                         const T *__restrict__ b) {
-    __shared__ T sx[4][kRegion];
-    __shared__ T sb[2][kRegion];
+    __shared__ T sx[5][kRegion];
+    __shared__ T sb[3][kRegion];
     const int t = tid();
     const int X0 = blockIdx.x * kBx, Y0 = blockIdx.y * kBy;
     const int Z0 = blockIdx.z * kZc, Z1 = min(Z0 + kZc, nz);
     const long long plane = (long long)nx * ny;
     const T inv = T(1) / (a0 + T(6) * beta);
-    // the (at most 2) region cells this thread stages: plane offsets of their periodic images
+    // the (at most 2) region cells this thread stages and may update as red cells:
+    // plane offsets of their periodic images, ring-1 membership and parity
     long long goff[2];
-    bool have[2];
+    bool have[2], ring1[2];
+    int par[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int e = t + r * kFlThreads;
         have[r] = e < kRegion;
         const int rx = e % kRx, ry = e / kRx;
-        const int gx = (X0 - 2 + rx + nx) % nx, gy = (Y0 - 2 + ry + ny) % ny;
+        int gx = X0 - 2 + rx, gy = Y0 - 2 + ry;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
         goff[r] = (long long)gy * nx + gx;
+        ring1[r] = have[r] && rx >= 1 && rx <= kRx - 2 && ry >= 1 && ry <= kRy - 2;
+        par[r] = (rx + ry) & 1;
     }
     // this thread's tile cell (region position tx + 2, ty + 2) and whether it is inside the box
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool inside = X0 + tx < nx && Y0 + ty < ny;
     const int rc = (ty + 2) * kRx + tx + 2;
-    for (int zp = Z0 - 2; zp <= Z1 + 1; ++zp) {
-        const long long zo = (long long)((zp + nz) % nz) * plane;
-        T *px = sx[(zp + 4) & 3];
+    const int tpar = (tx + ty) & 1;
+    auto wrapz = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
+    // the next plane's values are loaded into registers one iteration ahead, so
+    // that their latency overlaps the current plane's updates
+    T vx[2] = {T(0), T(0)}, vb[2] = {T(0), T(0)};
+    auto fetch = [&](int zq) {
+        const long long zo = (long long)wrapz(zq) * plane;
+        const long long bo = (long long)wrapz(zq - 1) * plane;
 #pragma unroll
         for (int r = 0; r < 2; ++r)
-            if (have[r]) px[t + r * kFlThreads] = xin[zo + goff[r]];
-        if (zp >= Z0) {
-            const int pb = zp - 1;
-            const long long bo = (long long)((pb + nz) % nz) * plane;
-            T *pbv = sb[(pb + 2) & 1];
+            if (have[r]) {
+                vx[r] = xin[zo + goff[r]];
+                if (zq >= Z0) vb[r] = b[bo + goff[r]];
+            }
+    };
+    fetch(Z0 - 2);
+    // ring buffers: x of plane z in sx[(z - Z0 + 2) % 5], b of plane z in sb[(z - Z0 + 1) % 3].  With five
+    // and three slots a plane is overwritten only after every warp has passed the first barrier of the
+    // iteration after its last use, so one barrier after the staging and one after the red cells suffice.
+    for (int zp = Z0 - 2, it = 0; zp <= Z1 + 1; ++zp, ++it) {
+        T *px = sx[it % 5];
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
-                if (have[r]) pbv[t + r * kFlThreads] = b[bo + goff[r]];
-        }
+        for (int r = 0; r < 2; ++r)
+            if (have[r]) {
+                px[t + r * kFlThreads] = vx[r];
+                if (zp >= Z0) sb[(it - 2) % 3][t + r * kFlThreads] = vb[r];
+            }
+        if (zp + 1 <= Z1 + 1) fetch(zp + 1);
         __syncthreads();
         // red cells of plane p = zp - 1 on the tile and its ring of 1
         const int p = zp - 1;
         if (p >= Z0 - 1 && p <= Z1) {
-            T *cx = sx[(p + 4) & 3];
-            const T *dn = sx[(p + 3) & 3], *up = sx[(p + 5) & 3];
-            const T *cb = sb[(p + 2) & 1];
+            T *cx = sx[(it + 4) % 5];
+            const T *dn = sx[(it + 3) % 5], *up = sx[it % 5];
+            const T *cb = sb[(it + 1) % 3];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const int e = t + r * kFlThreads;
-                if (e < kRegion) {
-                    const int rx = e % kRx, ry = e / kRx;
-                    if (rx >= 1 && rx <= kRx - 2 && ry >= 1 && ry <= kRy - 2 && ((rx + ry + p) & 1) == 0) {
-                        const T sum = cx[e + 1] + cx[e - 1] + cx[e + kRx] + cx[e - kRx] + up[e] + dn[e];
-                        cx[e] = (cb[e] + beta * sum) * inv;
-                    }
+                if (ring1[r] && ((par[r] + p) & 1) == 0) {
+                    const T sum = cx[e + 1] + cx[e - 1] + cx[e + kRx] + cx[e - kRx] + up[e] + dn[e];
+                    cx[e] = (cb[e] + beta * sum) * inv;
                 }
             }
         }
@@ -425,16 +442,15 @@ __global__ void __launch_bounds__(kFlThreads) k_mg_rbgs(int nx, int ny, int nz, 
         // black cells of plane q = zp - 2 on the tile, and the tile written out
         const int q = zp - 2;
         if (q >= Z0 && q <= Z1 - 1) {
-            T *cx = sx[(q + 4) & 3];
-            const T *dn = sx[(q + 3) & 3], *up = sx[(q + 5) & 3];
-            const T *cb = sb[(q + 2) & 1];
-            if (((tx + ty + q) & 1) == 1) {
+            T *cx = sx[(it + 3) % 5];
+            const T *dn = sx[(it + 2) % 5], *up = sx[(it + 4) % 5];
+            const T *cb = sb[it % 3];
+            if (((tpar + q) & 1) == 1) {
                 const T sum = cx[rc + 1] + cx[rc - 1] + cx[rc + kRx] + cx[rc - kRx] + up[rc] + dn[rc];
                 cx[rc] = (cb[rc] + beta * sum) * inv;
             }
             if (inside) xout[(long long)q * plane + (long long)(Y0 + ty) * nx + X0 + tx] = cx[rc];
         }
-        __syncthreads();
     }
 }
 
