@@ -544,7 +544,7 @@ def collision_leg(W, parts, dims, stream, fctx, peaks):
 
 def fluid_leg(W, parts, dims, u0, stream, peaks):
     """One time step (three RK3 stages) of the collocated fractional-step solver
-    of Sec. 2.2.3-2.2.5 on the workload's grid, FP64, with the IBM forcing loop
+    of Sec. 2.2.1 and 2.2.4 on the workload's grid, FP64, with the IBM forcing loop
     of the workload's particles (plain FP64 path) inside every stage: step (a),
     n_F forcing iterations, the grid-pass mean force, the Crank-Nicolson
     Helmholtz solves and the Poisson solve (FP64 residuals around FP32 multigrid
@@ -602,7 +602,7 @@ def fluid_leg(W, parts, dims, u0, stream, peaks):
 
 
 def exclusion_leg(cfg, us, u_host, W, parts, dims, stream):
-    """Marker exclusion near contact (Sec. 2.2.6) costs: the FP32 plain step of
+    """Marker exclusion near contact (Sec. 2.2.5) costs: the FP32 plain step of
     the same workload with and without it (eager, CUDA events, 10 steps each)."""
     import torch
     from paper_2109_03972_gb300 import ibm

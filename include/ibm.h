@@ -172,11 +172,11 @@ ibm_status ibm_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau,
 ibm_status ibm_particle_loads(ibm_ctx *ctx, double *F, double *T, double *x_p, double *u_p,
                               double *omega_p, int on_device);
 
-/* Mean IBM force of each scene over its grid, Eq. (fe_IBM) of Sec. 2.2.5:
+/* Mean IBM force of each scene over its grid, Eq. (fe_IBM) of Sec. 2.2.4:
  *   fbar_s = -(1 / (nx ny nz)) sum over all cells of f,   per component,
  * the volume-averaged forcing that a triply-periodic fluid solver removes from
  * its momentum equation.  (The paper's integral form of the same average, the
- * aperiodic pressure gradient of Sec. 2.2.5, carries the opposite sign; this
+ * aperiodic pressure gradient of Sec. 2.2.4, carries the opposite sign; this
  * call returns the grid-pass form with its minus sign.)
  * f_ptrs[n_scenes]: HOST array of DEVICE pointers to force fields of the
  *   precision's type, layout [3][nz][ny][nx] (for example the f_out of
@@ -211,7 +211,7 @@ ibm_status ibm_mean_force(ibm_ctx *ctx, void *const *f_ptrs, double *fbar_out, i
 ibm_status ibm_particle_inertia(ibm_ctx *ctx, void *const *u_ptrs, double *Iu, double *Ir, double *V,
                                 int on_device);
 
-/* Marker exclusion near contact, Sec. 2.2.6: from the next forcing step on,
+/* Marker exclusion near contact, Sec. 2.2.5: from the next forcing step on,
  * markers are left out of f_IBM where two particles come within reach of each
  * other.  For every pair (p, q) of a scene whose surface gap
  *   zeta = |x_q - x_p| - d_p/2 - d_q/2   (minimum image)
@@ -421,10 +421,10 @@ ibm_status ibm_set_wait_limit(ibm_ctx *ctx, int64_t iterations);
 ibm_status ibm_debug_fail_allocation(int64_t n);
 
 /* ------------------------------------------------------------------------
- * Collocated fractional-step fluid solver (Sec. 2.2.3 "Pressure-momentum
- * coupling on a collocated grid" and Sec. 2.2.5, the modified solver
+ * Collocated fractional-step fluid solver (Sec. 2.2.1 "Pressure-momentum
+ * coupling on a collocated grid" and Sec. 2.2.4, the modified solver
  * Eq. fluid-solver (a)-(i)) on one triply periodic grid, FP64.  One RK3 stage
- * k (alpha_k, gamma_k, zeta_k of Rai and Moin, Sec. 2.2.1) is
+ * k (alpha_k, gamma_k, zeta_k of the Rai and Moin scheme that Sec. 2.1 names) is
  *   (a)  u~ = u + dt (2 alpha nu lap u - 2 alpha grad P - gamma N(u) - zeta N_old),
  *        N(u) = (u . grad) u (advective form, central differences), kept as
  *        the next stage's N_old;

@@ -1,5 +1,5 @@
 """FP64 CPU oracle of the collocated fractional-step fluid solver that carries
-the direct-forcing IBM (Sec. 2.2.3-2.2.5: the Zang et al. pressure-momentum
+the direct-forcing IBM (Sec. 2.2.1 and 2.2.4: the Zang et al. pressure-momentum
 coupling and the modified solver, Eq. fluid-solver (a)-(i)), on a triply
 periodic grid.
 
@@ -25,7 +25,7 @@ Readings (the paper names the scheme and its order, not each stencil):
   * the forcing loop updates u~ in place to u~ + 2 alpha dt f_IBM (its f_out
     is f_IBM), so step (e)'s right-hand side is that field minus
     2 alpha dt f_mean, with f_mean the volume average of f_IBM (the aperiodic
-    pressure gradient of Sec. 2.2.5, subtracted so the net forcing vanishes);
+    pressure gradient of Sec. 2.2.4, subtracted so the net forcing vanishes);
   * the implicit viscous equation of step (e) and the Poisson equation of
     step (g) are solved exactly by diagonalising the periodic 7-point
     Laplacian with the FFT (a library step); phi has zero mean;
@@ -35,8 +35,9 @@ Readings (the paper names the scheme and its order, not each stencil):
 Parity: pinned in tests/test_fluid_oracle.py by closed forms of the
 stencils on trigonometric fields, brute-force loops on tiny grids, the
 discrete divergence of the corrected face velocities, uniform-flow
-preservation and the Taylor-Green vortex (decay rate, pressure, second-order
-convergence in space, at least second order in time).
+preservation, the Taylor-Green vortex (decay rate, pressure, second-order
+convergence in space) and first-order convergence in time on a nonlinear
+flow (the projection as printed is non-incremental).
 """
 from __future__ import annotations
 
@@ -44,7 +45,7 @@ import numpy as np
 
 from . import oracle as O
 
-# Rai-Moin low-storage RK3 (Sec. 2.2.1): alpha_k, gamma_k, zeta_k
+# the low-storage RK3 of Rai and Moin that Sec. 2.1 names: alpha_k, gamma_k, zeta_k (their published values)
 ALPHA = (4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0)
 GAMMA = (8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0)
 ZETA = (0.0, -17.0 / 60.0, -5.0 / 12.0)

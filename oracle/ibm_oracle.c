@@ -445,7 +445,7 @@ long ora_touched_count(int width, long nx, long ny, long nz, double h, long np,
  * Returns 0, or -1 on allocation failure.
  * Parity: pinned by the single-marker closed form, the dense linear-algebra
  * recursion, the no-op cases and the load identities (tests). */
-/* Forcing loop of Sec. 2.2.2 with some markers left out of f_IBM (Sec. 2.2.6):
+/* Forcing loop of Sec. 2.2.2 with some markers left out of f_IBM (Sec. 2.2.5):
  * disabled[m] != 0 (markers in particle-then-l order; NULL = none) gives
  * marker m the force F_m = 0 in every iteration, so it neither spreads nor adds
  * to the loads.  The slip is still reported over all markers. */
@@ -539,7 +539,7 @@ static uint64_t ora_splitmix64(uint64_t x)
  * generator's published outputs). */
 uint64_t ora_splitmix64_out(uint64_t x) { return ora_splitmix64(x); }
 
-/* Marker exclusion near contact, Sec. 2.2.6 (reading).  For every pair p < q
+/* Marker exclusion near contact, Sec. 2.2.5 (reading).  For every pair p < q
  * of the scene whose surface gap zeta = |x_q - x_p| - a_p - a_q (minimum
  * image) is below 2 eps_sep, one particle of the pair is chosen at random: with
  * i < j the pair's ids (ids[p], ids[q], or p, q when ids is NULL),

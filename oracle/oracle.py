@@ -220,19 +220,19 @@ def backward(u0, x_p, u_p, om_p, d_p, grad_u_out, h=1.0, n_forcing=3, width=3):
 
 
 def mean_force(f) -> np.ndarray:
-    """Grid-pass mean IBM force, Sec. 2.2.5 Eq. (fe_IBM): the negated average
+    """Grid-pass mean IBM force, Sec. 2.2.4 Eq. (fe_IBM): the negated average
     of f_IBM over all N_i N_j N_k cells, per component.  f: [3][nz][ny][nx]."""
     f = _f64(f)
     return -f.reshape(3, -1).sum(axis=1) / float(f[0].size)
 
 
 def eps_sep(width=3, h=1.0) -> float:
-    """Threshold separation of Sec. 2.2.6: 1.5h for the three-point kernel, 2h for four."""
+    """Threshold separation of Sec. 2.2.4: 1.5h for the three-point kernel, 2h for four."""
     return (2.0 if width == 4 else 1.5) * h
 
 
 def contact_exclusion(dims, x_p, d_p, h=1.0, eps=None, seed=0, ids=None, width=3) -> np.ndarray:
-    """Markers left out of f_IBM near contact (Sec. 2.2.6, reading in
+    """Markers left out of f_IBM near contact (Sec. 2.2.5, reading in
     ora_contact_exclusion): bool [n_markers], particle-then-l order."""
     nx, ny, nz = dims
     x_p = _f64(x_p, (-1, 3))

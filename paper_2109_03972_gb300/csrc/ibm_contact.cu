@@ -1,4 +1,4 @@
-// Marker exclusion near contact, Sec. 2.2.6.
+// Marker exclusion near contact, Sec. 2.2.5.
 //
 // Markers are left out of f_IBM where two particles come closer than the
 // forcing can resolve: for every pair (p, q) of a scene whose surface gap

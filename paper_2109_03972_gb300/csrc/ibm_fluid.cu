@@ -1,6 +1,6 @@
-// Collocated fractional-step fluid solver of the modified method (Sec. 2.2.3
-// "Pressure-momentum coupling on a collocated grid", Sec. 2.2.4-2.2.5 and the
-// steps (a)-(i) of Eq. fluid-solver) on one triply periodic grid.  The state
+// Collocated fractional-step fluid solver of the modified method (Sec. 2.2.1
+// "Pressure-momentum coupling on a collocated grid"; Sec. 2.2.4, the steps
+// (a)-(i) of Eq. fluid-solver) on one triply periodic grid.  The state
 // and every result are FP64; the multigrid corrections inside the solves are
 // FP32 (see the multigrid section).
 //
@@ -67,7 +67,7 @@ constexpr int kFlThreads = 256;
 constexpr int kCgThreads = 1024;
 constexpr long long kCoarseMax = 32768;
 
-// RK3 coefficients of Rai and Moin (Sec. 2.2.1)
+// RK3 coefficients of the Rai and Moin scheme that Sec. 2.1 names (their published values)
 constexpr double kAlpha[3] = {4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0};
 constexpr double kGamma[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 constexpr double kZeta[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};

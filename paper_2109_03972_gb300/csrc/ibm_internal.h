@@ -122,7 +122,7 @@ struct ibm_ctx {
     // collision models and particle sub-steps (ibm_collision.cu)
     void *col = nullptr;
 
-    // marker exclusion near contact (ibm_contact.cu, Sec. 2.2.6)
+    // marker exclusion near contact (ibm_contact.cu, Sec. 2.2.5)
     void *ct = nullptr;
     int ct_enable = 0;
     double ct_eps = 0.0;

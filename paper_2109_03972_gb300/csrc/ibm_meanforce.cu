@@ -1,4 +1,4 @@
-// Mean IBM force over the grid, Sec. 2.2.5 Eq. (fe_IBM):
+// Mean IBM force over the grid, Sec. 2.2.4 Eq. (fe_IBM):
 //   fbar = -(1 / (N_i N_j N_k)) sum_{i,j,k} f_IBM,ijk      per scene and component.
 //
 // One streaming pass over the force field: every scene's component array is

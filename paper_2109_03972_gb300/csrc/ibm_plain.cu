@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kBlock) k_plain_interp(
                 }
             }
             T e[3];
-            // a marker left out near contact (Sec. 2.2.6) has F = 0
+            // a marker left out near contact (Sec. 2.2.5) has F = 0
             const long long mk = (long long)Pp.moff + l;
             const bool off = dis && ((dis[mk >> 5] >> (mk & 31)) & 1u);
 #pragma unroll

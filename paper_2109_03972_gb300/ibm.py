@@ -292,7 +292,7 @@ class Context:
         return dict(zip(("Iu", "Ir", "V"), out))
 
     def set_contact_exclusion(self, enable=True, eps_sep=0.0, seed=0):
-        """Leave markers out of f_IBM near contact (Sec. 2.2.6); eps_sep = 0: the paper's value."""
+        """Leave markers out of f_IBM near contact (Sec. 2.2.5); eps_sep = 0: the paper's value."""
         self._check(self.L.ibm_set_contact_exclusion(self.h, int(enable), float(eps_sep),
                                                      int(seed) & (2 ** 64 - 1)))
 
@@ -397,7 +397,7 @@ class FluidFields:
 
 
 class Fluid:
-    """ibm_fluid: the collocated fractional-step solver of Sec. 2.2.3-2.2.5 on
+    """ibm_fluid: the collocated fractional-step solver of Sec. 2.2.1 and 2.2.4 on
     one periodic grid (FP64), on a CUDA stream (torch's current by default)."""
 
     def __init__(self, dims, h=1.0, nu=0.01, theta=1.0, rtol=0.0, max_cycles=0, profile=False,

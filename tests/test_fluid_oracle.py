@@ -1,4 +1,4 @@
-"""Pins of the fluid-solver oracle (Sec. 2.2.3-2.2.5, Eq. fluid-solver), CPU
+"""Pins of the fluid-solver oracle (Sec. 2.2.1 and 2.2.4, Eq. fluid-solver), CPU
 only.  Each pin checks the oracle against something other than its own
 formulas:
 

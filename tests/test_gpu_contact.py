@@ -1,4 +1,4 @@
-"""GPU parity of marker exclusion near contact (Sec. 2.2.6) against the oracle.
+"""GPU parity of marker exclusion near contact (Sec. 2.2.5) against the oracle.
 
 The set of markers left out is index work decided by FP64 distances: both sides
 compute the same distances in FP64 without contraction, so the bitmaps must

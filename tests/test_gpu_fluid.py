@@ -1,4 +1,4 @@
-"""GPU parity of the collocated fractional-step fluid solver (Sec. 2.2.3-2.2.5,
+"""GPU parity of the collocated fractional-step fluid solver (Sec. 2.2.1 and 2.2.4,
 steps (a)-(i) of Eq. fluid-solver) with the FP64 oracle, through the C ABI.
 
 The oracle solves the implicit viscous step and the Poisson equation exactly

@@ -1,4 +1,4 @@
-"""GPU parity of the grid-pass mean IBM force (Sec. 2.2.5, Eq. fe_IBM) against
+"""GPU parity of the grid-pass mean IBM force (Sec. 2.2.4, Eq. fe_IBM) against
 the oracle's plain definition on the same fields.
 
 Tolerances: the oracle sums in FP64.  The library adds FP32 fields in groups

@@ -567,7 +567,7 @@ def test_threaded_oracle_is_bitwise_serial(oracle):
         assert np.array_equal(a[k], b[k]), k
 
 
-# ----------------------------------------------- mean force (Sec. 2.2.5)
+# ----------------------------------------------- mean force (Sec. 2.2.4)
 
 def test_mean_force_closed_forms(oracle):
     # Eq. (fe_IBM): minus the cell average, per component, over N_i N_j N_k cells.
@@ -596,7 +596,7 @@ def test_mean_force_equals_minus_summed_loads(oracle):
     assert np.allclose(fbar * n, -out["F"].sum(0), rtol=1e-11, atol=1e-9)
 
 
-# --------------------------------------- marker exclusion near contact (Sec. 2.2.6)
+# --------------------------------------- marker exclusion near contact (Sec. 2.2.5)
 
 def _pair(rng, d1, d2, zeta, dims=(96, 96, 96)):
     v = rng.normal(size=3)
