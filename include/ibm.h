@@ -227,7 +227,9 @@ ibm_status ibm_particle_inertia(ibm_ctx *ctx, void *const *u_ptrs, double *Iu, d
  * z is set, else particle i.
  * enable: 1 on, 0 off.  eps_sep: the threshold separation in physical units;
  *   0 takes the paper's value, 1.5 h for kernel_width 3 and 2 h for 4.
- * Needs spread_mode PLAIN and requires_grad = 0 (INVALID_ARG otherwise).
+ * Every spread mode (the shared-memory cluster kernel and its plain fallback
+ * skip those markers the same way); needs requires_grad = 0 (INVALID_ARG
+ * otherwise: there is no adjoint of the exclusion).
  * Errors: INVALID_ARG.  A step whose pairs in reach exceed 32 per particle
  * reports CAPACITY at the next error check. */
 ibm_status ibm_set_contact_exclusion(ibm_ctx *ctx, int enable, double eps_sep, uint64_t seed);

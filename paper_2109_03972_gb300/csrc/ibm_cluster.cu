@@ -568,6 +568,7 @@ struct KParams {
     const int2 *batches;
     float4 *grec;   // per CTA: 2 * TPB * KM float4 (records a, then b)
     int *cnt, *fb_list, *err;
+    const unsigned *dis;   // markers left out near contact (Sec. 2.2.5): one bit per global marker, or NULL
     double *FD, *TD;
     int n_forcing, smem_bytes, max_rows;
     float finv;
@@ -984,7 +985,13 @@ __device__ __forceinline__ void forcing_rec(const KParams &prm, const Batch &bt,
             float em = 0.f;
             const float4 a = ra[m];
             const PS &s = s_ps[s_chunk[m >> 5]];
-            if (__float_as_uint(a.w) != kNoMarker) {
+            bool live = __float_as_uint(a.w) != kNoMarker;
+            if (live && prm.dis) {
+                // a marker left out near contact (Sec. 2.2.5) keeps e = 0: no force, nothing spread
+                const long long mk = (long long)s.P.moff + (m - s.mstart);
+                live = !((prm.dis[mk >> 5] >> (mk & 31)) & 1u);
+            }
+            if (live) {
                 const uint4 r = rb[m];
                 const unsigned s8 = __float_as_uint(a.w);
                 float w[3][3];
@@ -1666,6 +1673,11 @@ static constexpr int kTuneSteps = 4;
 ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, void *const *f_out) {
     ibm_status st = ensure_field_ptrs(ctx, u_ptrs, f_out);
     if (st != IBM_OK) return st;
+    if (ctx->ct_enable) {
+        // markers left out near contact (Sec. 2.2.5): the bitmap of this step's particle set
+        st = contact_exclusion(ctx);
+        if (st != IBM_OK) return st;
+    }
     st = cluster_alloc(ctx);
     if (st != IBM_OK) return st;
     ClusterScratch *S = reinterpret_cast<ClusterScratch *>(ctx->cl);
@@ -1739,6 +1751,7 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prm.cnt = S->cnt;
     prm.fb_list = S->fb_list;
     prm.err = ctx->err_d;
+    prm.dis = contact_bits(ctx);
     prm.FD = ctx->FD;
     prm.TD = ctx->TD;
     prm.n_forcing = ctx->cfg.n_forcing;

@@ -350,8 +350,6 @@ void contact_free(ibm_ctx *ctx) {
 extern "C" ibm_status ibm_set_contact_exclusion(ibm_ctx *ctx, int enable, double eps_sep, uint64_t seed) {
     if (!ctx) return IBM_ERR_INVALID_ARG;
     if (enable) {
-        if (ctx->cfg.spread_mode != IBM_SPREAD_PLAIN)
-            return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "marker exclusion needs spread_mode PLAIN");
         if (ctx->cfg.requires_grad)
             return ibm_fail(ctx, IBM_ERR_INVALID_ARG, "marker exclusion has no adjoint (requires_grad)");
         if (!(eps_sep >= 0.0) || !std::isfinite(eps_sep))

@@ -1028,7 +1028,7 @@ static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, co
         CK(cudaMemsetAsync(ctx->fb_cm, 0, 3 * (size_t)ctx->cap_p * sizeof(unsigned), ctx->stream), "zero maxima");
         k_plain_interp<float, true><<<grid, kBlock, 0, ctx->stream>>>(
             ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, u32,
-            reinterpret_cast<float *>(ctx->ebuf), ctx->cbuf, pcl, ctx->fb_cm);
+            reinterpret_cast<float *>(ctx->ebuf), ctx->cbuf, pcl, ctx->fb_cm, contact_bits(ctx));
         k_fb_convert<true><<<grid, kBlock, 0, ctx->stream>>>(ctx->pinfo, plist, n_list_d, ctx->tmpl64, ctx->tmpl32,
                                                              ctx->dims_d, ctx->cell_off_d, u32, pcl, ctx->fb_cm,
                                                              ctx->fb_own, first ? ctx->fb_bits : nullptr, ctx->err_d);
@@ -1042,8 +1042,8 @@ static ibm_status plain_iteration(ibm_ctx *ctx, const int *plist, int n_list, co
         ctx->launches += 4;
         return IBM_OK;
     }
-    // markers left out near contact: only on the whole-particle plain path
-    const unsigned *dis = plist ? nullptr : contact_bits(ctx);
+    // markers left out near contact (global marker bits, so any particle list)
+    const unsigned *dis = contact_bits(ctx);
     if (ctx->cfg.kernel_width == 4) {
         k_plain_interp<T, false, 4><<<grid, kBlock, 0, ctx->stream>>>(
             ctx->pinfo, plist, n_list, n_list_d, ctx->tmpl64, ctx->tmpl32, ctx->up, ctx->om, ctx->dims_d, uf,

@@ -64,8 +64,8 @@ def _borderline(O, dims, x_p, d_p, width, eps=None):
     return near
 
 
-def _run(sc, u0, prec, width=3, graph=False, steps=1):
-    ctx = gpu_context([sc.dims], sc.n_p, prec, ibm.IBM_SPREAD_PLAIN, width=width)
+def _run(sc, u0, prec, width=3, graph=False, steps=1, mode=ibm.IBM_SPREAD_PLAIN):
+    ctx = gpu_context([sc.dims], sc.n_p, prec, mode, width=width)
     if graph:
         ctx = ibm.Context(ibm.Config(**{**ctx.cfg.__dict__, "use_graph": True}))
     ctx.set_contact_exclusion(True, 0.0, SEED)
@@ -147,6 +147,39 @@ def test_exclusion_multi_scene_ids(oracle_mod):
     assert ra.any() and rb.any()
 
 
+@pytest.mark.parametrize("mode", [ibm.IBM_SPREAD_CLUSTER, ibm.IBM_SPREAD_DETERMINISTIC])
+def test_exclusion_on_the_cluster_kernel_matches_oracle(oracle_mod, mode):
+    # the shared-memory cluster kernel (and its plain fallback) leave the same markers out
+    sc = _dense_scene()
+    u0 = sc.field()
+    ctx, [(u, loads, mask, n)] = _run(sc, u0, ibm.IBM_FP32, mode=mode)
+    ref = _compare_mask(oracle_mod, sc, mask)
+    assert ref.sum() > 50
+    st = ctx.stats()
+    assert st["clusters_smem"] > 0                      # the step ran the shared-memory kernel
+    o = oracle_mod.forcing_step(u0, sc.x_p, sc.u_p, sc.omega_p, sc.d_p, disabled=ref)
+    scale = np.abs(u0).max()
+    assert np.abs(u - o["u"]).max() <= 2e-5 * scale
+    assert np.abs(loads["F"] - o["F"]).max() <= 1e-4 * np.abs(o["Fabs"]).sum()
+    plain = oracle_mod.forcing_step(u0, sc.x_p, sc.u_p, sc.omega_p, sc.d_p)
+    assert np.abs(plain["u"] - o["u"]).max() > 100 * 2e-5 * scale
+
+
+def test_exclusion_on_cluster_fallback_and_graph(oracle_mod):
+    # a dense 48^3 box of the batched workload (27 spheres, one cluster of about 17,700 markers) runs its
+    # big cluster on the plain fallback; the step replayed from a graph
+    sc = synth.workload("batched").scenes[123]
+    u0 = sc.field()
+    ctx, out = _run(sc, u0, ibm.IBM_FP32, mode=ibm.IBM_SPREAD_DETERMINISTIC, graph=True, steps=3)
+    assert ctx.stats()["markers_fallback"] > 0
+    u, loads, mask, n = out[0]
+    ref = _compare_mask(oracle_mod, sc, mask)
+    o = oracle_mod.forcing_step(u0, sc.x_p, sc.u_p, sc.omega_p, sc.d_p, disabled=ref)
+    assert np.abs(u - o["u"]).max() <= 2e-5 * np.abs(u0).max()
+    for u2, _, m2, _ in out[1:]:
+        assert np.array_equal(m2, mask) and np.array_equal(u2, u)   # deterministic mode: bit for bit
+
+
 def test_exclusion_graph_replay_and_config_errors(oracle_mod):
     sc = _dense_scene()
     u0 = sc.field()
@@ -156,10 +189,6 @@ def test_exclusion_graph_replay_and_config_errors(oracle_mod):
         assert np.array_equal(mask, out[0][2])
         assert np.abs(u - out[0][0]).max() <= 1e-12 * np.abs(u0).max()
     assert ref.any()
-    for mode in (ibm.IBM_SPREAD_CLUSTER, ibm.IBM_SPREAD_DETERMINISTIC):
-        c = gpu_context([sc.dims], sc.n_p, ibm.IBM_FP32, mode)
-        with pytest.raises(ibm.IBMError):
-            c.set_contact_exclusion(True)
     c = gpu_context([sc.dims], sc.n_p, ibm.IBM_FP64, ibm.IBM_SPREAD_PLAIN, requires_grad=True)
     with pytest.raises(ibm.IBMError):
         c.set_contact_exclusion(True)
