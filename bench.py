@@ -602,15 +602,16 @@ def fluid_leg(W, parts, dims, u0, stream, peaks):
 
 
 def exclusion_leg(cfg, us, u_host, W, parts, dims, stream):
-    """Marker exclusion near contact (Sec. 2.2.5) costs: the FP32 plain step of
-    the same workload with and without it (eager, CUDA events, 10 steps each)."""
+    """Marker exclusion near contact (Sec. 2.2.5) costs: the benchmark's step (same
+    spread mode, the cluster kernel for the shared-memory modes) with and without
+    it (eager, CUDA events, 10 steps each)."""
     import torch
     from paper_2109_03972_gb300 import ibm
     x, up, om, d, rho, so = parts
     res = {}
     for on in (False, True):
-        c = ibm.Context(ibm.Config(**{**cfg.__dict__, "spread_mode": ibm.IBM_SPREAD_PLAIN, "use_graph": False,
-                                      "threads_per_block": 0, "profile": False}), stream)
+        c = ibm.Context(ibm.Config(**{**cfg.__dict__, "use_graph": False, "threads_per_block": 0,
+                                      "profile": False}), stream)
         if on:
             c.set_contact_exclusion(True, 0.0, 2109)
         c.set_particles(x, up, om, d, rho, so if len(dims) > 1 else None)
@@ -628,7 +629,9 @@ def exclusion_leg(cfg, us, u_host, W, parts, dims, stream):
         if on:
             res["markers_disabled"] = c.disabled_markers()[1]
         del c
-    return {"path": "plain FP32", "ms_per_step_without": res["without"], "ms_per_step_with": res["with"],
+    mode = {ibm.IBM_SPREAD_CLUSTER: "cluster", ibm.IBM_SPREAD_DETERMINISTIC: "deterministic",
+            ibm.IBM_SPREAD_PLAIN: "plain"}[cfg.spread_mode]
+    return {"path": f"FP32 {mode}", "ms_per_step_without": res["without"], "ms_per_step_with": res["with"],
             "overhead_ms": res["with"] - res["without"], "markers_disabled": res["markers_disabled"],
             "eps_sep_h": 1.5}
 

@@ -371,13 +371,11 @@ __global__ void __launch_bounds__(kFlThreads) k_mg_rbgs(int nx, int ny, int nz, 
     const int t = tid();
     const int X0 = blockIdx.x * kBx, Y0 = blockIdx.y * kBy;
     const int Z0 = blockIdx.z * kZc, Z1 = min(Z0 + kZc, nz);
-    const long long plane = (long long)nx * ny;
+    const int plane = nx * ny;            // cells < 2^31 (checked at creation)
     const T inv = T(1) / (a0 + T(6) * beta);
-    // the (at most 2) region cells this thread stages and may update as red cells:
-    // plane offsets of their periodic images, ring-1 membership and parity
-    long long goff[2];
-    bool have[2], ring1[2];
-    int par[2];
+    // the (at most 2) region cells this thread stages: in-plane offsets of their periodic images
+    int goff[2];
+    bool have[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int e = t + r * kFlThreads;
@@ -386,27 +384,26 @@ __global__ void __launch_bounds__(kFlThreads) k_mg_rbgs(int nx, int ny, int nz, 
         int gx = X0 - 2 + rx, gy = Y0 - 2 + ry;
         gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
         gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-        goff[r] = (long long)gy * nx + gx;
-        ring1[r] = have[r] && rx >= 1 && rx <= kRx - 2 && ry >= 1 && ry <= kRy - 2;
-        par[r] = (rx + ry) & 1;
+        goff[r] = gy * nx + gx;
     }
-    // this thread's tile cell (region position tx + 2, ty + 2) and whether it is inside the box
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const bool inside = X0 + tx < nx && Y0 + ty < ny;
-    const int rc = (ty + 2) * kRx + tx + 2;
-    const int tpar = (tx + ty) & 1;
+    // red cells of a plane on the tile plus its ring of 1 (34 x 10 cells, 17 red per row): thread t < 170
+    // takes row 1 + t / 17, the (t % 17)-th red cell of it; black cells of the tile (32 x 8, 16 per row):
+    // thread t < 128 takes row t / 16, the (t % 16)-th black cell of it
+    constexpr int kRedPerRow = (kRx - 2) / 2, kRed = kRedPerRow * (kRy - 2), kBlackPerRow = kBx / 2;
+    const int red_ry = 1 + t / kRedPerRow, red_i = t % kRedPerRow;
+    const int blk_ty = t / kBlackPerRow, blk_i = t % kBlackPerRow;
     auto wrapz = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
     // the next plane's values are loaded into registers one iteration ahead, so
     // that their latency overlaps the current plane's updates
     T vx[2] = {T(0), T(0)}, vb[2] = {T(0), T(0)};
     auto fetch = [&](int zq) {
-        const long long zo = (long long)wrapz(zq) * plane;
-        const long long bo = (long long)wrapz(zq - 1) * plane;
+        const T *px = xin + wrapz(zq) * plane;
+        const T *pb = b + wrapz(zq - 1) * plane;
 #pragma unroll
         for (int r = 0; r < 2; ++r)
             if (have[r]) {
-                vx[r] = xin[zo + goff[r]];
-                if (zq >= Z0) vb[r] = b[bo + goff[r]];
+                vx[r] = px[goff[r]];
+                if (zq >= Z0) vb[r] = pb[goff[r]];
             }
     };
     fetch(Z0 - 2);
@@ -425,31 +422,34 @@ __global__ void __launch_bounds__(kFlThreads) k_mg_rbgs(int nx, int ny, int nz, 
         __syncthreads();
         // red cells of plane p = zp - 1 on the tile and its ring of 1
         const int p = zp - 1;
-        if (p >= Z0 - 1 && p <= Z1) {
+        if (p >= Z0 - 1 && p <= Z1 && t < kRed) {
             T *cx = sx[(it + 4) % 5];
             const T *dn = sx[(it + 3) % 5], *up = sx[it % 5];
             const T *cb = sb[(it + 1) % 3];
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int e = t + r * kFlThreads;
-                if (ring1[r] && ((par[r] + p) & 1) == 0) {
-                    const T sum = cx[e + 1] + cx[e - 1] + cx[e + kRx] + cx[e - kRx] + up[e] + dn[e];
-                    cx[e] = (cb[e] + beta * sum) * inv;
-                }
-            }
+            const int e = red_ry * kRx + 1 + ((red_ry + p + 1) & 1) + 2 * red_i;
+            const T sum = cx[e + 1] + cx[e - 1] + cx[e + kRx] + cx[e - kRx] + up[e] + dn[e];
+            cx[e] = (cb[e] + beta * sum) * inv;
         }
         __syncthreads();
-        // black cells of plane q = zp - 2 on the tile, and the tile written out
+        // black cells of plane q = zp - 2 on the tile, and the tile written out: each of the first 128
+        // threads writes the black cell it updates and one red cell of the same row (final since the
+        // previous iteration), so no barrier separates the update from the write
         const int q = zp - 2;
-        if (q >= Z0 && q <= Z1 - 1) {
+        if (q >= Z0 && q <= Z1 - 1 && t < kBx * kBy / 2) {
             T *cx = sx[(it + 3) % 5];
             const T *dn = sx[(it + 2) % 5], *up = sx[(it + 4) % 5];
             const T *cb = sb[it % 3];
-            if (((tpar + q) & 1) == 1) {
-                const T sum = cx[rc + 1] + cx[rc - 1] + cx[rc + kRx] + cx[rc - kRx] + up[rc] + dn[rc];
-                cx[rc] = (cb[rc] + beta * sum) * inv;
+            const int cb_x = ((blk_ty + q + 1) & 1) + 2 * blk_i;     // black column in the tile
+            const int cr_x = ((blk_ty + q) & 1) + 2 * blk_i;         // red column in the tile
+            const int e = (blk_ty + 2) * kRx + 2 + cb_x;
+            const T sum = cx[e + 1] + cx[e - 1] + cx[e + kRx] + cx[e - kRx] + up[e] + dn[e];
+            const T v = (cb[e] + beta * sum) * inv;
+            cx[e] = v;
+            if (Y0 + blk_ty < ny) {
+                T *row = xout + q * plane + (Y0 + blk_ty) * nx + X0;
+                if (X0 + cb_x < nx) row[cb_x] = v;
+                if (X0 + cr_x < nx) row[cr_x] = cx[(blk_ty + 2) * kRx + 2 + cr_x];
             }
-            if (inside) xout[(long long)q * plane + (long long)(Y0 + ty) * nx + X0 + tx] = cx[rc];
         }
     }
 }
