@@ -329,13 +329,15 @@ ibm_status ibm_contact_history(ibm_ctx *ctx, int64_t *n_pairs, int32_t *p, int32
  * = NULL to query it.  Synchronises.  Errors: STATE, INVALID_ARG, CUDA. */
 ibm_status ibm_marker_bases(ibm_ctx *ctx, int64_t *base_out, int64_t *n_markers);
 
-/* Diagnostics of the last forcing step (HOST int64[10], synchronises):
+/* Diagnostics of the last forcing step (HOST int64[12], synchronises):
  * [0] markers, [1] particle clusters, [2] clusters on the shared-memory path,
  * [3] markers on the plain fallback path, [4] largest cluster held in shared
  * memory (touched cells), [5] distinct touched cells on the shared-memory
  * path, [6] kernel launches per step, [7] threads per block of the cluster
  * kernel, [8] clusters run one velocity component at a time, [9] candidate
- * particle pairs tested.  Entries [1]-[5], [7]-[9] are 0 in PLAIN mode. */
+ * particle pairs tested, [10] clusters and [11] markers on the thread-block-
+ * cluster path (IBM_PATH_DSMEM).  Entries [1]-[5], [7]-[11] are 0 in PLAIN
+ * mode. */
 ibm_status ibm_step_stats(ibm_ctx *ctx, int64_t *stats);
 
 /* Code paths of a particle cluster in the last forcing step, as bits of
@@ -346,7 +348,10 @@ enum {
     IBM_PATH_ONE_COMPONENT = 4,   /* ... one velocity component at a time         */
     IBM_PATH_SPARSE_ROWS = 8,     /* ... with the sparse row table                */
     IBM_PATH_PERIODIC = 16,       /* the cluster's box wraps around the period    */
-    IBM_PATH_FALLBACK = 32        /* the plain path (global atomics)              */
+    IBM_PATH_FALLBACK = 32,       /* the plain path (global atomics)              */
+    IBM_PATH_DSMEM = 64           /* too large for one SM: the distributed shared
+                                     memory of a thread-block cluster of 8 or 16
+                                     CTAs holds its box                         */
 };
 
 /* Diagnostics of the cluster modes (CLUSTER, DETERMINISTIC).  Particles whose

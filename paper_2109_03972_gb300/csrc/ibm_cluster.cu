@@ -28,6 +28,7 @@
 // markers can have base cells within 2 of each other) are tested exactly
 // (some marker pair with |b_l - b_l'|_inf <= 2), and joined by a lock-free
 // union-find.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -65,6 +66,13 @@ enum {
     C_FBMARK,     // markers on the fallback path
     C_ONECOMP,    // clusters run one velocity component at a time
     C_NBATCH,     // shared-memory work items (batches of clusters)
+    C_NBIG,       // clusters on the distributed-shared-memory path (both sizes)
+    C_NBIG8,      // ... of them on 8-CTA thread-block clusters, and their work counter
+    C_WORK8,
+    C_NBIG16,     // ... on 16-CTA thread-block clusters, and their work counter
+    C_WORK16,
+    C_BIGMARK,    // markers on that path
+    C_NFB2,       // particles left on the plain fallback
     C_COUNT
 };
 
@@ -86,6 +94,18 @@ struct ClusterScratch {
     float4 *grec = nullptr;          // marker records of batches kept in global memory
     size_t grec_bytes = 0;
     int smem_bytes = 0, cap_c = 0, tpb = 0, kmax = 0, det = -1;
+    // clusters too large for one SM, held in the distributed shared memory of a
+    // thread-block cluster: the work list, a flag per cluster, the plain
+    // fallback's remaining particles, marker records and chunk sums per slot
+    int *big_list = nullptr, *big_flag = nullptr, *fb_list2 = nullptr;
+    uint4 *big_rec = nullptr;
+    float *big_part = nullptr;
+    int *big_wl = nullptr;
+    size_t big_rec_bytes = 0, big_part_bytes = 0, big_wl_bytes = 0;
+    // thread-block-cluster path: configured (-1: not yet), clusters of 8 and 16 CTAs that run at once
+    // (0: that size cannot run), dense cells per CTA
+    int big_k = -1, big_grid8 = 0, big_grid16 = 0, big_cells = 0, big_det = -1, big_smem = 0;
+    int *big_list16 = nullptr;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -1553,9 +1573,13 @@ void cluster_free(ibm_ctx *ctx) {
     int *ptrs[] = {S->scene_bin_off, S->scene_nb, S->bin_cnt, S->bin_start, S->bin_cur, S->bin_items,
                    S->parent, S->cand, S->cnt, S->root_flag, S->cid, S->pcl, S->poff, S->cl_np, S->cl_nm,
                    S->cl_first, S->cl_cur, S->cl_box, S->cl_plist, S->cl_bkt, S->bkt_cnt, S->bkt_start,
-                   S->order, S->fb_list, S->nm_ord, S->cum, S->cl_scene, S->cl_path};
+                   S->order, S->fb_list, S->nm_ord, S->cum, S->cl_scene, S->cl_path, S->big_list,
+                   S->big_flag, S->fb_list2, S->big_list16};
     for (int *p : ptrs)
         if (p) cudaFree(p);
+    if (S->big_rec) cudaFree(S->big_rec);
+    if (S->big_part) cudaFree(S->big_part);
+    if (S->big_wl) cudaFree(S->big_wl);
     if (S->batches) cudaFree(S->batches);
     if (S->grec) cudaFree(S->grec);
     if (S->tot) cudaFree(S->tot);
@@ -1616,7 +1640,8 @@ static ibm_status cluster_alloc(ibm_ctx *ctx) {
         const int cp = std::max(ctx->cap_p, np);
         int **arrs[] = {&S->bin_items, &S->parent, &S->root_flag, &S->cid, &S->pcl, &S->cl_np, &S->cl_nm,
                         &S->cl_first, &S->cl_cur, &S->cl_plist, &S->cl_bkt, &S->order, &S->fb_list,
-                        &S->nm_ord, &S->cum, &S->cl_scene, &S->cl_path};
+                        &S->nm_ord, &S->cum, &S->cl_scene, &S->cl_path, &S->big_list, &S->big_flag,
+                        &S->fb_list2, &S->big_list16};
         for (int **p : arrs) CK(dev_realloc(p, (size_t)(cp + 1) * sizeof(int)), "alloc cluster scratch");
         CK(dev_realloc(&S->batches, (size_t)(cp + 1) * sizeof(int2)), "alloc batch list");
         CK(dev_realloc(&S->poff, 3 * (size_t)cp * sizeof(int)), "alloc cluster scratch");
@@ -1664,6 +1689,600 @@ static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams
 }
 
 // marker slots per thread of the cluster kernel's recomputing path, and
+// ------------------------------------------ clusters held in distributed shared memory
+// A cluster whose touched cells exceed one SM's shared memory (the dense
+// boxes of small periodic scenes, long chains) would otherwise run the plain
+// path with global atomics.  When its stencil box fits the shared memory of a
+// thread-block cluster of kBigK CTAs (one per SM), it runs here instead: the
+// box is cut into z slabs, one per CTA, held densely (3 FP32 components per
+// cell plus a touched-cell bit), and every CTA reaches the other slabs through
+// distributed shared memory.  Per forcing iteration: interpolation of the
+// CTA's share of the markers (loads from any slab), the cluster-wide fixed-
+// point scale (deterministic mode: the same maxima as the plain fallback),
+// the CTA's own cells converted, spreading by shared-memory atomics into any
+// slab, cells converted back, with cluster barriers between the phases.  HBM
+// sees each touched cell once per step, as on the one-SM path.  The work list
+// is taken persistently, one cluster at a time per thread-block cluster.
+constexpr int kBigT = 1024, kBigKR = 4, kBigMaxP = 512;
+
+struct BigParams {
+    const PInfo *P;
+    const float *t32;
+    const double *t64;
+    const int32_t *dims;
+    float *const *uf;
+    float *const *ff;
+    int *cnt, *err;
+    const int *big_list, *cl_np, *cl_first, *cl_plist, *cl_box, *cl_scene;
+    int c_n, c_work;     // indices in cnt of the list's length and of its work counter
+    const unsigned *dis;
+    double *FD, *TD;
+    uint4 *rec;          // marker records, two per marker, K * kBigT * kBigKR markers per thread-block cluster
+    float *part;         // per marker: e and its load terms summed over the iterations (9 floats)
+    int *wlist;          // per thread-block cluster: its markers grouped by owning CTA
+    int n_forcing, cap_cells;
+    float finv;
+};
+
+struct BigHdr {
+    int c, np, nm, wrap;
+    int lo[3], B[3], n[3];
+    int slab, z0, z1, ncell;     // this CTA's slab [z0, z1) and its cells
+    int scene;
+};
+
+__device__ __forceinline__ int big_mod(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Box-relative cell of stencil start s (per axis) plus d, modulo the period
+// along the wrapped axes (their box is the whole period).
+__device__ __forceinline__ int big_ax(int s, int d, int B, bool wrapped) {
+    int v = s + d;
+    if (wrapped && v >= B) v -= B;
+    return v;
+}
+
+template <int K, bool DET>
+__global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char big_dyn[];
+    __shared__ BigHdr H;
+    __shared__ int s_item;
+    __shared__ int s_pid[kBigMaxP];
+    __shared__ int s_pref[kBigMaxP + 1];
+    __shared__ unsigned s_max[2][3];        // rank 0's copy: the cluster's maxima of an iteration (two buffers)
+    __shared__ float s_red[3][kBigT / 32];
+    __shared__ int s_own, s_cur;            // markers this CTA owns (their stencil's middle plane is in its slab)
+    __shared__ int s_off[K + 1];            // offsets of every CTA's markers in the work list
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int rank = (int)cl.block_rank();
+    const int slot = blockIdx.x / K;
+    const int cap = bp.cap_cells;
+    const int mcap = K * kBigT * kBigKR;
+    float *cells = reinterpret_cast<float *>(big_dyn);
+    unsigned *tb = reinterpret_cast<unsigned *>(big_dyn + 3ull * cap * sizeof(float));
+    uint4 *rec = bp.rec + (size_t)slot * mcap * 2;     // two records per marker of the item
+    float *eb = bp.part + (size_t)slot * mcap * 9;     // per marker: e (3) and the load terms summed over iterations (6)
+    int *wl = bp.wlist + (size_t)slot * mcap;          // work list: markers grouped by owning CTA
+    for (;;) {
+        if (rank == 0 && tid == 0) s_item = atomicAdd(bp.cnt + bp.c_work, 1);
+        cl.sync();
+        const int item = *cl.map_shared_rank(&s_item, 0);
+        cl.sync();   // rank 0's s_item stays valid until every CTA has read it
+        if (item >= bp.cnt[bp.c_n]) break;
+        // ---- header: box (whole period along wrapped axes), particles sorted by index, marker prefix
+        if (tid == 0) {
+            const int c = bp.big_list[item];
+            H.c = c;
+            H.np = bp.cl_np[c];
+            H.scene = bp.cl_scene[c] & 0x0fffffff;
+            H.wrap = (bp.cl_scene[c] >> 28) & 7;
+            for (int k = 0; k < 3; ++k) {
+                H.n[k] = bp.dims[3 * H.scene + k];
+                const bool w = (H.wrap >> k) & 1;
+                H.lo[k] = w ? 0 : bp.cl_box[12 * c + k];
+                H.B[k] = w ? H.n[k] : bp.cl_box[12 * c + 3 + k] - bp.cl_box[12 * c + k] + 1;
+            }
+            H.slab = (H.B[2] + K - 1) / K;
+            H.z0 = min(H.B[2], rank * H.slab);
+            H.z1 = min(H.B[2], H.z0 + H.slab);
+            H.ncell = (H.z1 - H.z0) * H.B[1] * H.B[0];
+            s_own = 0;
+            s_cur = 0;
+        }
+        __syncthreads();
+        const int np = H.np;
+        for (int i = tid; i < np; i += kBigT) s_pid[i] = bp.cl_plist[bp.cl_first[H.c] + i];
+        __syncthreads();
+        int my_pid = 0, my_pos = 0;
+        if (tid < np) {
+            my_pid = s_pid[tid];
+            for (int j = 0; j < np; ++j) my_pos += s_pid[j] < my_pid;
+        }
+        __syncthreads();
+        if (tid < np) s_pid[my_pos] = my_pid;
+        __syncthreads();
+        if (tid == 0) {
+            int a = 0;
+            for (int i = 0; i < np; ++i) {
+                s_pref[i] = a;
+                a += (bp.P[s_pid[i]].nl + 31) & ~31;
+            }
+            s_pref[np] = a;
+        }
+        if (rank == 0 && tid < 6) s_max[tid / 3][tid % 3] = 0u;
+        for (int w = tid; w < (H.ncell + 31) / 32; w += kBigT) tb[w] = 0u;
+        __syncthreads();
+        const int nm = s_pref[np];
+        const int per = (((nm >> 5) + K - 1) / K) << 5;          // flat markers set up by each CTA
+        const int m0 = min(nm, rank * per), m1 = min(nm, m0 + per);
+        const int B0 = H.B[0], B1 = H.B[1], B2 = H.B[2], slab = H.slab;
+        const bool wx = H.wrap & 1, wy = (H.wrap >> 1) & 1, wz = (H.wrap >> 2) & 1;
+        cl.sync();   // bitmasks clear and counters zero everywhere
+        // ---- records of this CTA's flat markers (box-relative stencil start, fractions), touched bits,
+        // and the count of each owning CTA
+        for (int m = m0 + tid; m < m1; m += kBigT) {
+            int lo = 0, hi = np;   // particle of flat marker m
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_pref[mid] <= m) lo = mid;
+                else hi = mid;
+            }
+            const int p = s_pid[lo];
+            const int l = m - s_pref[lo];
+            const PInfo &Pp = bp.P[p];
+            bool live = l < Pp.nl;
+            if (live && bp.dis) {
+                const long long mk = (long long)Pp.moff + l;
+                live = !((bp.dis[mk >> 5] >> (mk & 31)) & 1u);
+            }
+            uint4 r0 = make_uint4(0u, 0u, 0u, 0u), r1 = make_uint4(0u, 0u, 0u, 0u);
+            if (live) {
+                int st[3];
+                float fr[3];
+                for (int c = 0; c < 3; ++c) {
+                    const int b = marker_split32(Pp, bp.t32 + 3ll * (Pp.toff + l), bp.t64 + 3ll * (Pp.toff + l), c, &fr[c]);
+                    st[c] = big_mod(b - 1 - H.lo[c], H.n[c]);
+                }
+                r0 = make_uint4((unsigned)st[0] | ((unsigned)st[1] << 10) | ((unsigned)st[2] << 20) | (1u << 31),
+                                __float_as_uint(fr[0]), __float_as_uint(fr[1]), __float_as_uint(fr[2]));
+                r1 = make_uint4((unsigned)lo, (unsigned)l, (unsigned)p, 0u);
+                for (int cz = 0; cz < 3; ++cz) {
+                    const int z = big_ax(st[2], cz, B2, wz);
+                    const int rk = z / slab;
+                    unsigned *rtb = cl.map_shared_rank(tb, rk);
+                    for (int cy = 0; cy < 3; ++cy) {
+                        const int y = big_ax(st[1], cy, B1, wy);
+                        for (int cx = 0; cx < 3; ++cx) {
+                            const int x = big_ax(st[0], cx, B0, wx);
+                            const int idx = ((z - rk * slab) * B1 + y) * B0 + x;
+                            atomicOr(rtb + (idx >> 5), 1u << (idx & 31));
+                        }
+                    }
+                }
+                atomicAdd(cl.map_shared_rank(&s_own, big_ax(st[2], 1, B2, wz) / slab), 1);
+            }
+            rec[2 * m] = r0;
+            rec[2 * m + 1] = r1;
+#pragma unroll
+            for (int q = 3; q < 9; ++q) eb[9 * m + q] = 0.f;
+        }
+        cl.sync();   // touched bits and owner counts complete
+        if (tid == 0) {
+            int a = 0;
+            for (int r = 0; r < K; ++r) {
+                s_off[r] = a;
+                a += *cl.map_shared_rank(&s_own, r);
+            }
+            s_off[K] = a;
+        }
+        __syncthreads();
+        // work list: each marker into its owner's range (order within a range is free: the loads are
+        // summed per marker index afterwards)
+        for (int m = m0 + tid; m < m1; m += kBigT) {
+            const uint4 r0 = rec[2 * m];
+            if (!(r0.x >> 31)) continue;
+            const int owner = big_ax((int)((r0.x >> 20) & 1023u), 1, B2, wz) / slab;
+            wl[s_off[owner] + atomicAdd(cl.map_shared_rank(&s_cur, owner), 1)] = m;
+        }
+        // ---- gather the touched cells of this CTA's slab
+        const float *const u0 = bp.uf[H.scene];
+        const long long ncs = (long long)H.n[0] * H.n[1] * H.n[2];
+        for (int i = tid; i < H.ncell; i += kBigT) {
+            if (!((tb[i >> 5] >> (i & 31)) & 1u)) continue;
+            const int x = i % B0, t = i / B0, y = t % B1, z = H.z0 + t / B1;
+            const long long g = ((long long)big_mod(H.lo[2] + z, H.n[2]) * H.n[1] + big_mod(H.lo[1] + y, H.n[1])) *
+                                    H.n[0] + big_mod(H.lo[0] + x, H.n[0]);
+            for (int q = 0; q < 3; ++q) cells[q * cap + i] = u0[q * ncs + g];
+        }
+        __threadfence();
+        cl.sync();   // work list and cells complete
+        const int w0 = s_off[rank], w1 = s_off[rank + 1];
+        // ---- the n_F iterations; a CTA works on the markers whose stencil's middle plane it holds, so
+        // most of their cells are its own (plain shared-memory accesses), the rest in the neighbour slabs
+        for (int it = 0; it < bp.n_forcing; ++it) {
+            float umax = 0.f, emax = 0.f, dmax = 0.f;
+            for (int i = w0 + tid; i < w1; i += kBigT) {
+                const int m = wl[i];
+                const uint4 r0 = rec[2 * m];
+                const uint4 r1 = rec[2 * m + 1];
+                const PInfo &Pp = bp.P[r1.z];
+                const int st[3] = {(int)(r0.x & 1023u), (int)((r0.x >> 10) & 1023u), (int)((r0.x >> 20) & 1023u)};
+                float w[3][3];
+                phi3_weights(__uint_as_float(r0.y), w[0]);
+                phi3_weights(__uint_as_float(r0.z), w[1]);
+                phi3_weights(__uint_as_float(r0.w), w[2]);
+                float U[3] = {0.f, 0.f, 0.f};
+                for (int cz = 0; cz < 3; ++cz) {
+                    const int z = big_ax(st[2], cz, B2, wz);
+                    const int rk = z / slab;
+                    const int zb = (z - rk * slab) * B1;
+                    auto row = [&](const float *rc) {
+                        for (int cy = 0; cy < 3; ++cy) {
+                            const int y = big_ax(st[1], cy, B1, wy);
+                            const float wyz = w[2][cz] * w[1][cy];
+                            for (int cx = 0; cx < 3; ++cx) {
+                                const int x = big_ax(st[0], cx, B0, wx);
+                                const int idx = (zb + y) * B0 + x;
+                                const float ww = wyz * w[0][cx];
+                                for (int q = 0; q < 3; ++q) {
+                                    const float c = rc[q * cap + idx];
+                                    U[q] += ww * c;
+                                    if (DET) umax = fmaxf(umax, fabsf(c));
+                                }
+                            }
+                        }
+                    };
+                    if (rk == rank) row(cells);
+                    else row(cl.map_shared_rank(cells, rk));
+                }
+                const float *t = bp.t32 + 3ll * (Pp.toff + r1.y);
+                const float r[3] = {Pp.rphys * t[0], Pp.rphys * t[1], Pp.rphys * t[2]};
+                const float ud[3] = {Pp.ud[0] + (Pp.om[1] * r[2] - Pp.om[2] * r[1]),
+                                     Pp.ud[1] + (Pp.om[2] * r[0] - Pp.om[0] * r[2]),
+                                     Pp.ud[2] + (Pp.om[0] * r[1] - Pp.om[1] * r[0])};
+                const float D = Pp.D;
+                float e[3];
+                for (int q = 0; q < 3; ++q) {
+                    e[q] = ud[q] - U[q];
+                    emax = fmaxf(emax, fabsf(e[q]));
+                    eb[9 * m + q] = e[q];
+                }
+                dmax = fmaxf(dmax, D);
+                const float ed[3] = {e[0] * D, e[1] * D, e[2] * D};
+                eb[9 * m + 3] += ed[0];
+                eb[9 * m + 4] += ed[1];
+                eb[9 * m + 5] += ed[2];
+                eb[9 * m + 6] += r[1] * ed[2] - r[2] * ed[1];
+                eb[9 * m + 7] += r[2] * ed[0] - r[0] * ed[2];
+                eb[9 * m + 8] += r[0] * ed[1] - r[1] * ed[0];
+            }
+            if (DET) {
+                umax = warp_max(umax);
+                emax = warp_max(emax);
+                dmax = warp_max(dmax);
+                if (lane == 0) {
+                    s_red[0][wid] = umax;
+                    s_red[1][wid] = emax;
+                    s_red[2][wid] = dmax;
+                }
+                __syncthreads();
+                if (tid < 3) {
+                    float mx = 0.f;
+                    for (int i = 0; i < kBigT / 32; ++i) mx = fmaxf(mx, s_red[tid][i]);
+                    atomicMax(cl.map_shared_rank(&s_max[it & 1][tid], 0), __float_as_uint(mx));
+                }
+            }
+            cl.sync();   // interpolation done everywhere (and the maxima complete)
+            float S = 1.f, inv = 1.f;
+            if (DET) {
+                const unsigned *mx = cl.map_shared_rank(&s_max[it & 1][0], 0);
+                const float range = __uint_as_float(mx[0]) + 64.f * __uint_as_float(mx[2]) * __uint_as_float(mx[1]);
+                int ex = 100;
+                if (range > 0.f) ex = min(100, max(-100, 27 - (int)ceilf(log2f(range))));
+                S = ldexpf(1.f, ex);
+                inv = ldexpf(1.f, -ex);
+                for (int i = tid; i < H.ncell; i += kBigT) {
+                    if (!((tb[i >> 5] >> (i & 31)) & 1u)) continue;
+                    for (int q = 0; q < 3; ++q) {
+                        float *c = cells + q * cap + i;
+                        *reinterpret_cast<int *>(c) = __float2int_rn(*c * S);
+                    }
+                }
+                if (rank == 0 && tid < 3) s_max[(it + 1) & 1][tid] = 0u;   // the next iteration's buffer
+                cl.sync();   // every slab in fixed point
+            }
+            // spreading: u += w D e
+            for (int i = w0 + tid; i < w1; i += kBigT) {
+                const int m = wl[i];
+                const uint4 r0 = rec[2 * m];
+                const float D = bp.P[rec[2 * m + 1].z].D;
+                const int st[3] = {(int)(r0.x & 1023u), (int)((r0.x >> 10) & 1023u), (int)((r0.x >> 20) & 1023u)};
+                float w[3][3];
+                phi3_weights(__uint_as_float(r0.y), w[0]);
+                phi3_weights(__uint_as_float(r0.z), w[1]);
+                phi3_weights(__uint_as_float(r0.w), w[2]);
+                const float gv[3] = {D * eb[9 * m], D * eb[9 * m + 1], D * eb[9 * m + 2]};
+                for (int cz = 0; cz < 3; ++cz) {
+                    const int z = big_ax(st[2], cz, B2, wz);
+                    const int rk = z / slab;
+                    const int zb = (z - rk * slab) * B1;
+                    auto row = [&](float *rc) {
+                        for (int cy = 0; cy < 3; ++cy) {
+                            const int y = big_ax(st[1], cy, B1, wy);
+                            const float wyz = w[2][cz] * w[1][cy];
+                            for (int cx = 0; cx < 3; ++cx) {
+                                const int x = big_ax(st[0], cx, B0, wx);
+                                const int idx = (zb + y) * B0 + x;
+                                const float ww = wyz * w[0][cx];
+                                for (int q = 0; q < 3; ++q) {
+                                    if (DET)
+                                        atomicAdd(reinterpret_cast<int *>(rc + q * cap + idx),
+                                                  __float2int_rn((ww * gv[q]) * S));
+                                    else
+                                        atomicAdd(rc + q * cap + idx, ww * gv[q]);
+                                }
+                            }
+                        }
+                    };
+                    if (rk == rank) row(cells);
+                    else row(cl.map_shared_rank(cells, rk));
+                }
+            }
+            cl.sync();   // spreading done everywhere
+            if (DET) {
+                for (int i = tid; i < H.ncell; i += kBigT) {
+                    if (!((tb[i >> 5] >> (i & 31)) & 1u)) continue;
+                    for (int q = 0; q < 3; ++q) {
+                        float *c = cells + q * cap + i;
+                        const int v = *reinterpret_cast<const int *>(c);
+                        if (abs(v) > (1 << 28)) set_err(bp.err, IBM_EBIT_FIXEDPOINT);
+                        *c = (float)v * inv;
+                    }
+                }
+                cl.sync();   // back in FP32 before the next interpolation
+            }
+        }
+        // ---- write back this slab's touched cells (and f = (u^{n_F} - u^0) / tau)
+        float *const uw = bp.uf[H.scene];
+        float *const fw = bp.ff ? bp.ff[H.scene] : nullptr;
+        for (int i = tid; i < H.ncell; i += kBigT) {
+            if (!((tb[i >> 5] >> (i & 31)) & 1u)) continue;
+            const int x = i % B0, t = i / B0, y = t % B1, z = H.z0 + t / B1;
+            const long long g = ((long long)big_mod(H.lo[2] + z, H.n[2]) * H.n[1] + big_mod(H.lo[1] + y, H.n[1])) *
+                                    H.n[0] + big_mod(H.lo[0] + x, H.n[0]);
+            for (int q = 0; q < 3; ++q) {
+                const float v = cells[q * cap + i];
+                if (fw) fw[q * ncs + g] = (v - uw[q * ncs + g]) * bp.finv;
+                uw[q * ncs + g] = v;
+            }
+        }
+        // ---- loads: each particle's markers added in order, FP32 within 32-marker chunks, FP64 across
+        __threadfence();
+        cl.sync();
+        if (rank == 0) {
+            for (int j = tid; j < np * 6; j += kBigT) {
+                const int i = j / 6, q = j % 6;
+                double sum = 0.0;
+                for (int c0 = s_pref[i]; c0 < s_pref[i + 1]; c0 += 32) {
+                    float cs = 0.f;
+                    for (int m = c0; m < c0 + 32; ++m) cs += eb[9 * m + 3 + q];
+                    sum += (double)cs;
+                }
+                const int p = s_pid[i];
+                if (q < 3) bp.FD[3 * p + q] += sum;
+                else bp.TD[3 * p + q - 3] += sum;
+            }
+        }
+        cl.sync();   // nothing of this cluster is read any more: the next one may start
+    }
+}
+
+// Which fallback clusters fit a thread-block cluster (dense slabs of at most cap
+// cells, at most kBigMaxP particles and K (kBigT kBigKR - 32) markers): each goes
+// to the smaller size that fits and can run (8 or 16 CTAs), with a flag per
+// cluster and its path bits.
+__global__ void k_big_select(const long long *n_clust_d, const int32_t *dims, const int *cl_np, const int *cl_nm,
+                             const int *cl_box, const int *cl_scene, int *cl_path, int use8, int use16, int cap,
+                             int *list8, int *list16, int *big_flag, int *cnt) {
+    const int n = (int)*n_clust_d;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        big_flag[c] = 0;
+        if (!(cl_path[c] & IBM_PATH_FALLBACK)) continue;
+        const int s = cl_scene[c] & 0x0fffffff, wrap = (cl_scene[c] >> 28) & 7;
+        long long B[3];
+        bool ok = cl_np[c] <= kBigMaxP;
+        for (int k = 0; k < 3; ++k) {
+            const int nk = dims[3 * s + k];
+            B[k] = ((wrap >> k) & 1) ? nk : cl_box[12 * c + 3 + k] - cl_box[12 * c + k] + 1;
+            ok = ok && B[k] <= nk && B[k] <= 1023;
+        }
+        if (!ok) continue;
+        auto fits = [&](int K) {
+            return cl_nm[c] <= K * (kBigT * kBigKR - 32) && (B[2] + K - 1) / K * B[1] * B[0] <= cap;
+        };
+        int K = 0;
+        if (use8 && fits(8)) K = 8;
+        else if (use16 && fits(16)) K = 16;
+        if (!K) continue;
+        big_flag[c] = 1;
+        if (K == 8) list8[atomicAdd(cnt + C_NBIG8, 1)] = c;
+        else list16[atomicAdd(cnt + C_NBIG16, 1)] = c;
+        atomicAdd(cnt + C_NBIG, 1);
+        atomicAdd(cnt + C_BIGMARK, cl_nm[c]);
+        cl_path[c] = (cl_path[c] & ~IBM_PATH_FALLBACK) | IBM_PATH_DSMEM;
+    }
+}
+
+// The plain fallback keeps the particles of the clusters that did not move to
+// the thread-block-cluster path.
+__global__ void k_fb_compact(const int *fb_list, const int *pcl, const int *big_flag, int *fb_list2, int *cnt) {
+    const int n = cnt[C_NFB];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p = fb_list[i];
+        if (!big_flag[pcl[p]]) fb_list2[atomicAdd(cnt + C_NFB2, 1)] = p;
+    }
+}
+
+// Cluster size of the distributed-shared-memory path on this device (16 if a
+// 16-CTA cluster of kBigT threads with the full shared memory can run, else 8,
+// else 0 = path off), the dynamic shared memory and the number of clusters
+// that run at once.
+template <int K, bool DET>
+static bool big_config(int *smem_out, int *grid) {
+    auto kern = k_big_cluster<K, DET>;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int smem = (optin - (int)fa.sharedSizeBytes - 256) & ~15;
+    *smem_out = smem;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (K > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(K);
+    cfg.blockDim = dim3(kBigT);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = K;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    *grid = n;
+    return n > 0;
+}
+
+template <int K, bool DET>
+static ibm_status big_launch_t(ibm_ctx *ctx, ClusterScratch *S, BigParams bp, int grid, const int *list, int c_n,
+                               int c_work) {
+    bp.big_list = list;
+    bp.c_n = c_n;
+    bp.c_work = c_work;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(K * grid);
+    cfg.blockDim = dim3(kBigT);
+    cfg.dynamicSmemBytes = (size_t)S->big_smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = K;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return ibm_cuda_check(ctx, cudaLaunchKernelEx(&cfg, k_big_cluster<K, DET>, bp), "thread-block-cluster kernel");
+}
+
+// Move the fallback clusters that fit a thread-block cluster to the
+// distributed-shared-memory kernel; *fb_list / *fb_cnt then name what is left
+// for the plain path.
+static ibm_status big_clusters(ibm_ctx *ctx, ClusterScratch *S, float finv, bool with_f, bool det,
+                               const int **fb_list, const int **fb_cnt) {
+    *fb_list = S->fb_list;
+    *fb_cnt = S->cnt + C_NFB;
+    cudaStream_t sm = ctx->stream;
+    if (S->big_k < 0 || S->big_det != (int)det) {
+        // once per context: which thread-block-cluster sizes this device runs with the full shared memory
+        int g8 = 0, g16 = 0, smem8 = 0, smem16 = 0;
+        if (!(det ? big_config<8, true>(&smem8, &g8) : big_config<8, false>(&smem8, &g8))) g8 = 0;
+        if (!(det ? big_config<16, true>(&smem16, &g16) : big_config<16, false>(&smem16, &g16))) g16 = 0;
+        S->big_grid8 = g8;
+        S->big_grid16 = g16;
+        S->big_k = (g8 || g16) ? 1 : 0;
+        S->big_det = (int)det;
+        S->big_smem = std::min(g8 ? smem8 : INT_MAX, g16 ? smem16 : INT_MAX);
+        // dense cells: 12 B and one bit each
+        S->big_cells = S->big_k ? (int)(((long long)S->big_smem * 8 / 97) & ~31ll) : 0;
+        if (S->big_k) {
+            if (g8) CK(cudaFuncSetAttribute(det ? (const void *)k_big_cluster<8, true> : (const void *)k_big_cluster<8, false>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, S->big_smem), "shared memory");
+            if (g16) CK(cudaFuncSetAttribute(det ? (const void *)k_big_cluster<16, true> : (const void *)k_big_cluster<16, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, S->big_smem), "shared memory");
+        }
+    }
+    if (S->big_k == 0) return IBM_OK;
+    // scratch per slot: K * kBigT * kBigKR markers; the two launches run one after the other and share it
+    const size_t mk = std::max((size_t)S->big_grid8 * 8, (size_t)S->big_grid16 * 16) * kBigT * kBigKR;
+    const size_t rec = mk * 2 * sizeof(uint4);
+    const size_t part = mk * 9 * sizeof(float);
+    const size_t wl = mk * sizeof(int);
+    if (S->big_rec_bytes < rec) {
+        S->big_rec_bytes = 0;
+        CK(dev_realloc(&S->big_rec, rec), "alloc cluster records");
+        S->big_rec_bytes = rec;
+    }
+    if (S->big_part_bytes < part) {
+        S->big_part_bytes = 0;
+        CK(dev_realloc(&S->big_part, part), "alloc cluster marker sums");
+        S->big_part_bytes = part;
+    }
+    if (S->big_wl_bytes < wl) {
+        S->big_wl_bytes = 0;
+        CK(dev_realloc(&S->big_wl, wl), "alloc cluster work lists");
+        S->big_wl_bytes = wl;
+    }
+    const int n = std::max(ctx->n_p, 1);
+    k_big_select<<<grid_for(n, 256), 256, 0, sm>>>(S->tot + 1, ctx->dims_d, S->cl_np, S->cl_nm, S->cl_box,
+                                                   S->cl_scene, S->cl_path, S->big_grid8 > 0, S->big_grid16 > 0,
+                                                   S->big_cells, S->big_list, S->big_list16, S->big_flag, S->cnt);
+    k_fb_compact<<<grid_for(n, 256), 256, 0, sm>>>(S->fb_list, S->pcl, S->big_flag, S->fb_list2, S->cnt);
+    BigParams bp;
+    bp.P = ctx->pinfo;
+    bp.t32 = ctx->tmpl32;
+    bp.t64 = ctx->tmpl64;
+    bp.dims = ctx->dims_d;
+    bp.uf = reinterpret_cast<float *const *>(ctx->uptr_d);
+    bp.ff = with_f ? reinterpret_cast<float *const *>(ctx->fptr_d) : nullptr;
+    bp.cnt = S->cnt;
+    bp.err = ctx->err_d;
+    bp.cl_np = S->cl_np;
+    bp.cl_first = S->cl_first;
+    bp.cl_plist = S->cl_plist;
+    bp.cl_box = S->cl_box;
+    bp.cl_scene = S->cl_scene;
+    bp.dis = contact_bits(ctx);
+    bp.FD = ctx->FD;
+    bp.TD = ctx->TD;
+    bp.rec = S->big_rec;
+    bp.part = S->big_part;
+    bp.wlist = S->big_wl;
+    bp.n_forcing = ctx->cfg.n_forcing;
+    bp.cap_cells = S->big_cells;
+    bp.finv = finv;
+    ibm_status st = IBM_OK;
+    if (S->big_grid8)
+        st = det ? big_launch_t<8, true>(ctx, S, bp, S->big_grid8, S->big_list, C_NBIG8, C_WORK8)
+                 : big_launch_t<8, false>(ctx, S, bp, S->big_grid8, S->big_list, C_NBIG8, C_WORK8);
+    if (st == IBM_OK && S->big_grid16)
+        st = det ? big_launch_t<16, true>(ctx, S, bp, S->big_grid16, S->big_list16, C_NBIG16, C_WORK16)
+                 : big_launch_t<16, false>(ctx, S, bp, S->big_grid16, S->big_list16, C_NBIG16, C_WORK16);
+    if (st != IBM_OK) return st;
+    ctx->launches += 2 + (S->big_grid8 > 0) + (S->big_grid16 > 0);
+    *fb_list = S->fb_list2;
+    *fb_cnt = S->cnt + C_NFB2;
+    return IBM_OK;
+}
+
 // markers per thread of its record path, for a block size
 static int markers_per_thread(int) { return 12; }
 static int records_per_thread(int) { return 2; }
@@ -1773,9 +2392,13 @@ ibm_status cluster_forcing_step(ibm_ctx *ctx, void *const *u_ptrs, double tau, v
     prof_end(ctx);
     if (st == IBM_OK) {
         ctx->launches += 1;
-        // clusters that did not fit: plain FP32 iterations over their particles
-        st = plain_iterations_f32(ctx, S->fb_list, n, S->cnt + C_NFB, tau, f_out != nullptr, ctx->cfg.n_forcing,
-                                  det ? S->pcl : nullptr);
+        // clusters that did not fit one SM: a thread-block cluster's distributed shared memory where
+        // their box fits it, else plain FP32 iterations over their particles
+        const int *fbl = S->fb_list, *fbn = S->cnt + C_NFB;
+        st = big_clusters(ctx, S, (float)(1.0 / tau), f_out != nullptr, det, &fbl, &fbn);
+        if (st == IBM_OK)
+            st = plain_iterations_f32(ctx, fbl, n, fbn, tau, f_out != nullptr, ctx->cfg.n_forcing,
+                                      det ? S->pcl : nullptr);
     }
     if (tev[0]) {
         // tuning step: time this variant together with the fallback work its routing leaves (host sync);
@@ -1805,10 +2428,12 @@ void cluster_graph_key(const ibm_ctx *ctx, std::vector<uintptr_t> &key) {
                           S->parent, S->cand, S->cnt, S->tot, S->root_flag, S->cid, S->pcl, S->poff, S->cl_np,
                           S->cl_nm, S->cl_first, S->cl_cur, S->cl_box, S->cl_plist, S->cl_bkt, S->bkt_cnt,
                           S->bkt_start, S->order, S->fb_list, S->nm_ord, S->cum, S->cl_scene, S->cl_path,
-                          S->batches, S->grec};
+                          S->batches, S->grec, S->big_list, S->big_flag, S->fb_list2, S->big_rec, S->big_part,
+                          S->big_wl, S->big_list16};
     for (const void *b : bufs) key.push_back((uintptr_t)b);
     const long long sizes[] = {S->cap_p, S->cap_bins, S->cap_cand, S->nbins, S->max_nl, S->n_scenes,
-                               S->smem_bytes, S->tpb, S->det, (long long)S->grec_bytes};
+                               S->smem_bytes, S->tpb, S->det, (long long)S->grec_bytes, S->big_k, S->big_grid8,
+                               S->big_grid16, S->big_cells};
     for (long long v : sizes) key.push_back((uintptr_t)v);
 }
 
@@ -1822,12 +2447,14 @@ ibm_status cluster_stats(ibm_ctx *ctx, int64_t *stats) {
     CK(cudaStreamSynchronize(ctx->stream), "sync stats");
     stats[1] = nclust;
     stats[2] = c[C_NITEMS] - c[C_OVERFLOW];
-    stats[3] = c[C_FBMARK];
+    stats[3] = c[C_FBMARK] - c[C_BIGMARK];
     stats[4] = c[C_MAXCELLS];
     stats[5] = c[C_TOUCHED];
     stats[7] = S->tpb;
     stats[8] = c[C_ONECOMP];
     stats[9] = c[C_NCAND];
+    stats[10] = c[C_NBIG];
+    stats[11] = c[C_BIGMARK];
     return IBM_OK;
 }
 

@@ -507,7 +507,7 @@ ibm_status ibm_kernel_timing(ibm_ctx *ctx, double *total_ms, int64_t *count, int
 ibm_status ibm_step_stats(ibm_ctx *ctx, int64_t *stats) {
     if (!ctx || !stats) return IBM_ERR_INVALID_ARG;
     ibm_status s = ibm_check_err_word(ctx);
-    for (int i = 0; i < 10; ++i) stats[i] = 0;
+    for (int i = 0; i < 12; ++i) stats[i] = 0;
     stats[0] = ctx->n_markers;
     stats[6] = ctx->launches;
     if (s == IBM_OK && ctx->cfg.spread_mode != IBM_SPREAD_PLAIN) s = cluster_stats(ctx, stats);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libibm.so")
 IBM_FP64, IBM_FP32 = 0, 1
 IBM_SPREAD_CLUSTER, IBM_SPREAD_DETERMINISTIC, IBM_SPREAD_PLAIN = 0, 1, 2
 IBM_PATH_SMEM, IBM_PATH_GLOBAL_RECORDS, IBM_PATH_ONE_COMPONENT = 1, 2, 4
-IBM_PATH_SPARSE_ROWS, IBM_PATH_PERIODIC, IBM_PATH_FALLBACK = 8, 16, 32
+IBM_PATH_SPARSE_ROWS, IBM_PATH_PERIODIC, IBM_PATH_FALLBACK, IBM_PATH_DSMEM = 8, 16, 32, 64
 
 STATUS = {0: "IBM_OK", 1: "IBM_ERR_INVALID_ARG", 2: "IBM_ERR_CUDA", 3: "IBM_ERR_OOM",
           4: "IBM_ERR_CAPACITY", 5: "IBM_ERR_NONFINITE", 6: "IBM_ERR_TIMEOUT", 7: "IBM_ERR_STATE",
@@ -371,10 +371,11 @@ class Context:
         return cl[:n], path[:n], int(nc.value)
 
     def stats(self):
-        out = np.zeros(10, dtype=np.int64)
+        out = np.zeros(12, dtype=np.int64)
         self._check(self.L.ibm_step_stats(self.h, _ptr(out)))
         keys = ("markers", "clusters", "clusters_smem", "markers_fallback", "largest_cluster_cells",
-                "touched_cells", "launches", "threads_per_block", "clusters_one_component", "candidate_pairs")
+                "touched_cells", "launches", "threads_per_block", "clusters_one_component", "candidate_pairs",
+                "clusters_dsmem", "markers_dsmem")
         return dict(zip(keys, (int(v) for v in out)))
 
 

@@ -74,6 +74,7 @@ def test_batched_scenes_match_oracle(batch, tpb, graph):
     ctx, us, loads = _run(scenes, u0s, tpb=tpb, graph=graph, steps=3 if graph else 1)
     st = ctx.stats()
     assert st["threads_per_block"] == tpb
+    assert st["markers_dsmem"] > 0         # the dense 48^3 boxes' clusters run on thread-block clusters
     off = np.cumsum([0] + [s.n_p for s in scenes])
     for k in pick:
         s, ref = scenes[k], refs[k]

@@ -157,12 +157,26 @@ def test_moderate_overlap_stays_in_fixed_point_range(oracle_mod):
     assert load_err(got["F"], ref["F"], ref["Fabs"]) <= LOAD_TOL32
 
 
-def test_extreme_overlap_reports_fixed_point_range(oracle_mod):
-    # 320 coincident spheres (a fallback cluster): about 250 unit weights per
-    # cell, four times the bound the fixed-point scale assumes; deterministic
-    # mode must say so rather than return wrapped integers, and the context must
-    # run a valid scene afterwards; the FP32 atomic mode has no such range
+def test_overlap_beyond_range_on_the_thread_block_cluster_path():
+    # 320 coincident spheres (20,480 markers: too many for one SM, not for a thread-block cluster): the
+    # distributed-shared-memory kernel's conversion reports the range too
     sc = _coincident(320)
+    u0 = np.full((3, 32, 32, 32), 5.0)
+    ctx = gpu_context([sc.dims], sc.n_p, ibm.IBM_FP32, ibm.IBM_SPREAD_DETERMINISTIC)
+    ctx.set_particles(sc.x_p, sc.u_p, sc.omega_p, sc.d_p)
+    u = torch.from_numpy(u0).float().cuda()
+    with pytest.raises(ibm.IBMError) as e:
+        ctx.forcing_step([u], 0.01, want_slip=True)
+    assert e.value.status == IBM_ERR_CAPACITY
+    assert ctx.stats()["markers_dsmem"] > 0
+
+
+def test_extreme_overlap_reports_fixed_point_range(oracle_mod):
+    # 520 coincident spheres (more particles than a thread-block cluster takes: the plain fallback): about
+    # 400 unit weights per cell, six times the bound the fixed-point scale assumes; deterministic mode must
+    # say so rather than return wrapped integers, and the context must run a valid scene afterwards; the
+    # FP32 atomic mode has no such range
+    sc = _coincident(520)
     u0 = np.full((3, 32, 32, 32), 5.0)
     ctx = gpu_context([sc.dims], sc.n_p, ibm.IBM_FP32, ibm.IBM_SPREAD_DETERMINISTIC)
     ctx.set_particles(sc.x_p, sc.u_p, sc.omega_p, sc.d_p)

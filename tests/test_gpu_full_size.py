@@ -157,7 +157,7 @@ def _pick_clusters(sc, cl, path):
     nl = {d: O.marker_count(d) for d in np.unique(sc.d_p)}
     nm = np.array([sum((nl[sc.d_p[p]] + 31) // 32 * 32 for p in m) for m in members])
     cpath = np.array([path[m[0]] for m in members])
-    picked = {k for k in range(len(ids)) if cpath[k] & ibm.IBM_PATH_FALLBACK}
+    picked = {k for k in range(len(ids)) if cpath[k] & (ibm.IBM_PATH_FALLBACK | ibm.IBM_PATH_DSMEM)}
     smem = [k for k in range(len(ids)) if cpath[k] & ibm.IBM_PATH_SMEM]
     multi = sorted((k for k in smem if len(members[k]) > 1), key=lambda k: nm[k])
     picked.add(max(smem, key=lambda k: nm[k]))
@@ -179,8 +179,11 @@ def test_full_bed_clusters_match_oracle(oracle_mod, bed_step):
     assert n_clusters == stats["clusters"]
     chosen = _pick_clusters(sc, cl, path)
     n_fb = sum(1 for _, cp, _ in chosen if cp & ibm.IBM_PATH_FALLBACK)
-    assert n_fb == stats["clusters"] - stats["clusters_smem"]
+    n_ds = sum(1 for _, cp, _ in chosen if cp & ibm.IBM_PATH_DSMEM)
+    assert n_ds == stats["clusters_dsmem"]
+    assert n_fb + n_ds == stats["clusters"] - stats["clusters_smem"]
     assert sum(nm for _, cp, nm in chosen if cp & ibm.IBM_PATH_FALLBACK) == stats["markers_fallback"]
+    assert sum(nm for _, cp, nm in chosen if cp & ibm.IBM_PATH_DSMEM) == stats["markers_dsmem"]
     assert sum(1 for m, cp, _ in chosen if len(m) > 1 and cp & ibm.IBM_PATH_SMEM) >= 10
     seen = 0
     for members, cpath, nm in chosen:
