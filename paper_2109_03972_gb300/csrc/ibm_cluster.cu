@@ -1850,19 +1850,6 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
                 r0 = make_uint4((unsigned)st[0] | ((unsigned)st[1] << 10) | ((unsigned)st[2] << 20) | (1u << 31),
                                 __float_as_uint(fr[0]), __float_as_uint(fr[1]), __float_as_uint(fr[2]));
                 r1 = make_uint4((unsigned)lo, (unsigned)l, (unsigned)p, 0u);
-                for (int cz = 0; cz < 3; ++cz) {
-                    const int z = big_ax(st[2], cz, B2, wz);
-                    const int rk = z / slab;
-                    unsigned *rtb = cl.map_shared_rank(tb, rk);
-                    for (int cy = 0; cy < 3; ++cy) {
-                        const int y = big_ax(st[1], cy, B1, wy);
-                        for (int cx = 0; cx < 3; ++cx) {
-                            const int x = big_ax(st[0], cx, B0, wx);
-                            const int idx = ((z - rk * slab) * B1 + y) * B0 + x;
-                            atomicOr(rtb + (idx >> 5), 1u << (idx & 31));
-                        }
-                    }
-                }
                 atomicAdd(cl.map_shared_rank(&s_own, big_ax(st[2], 1, B2, wz) / slab), 1);
             }
             rec[2 * m] = r0;
@@ -1870,7 +1857,7 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
 #pragma unroll
             for (int q = 3; q < 9; ++q) eb[9 * m + q] = 0.f;
         }
-        cl.sync();   // touched bits and owner counts complete
+        cl.sync();   // records and owner counts complete
         if (tid == 0) {
             int a = 0;
             for (int r = 0; r < K; ++r) {
@@ -1888,6 +1875,28 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
             const int owner = big_ax((int)((r0.x >> 20) & 1023u), 1, B2, wz) / slab;
             wl[s_off[owner] + atomicAdd(cl.map_shared_rank(&s_cur, owner), 1)] = m;
         }
+        __threadfence();
+        cl.sync();   // work lists complete
+        const int w0 = s_off[rank], w1 = s_off[rank + 1];
+        // touched bits, set by the owner of each marker (its own slab for the middle plane)
+        for (int i = w0 + tid; i < w1; i += kBigT) {
+            const uint4 r0 = rec[2 * wl[i]];
+            const int st[3] = {(int)(r0.x & 1023u), (int)((r0.x >> 10) & 1023u), (int)((r0.x >> 20) & 1023u)};
+            for (int cz = 0; cz < 3; ++cz) {
+                const int z = big_ax(st[2], cz, B2, wz);
+                const int rk = z / slab;
+                unsigned *rtb = rk == rank ? tb : cl.map_shared_rank(tb, rk);
+                for (int cy = 0; cy < 3; ++cy) {
+                    const int y = big_ax(st[1], cy, B1, wy);
+                    for (int cx = 0; cx < 3; ++cx) {
+                        const int x = big_ax(st[0], cx, B0, wx);
+                        const int idx = ((z - rk * slab) * B1 + y) * B0 + x;
+                        atomicOr(rtb + (idx >> 5), 1u << (idx & 31));
+                    }
+                }
+            }
+        }
+        cl.sync();   // touched bits complete
         // ---- gather the touched cells of this CTA's slab
         const float *const u0 = bp.uf[H.scene];
         const long long ncs = (long long)H.n[0] * H.n[1] * H.n[2];
@@ -1898,9 +1907,7 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
                                     H.n[0] + big_mod(H.lo[0] + x, H.n[0]);
             for (int q = 0; q < 3; ++q) cells[q * cap + i] = u0[q * ncs + g];
         }
-        __threadfence();
-        cl.sync();   // work list and cells complete
-        const int w0 = s_off[rank], w1 = s_off[rank + 1];
+        cl.sync();   // cells complete
         // ---- the n_F iterations; a CTA works on the markers whose stencil's middle plane it holds, so
         // most of their cells are its own (plain shared-memory accesses), the rest in the neighbour slabs
         for (int it = 0; it < bp.n_forcing; ++it) {
