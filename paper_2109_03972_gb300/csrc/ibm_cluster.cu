@@ -1726,10 +1726,19 @@ struct BigParams {
 
 struct BigHdr {
     int c, np, nm, wrap;
-    int lo[3], B[3], n[3];
-    int slab, z0, z1, ncell;     // this CTA's slab [z0, z1) and its cells
+    int lo[3], B[3], n[3];       // the box, per axis of the grid
+    int perm[3], Bp[3], wp;      // local axis j is grid axis perm[j]; local axis 2 (the longest) is cut into slabs
+    int slab, z0, z1, ncell;     // this CTA's slab [z0, z1) along local axis 2 and its cells
     int scene;
 };
+
+// The slab axis of a box: its longest axis (z on ties), so that the slabs are thin.
+__device__ __forceinline__ int big_slab_axis(const long long B[3]) {
+    int a = 2;
+    if (B[0] > B[a]) a = 0;
+    if (B[1] > B[a]) a = 1;
+    return a;
+}
 
 __device__ __forceinline__ int big_mod(int v, int n) {
     v %= n;
@@ -1786,10 +1795,20 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
                 H.lo[k] = w ? 0 : bp.cl_box[12 * c + k];
                 H.B[k] = w ? H.n[k] : bp.cl_box[12 * c + 3 + k] - bp.cl_box[12 * c + k] + 1;
             }
-            H.slab = (H.B[2] + K - 1) / K;
-            H.z0 = min(H.B[2], rank * H.slab);
-            H.z1 = min(H.B[2], H.z0 + H.slab);
-            H.ncell = (H.z1 - H.z0) * H.B[1] * H.B[0];
+            const long long Bl[3] = {H.B[0], H.B[1], H.B[2]};
+            const int a = big_slab_axis(Bl);
+            H.perm[2] = a;
+            H.perm[0] = a == 0 ? 1 : 0;
+            H.perm[1] = a == 2 ? 1 : 2;
+            H.wp = 0;
+            for (int j = 0; j < 3; ++j) {
+                H.Bp[j] = H.B[H.perm[j]];
+                H.wp |= ((H.wrap >> H.perm[j]) & 1) << j;
+            }
+            H.slab = (H.Bp[2] + K - 1) / K;
+            H.z0 = min(H.Bp[2], rank * H.slab);
+            H.z1 = min(H.Bp[2], H.z0 + H.slab);
+            H.ncell = (H.z1 - H.z0) * H.Bp[1] * H.Bp[0];
             s_own = 0;
             s_cur = 0;
         }
@@ -1819,8 +1838,17 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
         const int nm = s_pref[np];
         const int per = (((nm >> 5) + K - 1) / K) << 5;          // flat markers set up by each CTA
         const int m0 = min(nm, rank * per), m1 = min(nm, m0 + per);
-        const int B0 = H.B[0], B1 = H.B[1], B2 = H.B[2], slab = H.slab;
-        const bool wx = H.wrap & 1, wy = (H.wrap >> 1) & 1, wz = (H.wrap >> 2) & 1;
+        const int B0 = H.Bp[0], B1 = H.Bp[1], B2 = H.Bp[2], slab = H.slab;
+        const bool wx = H.wp & 1, wy = (H.wp >> 1) & 1, wz = (H.wp >> 2) & 1;
+        // grid cell of local cell (x, y, z) of the box
+        auto grid_cell = [&](int x, int y, int z) {
+            int o[3];
+            o[H.perm[0]] = x;
+            o[H.perm[1]] = y;
+            o[H.perm[2]] = z;
+            return ((long long)big_mod(H.lo[2] + o[2], H.n[2]) * H.n[1] + big_mod(H.lo[1] + o[1], H.n[1])) * H.n[0] +
+                   big_mod(H.lo[0] + o[0], H.n[0]);
+        };
         cl.sync();   // bitmasks clear and counters zero everywhere
         // ---- records of this CTA's flat markers (box-relative stencil start, fractions), touched bits,
         // and the count of each owning CTA
@@ -1841,11 +1869,15 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
             }
             uint4 r0 = make_uint4(0u, 0u, 0u, 0u), r1 = make_uint4(0u, 0u, 0u, 0u);
             if (live) {
-                int st[3];
-                float fr[3];
+                int sg[3], st[3];
+                float fg[3], fr[3];
                 for (int c = 0; c < 3; ++c) {
-                    const int b = marker_split32(Pp, bp.t32 + 3ll * (Pp.toff + l), bp.t64 + 3ll * (Pp.toff + l), c, &fr[c]);
-                    st[c] = big_mod(b - 1 - H.lo[c], H.n[c]);
+                    const int b = marker_split32(Pp, bp.t32 + 3ll * (Pp.toff + l), bp.t64 + 3ll * (Pp.toff + l), c, &fg[c]);
+                    sg[c] = big_mod(b - 1 - H.lo[c], H.n[c]);
+                }
+                for (int j = 0; j < 3; ++j) {   // in the box's local axes
+                    st[j] = sg[H.perm[j]];
+                    fr[j] = fg[H.perm[j]];
                 }
                 r0 = make_uint4((unsigned)st[0] | ((unsigned)st[1] << 10) | ((unsigned)st[2] << 20) | (1u << 31),
                                 __float_as_uint(fr[0]), __float_as_uint(fr[1]), __float_as_uint(fr[2]));
@@ -1903,8 +1935,7 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
         for (int i = tid; i < H.ncell; i += kBigT) {
             if (!((tb[i >> 5] >> (i & 31)) & 1u)) continue;
             const int x = i % B0, t = i / B0, y = t % B1, z = H.z0 + t / B1;
-            const long long g = ((long long)big_mod(H.lo[2] + z, H.n[2]) * H.n[1] + big_mod(H.lo[1] + y, H.n[1])) *
-                                    H.n[0] + big_mod(H.lo[0] + x, H.n[0]);
+            const long long g = grid_cell(x, y, z);
             for (int q = 0; q < 3; ++q) cells[q * cap + i] = u0[q * ncs + g];
         }
         cl.sync();   // cells complete
@@ -2059,8 +2090,7 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
         for (int i = tid; i < H.ncell; i += kBigT) {
             if (!((tb[i >> 5] >> (i & 31)) & 1u)) continue;
             const int x = i % B0, t = i / B0, y = t % B1, z = H.z0 + t / B1;
-            const long long g = ((long long)big_mod(H.lo[2] + z, H.n[2]) * H.n[1] + big_mod(H.lo[1] + y, H.n[1])) *
-                                    H.n[0] + big_mod(H.lo[0] + x, H.n[0]);
+            const long long g = grid_cell(x, y, z);
             for (int q = 0; q < 3; ++q) {
                 const float v = cells[q * cap + i];
                 if (fw) fw[q * ncs + g] = (v - uw[q * ncs + g]) * bp.finv;
@@ -2108,8 +2138,9 @@ __global__ void k_big_select(const long long *n_clust_d, const int32_t *dims, co
             ok = ok && B[k] <= nk && B[k] <= 1023;
         }
         if (!ok) continue;
+        const int a = big_slab_axis(B);
         auto fits = [&](int K) {
-            return cl_nm[c] <= K * (kBigT * kBigKR - 32) && (B[2] + K - 1) / K * B[1] * B[0] <= cap;
+            return cl_nm[c] <= K * (kBigT * kBigKR - 32) && (B[a] + K - 1) / K * (B[0] * B[1] * B[2] / B[a]) <= cap;
         };
         int K = 0;
         if (use8 && fits(8)) K = 8;
