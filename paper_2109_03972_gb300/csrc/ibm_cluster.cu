@@ -1703,6 +1703,7 @@ static ibm_status launch_cluster_kernel(ibm_ctx *ctx, ClusterScratch *S, KParams
 // slab, cells converted back, with cluster barriers between the phases.  HBM
 // sees each touched cell once per step, as on the one-SM path.  The work list
 // is taken persistently, one cluster at a time per thread-block cluster.
+// threads per CTA; marker capacity per CTA of a thread-block cluster, in units of its threads; particles
 constexpr int kBigT = 1024, kBigKR = 4, kBigMaxP = 512;
 
 struct BigParams {
