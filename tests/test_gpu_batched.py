@@ -1,12 +1,13 @@
 """Batched scenes against the oracle: the first 80 scenes of the batched
 workload (periodic boxes of edge 32..128, 1-40 spheres each, D ~ U[8, 20]h) run
 in one context, i.e. one persistent cluster-kernel launch per step over all
-scenes, in the benchmark's mode (FP32, deterministic spreading); 40 scenes are
+scenes, in the benchmark's mode (FP32, deterministic spreading) and with FP32 atomics; 40 scenes are
 then compared with the oracle scene by scene: every 32^3 box (the densest:
 40-46% solid, clusters that wrap the period) and the densest boxes of the other
 edges.  Both kernel variants (one 1024-thread CTA per SM, two 512-thread CTAs)
 and the CUDA-graph replay of the step give the same result within the FP32
-tolerances.
+tolerances; the clusters too large for one SM run on thread-block clusters
+(distributed shared memory).
 """
 import numpy as np
 import pytest
@@ -45,9 +46,9 @@ def batch():
     return scenes, u0s, pick, refs
 
 
-def _run(scenes, u0s, tpb=0, graph=False, steps=1):
+def _run(scenes, u0s, tpb=0, graph=False, steps=1, mode=ibm.IBM_SPREAD_DETERMINISTIC):
     n = sum(s.n_p for s in scenes)
-    ctx = gpu_context([s.dims for s in scenes], n, ibm.IBM_FP32, ibm.IBM_SPREAD_DETERMINISTIC, tpb=tpb)
+    ctx = gpu_context([s.dims for s in scenes], n, ibm.IBM_FP32, mode, tpb=tpb)
     if graph:
         cfg = ibm.Config(**{**ctx.cfg.__dict__, "use_graph": True})
         ctx = ibm.Context(cfg)
@@ -67,11 +68,15 @@ def _run(scenes, u0s, tpb=0, graph=False, steps=1):
     return ctx, [u.double().cpu().numpy() for u in us], loads
 
 
-@pytest.mark.parametrize("tpb,graph", [(1024, False), (512, False), (1024, True)])
-def test_batched_scenes_match_oracle(batch, tpb, graph):
+@pytest.mark.parametrize("tpb,graph,mode", [(1024, False, ibm.IBM_SPREAD_DETERMINISTIC),
+                                             (512, False, ibm.IBM_SPREAD_DETERMINISTIC),
+                                             (1024, True, ibm.IBM_SPREAD_DETERMINISTIC),
+                                             (1024, False, ibm.IBM_SPREAD_CLUSTER)])
+def test_batched_scenes_match_oracle(batch, tpb, graph, mode):
+    # the last case runs every path with FP32 atomics (shared, distributed shared and global memory)
     scenes, u0s, pick, refs = batch
     assert len(pick) == N_CHECK and sum(scenes[k].dims[0] == 32 for k in pick) >= 10
-    ctx, us, loads = _run(scenes, u0s, tpb=tpb, graph=graph, steps=3 if graph else 1)
+    ctx, us, loads = _run(scenes, u0s, tpb=tpb, graph=graph, steps=3 if graph else 1, mode=mode)
     st = ctx.stats()
     assert st["threads_per_block"] == tpb
     assert st["markers_dsmem"] > 0         # the dense 48^3 boxes' clusters run on thread-block clusters
