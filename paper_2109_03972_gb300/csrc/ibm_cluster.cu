@@ -106,6 +106,9 @@ struct ClusterScratch {
     // (0: that size cannot run), dense cells per CTA
     int big_k = -1, big_grid8 = 0, big_grid16 = 0, big_cells = 0, big_det = -1, big_smem = 0;
     int *big_list16 = nullptr;
+    // the 16-CTA launch runs beside the 8-CTA one on a stream of its own (fork and join by events)
+    cudaStream_t big_side = nullptr;
+    cudaEvent_t big_fork = nullptr, big_join = nullptr;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -1580,6 +1583,9 @@ void cluster_free(ibm_ctx *ctx) {
     if (S->big_rec) cudaFree(S->big_rec);
     if (S->big_part) cudaFree(S->big_part);
     if (S->big_wl) cudaFree(S->big_wl);
+    if (S->big_fork) cudaEventDestroy(S->big_fork);
+    if (S->big_join) cudaEventDestroy(S->big_join);
+    if (S->big_side) cudaStreamDestroy(S->big_side);
     if (S->batches) cudaFree(S->batches);
     if (S->grec) cudaFree(S->grec);
     if (S->tot) cudaFree(S->tot);
@@ -1767,6 +1773,7 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
     __shared__ float s_red[3][kBigT / 32];
     __shared__ int s_own, s_cur;            // markers this CTA owns (their stencil's middle plane is in its slab)
     __shared__ int s_off[K + 1];            // offsets of every CTA's markers in the work list
+    __shared__ int s_scan[32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int rank = (int)cl.block_rank();
     const int slot = blockIdx.x / K;
@@ -1825,13 +1832,13 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
         __syncthreads();
         if (tid < np) s_pid[my_pos] = my_pid;
         __syncthreads();
-        if (tid == 0) {
-            int a = 0;
-            for (int i = 0; i < np; ++i) {
-                s_pref[i] = a;
-                a += (bp.P[s_pid[i]].nl + 31) & ~31;
-            }
-            s_pref[np] = a;
+        {
+            // first flat marker of each particle (padded to 32-marker chunks): block scan
+            const int pad = tid < np ? (bp.P[s_pid[tid]].nl + 31) & ~31 : 0;
+            int total;
+            const int pre = block_excl_scan<kBigT>(pad, s_scan, &total);
+            if (tid < np) s_pref[tid] = pre;
+            if (tid == 0) s_pref[np] = total;
         }
         if (rank == 0 && tid < 6) s_max[tid / 3][tid % 3] = 0u;
         for (int w = tid; w < (H.ncell + 31) / 32; w += kBigT) tb[w] = 0u;
@@ -1933,17 +1940,22 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
         // ---- gather the touched cells of this CTA's slab
         const float *const u0 = bp.uf[H.scene];
         const long long ncs = (long long)H.n[0] * H.n[1] * H.n[2];
+        float ucarry = 0.f;   // max |u| over this thread's cells (deterministic mode's range)
         for (int i = tid; i < H.ncell; i += kBigT) {
             if (!((tb[i >> 5] >> (i & 31)) & 1u)) continue;
             const int x = i % B0, t = i / B0, y = t % B1, z = H.z0 + t / B1;
             const long long g = grid_cell(x, y, z);
-            for (int q = 0; q < 3; ++q) cells[q * cap + i] = u0[q * ncs + g];
+            for (int q = 0; q < 3; ++q) {
+                const float v = u0[q * ncs + g];
+                cells[q * cap + i] = v;
+                if (DET) ucarry = fmaxf(ucarry, fabsf(v));
+            }
         }
         cl.sync();   // cells complete
         // ---- the n_F iterations; a CTA works on the markers whose stencil's middle plane it holds, so
         // most of their cells are its own (plain shared-memory accesses), the rest in the neighbour slabs
         for (int it = 0; it < bp.n_forcing; ++it) {
-            float umax = 0.f, emax = 0.f, dmax = 0.f;
+            float emax = 0.f, dmax = 0.f;
             for (int i = w0 + tid; i < w1; i += kBigT) {
                 const int m = wl[i];
                 const uint4 r0 = rec[2 * m];
@@ -1954,24 +1966,25 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
                 phi3_weights(__uint_as_float(r0.y), w[0]);
                 phi3_weights(__uint_as_float(r0.z), w[1]);
                 phi3_weights(__uint_as_float(r0.w), w[2]);
+                int xs[3];
+#pragma unroll
+                for (int cx = 0; cx < 3; ++cx) xs[cx] = big_ax(st[0], cx, B0, wx);
                 float U[3] = {0.f, 0.f, 0.f};
+#pragma unroll
                 for (int cz = 0; cz < 3; ++cz) {
                     const int z = big_ax(st[2], cz, B2, wz);
                     const int rk = z / slab;
                     const int zb = (z - rk * slab) * B1;
                     auto row = [&](const float *rc) {
+#pragma unroll
                         for (int cy = 0; cy < 3; ++cy) {
-                            const int y = big_ax(st[1], cy, B1, wy);
+                            const float *rw = rc + (zb + big_ax(st[1], cy, B1, wy)) * B0;
                             const float wyz = w[2][cz] * w[1][cy];
+#pragma unroll
                             for (int cx = 0; cx < 3; ++cx) {
-                                const int x = big_ax(st[0], cx, B0, wx);
-                                const int idx = (zb + y) * B0 + x;
                                 const float ww = wyz * w[0][cx];
-                                for (int q = 0; q < 3; ++q) {
-                                    const float c = rc[q * cap + idx];
-                                    U[q] += ww * c;
-                                    if (DET) umax = fmaxf(umax, fabsf(c));
-                                }
+#pragma unroll
+                                for (int q = 0; q < 3; ++q) U[q] += ww * rw[q * cap + xs[cx]];
                             }
                         }
                     };
@@ -2000,7 +2013,7 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
                 eb[9 * m + 8] += r[0] * ed[1] - r[1] * ed[0];
             }
             if (DET) {
-                umax = warp_max(umax);
+                const float umax = warp_max(ucarry);
                 emax = warp_max(emax);
                 dmax = warp_max(dmax);
                 if (lane == 0) {
@@ -2045,24 +2058,27 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
                 phi3_weights(__uint_as_float(r0.z), w[1]);
                 phi3_weights(__uint_as_float(r0.w), w[2]);
                 const float gv[3] = {D * eb[9 * m], D * eb[9 * m + 1], D * eb[9 * m + 2]};
+                int xs[3];
+#pragma unroll
+                for (int cx = 0; cx < 3; ++cx) xs[cx] = big_ax(st[0], cx, B0, wx);
+#pragma unroll
                 for (int cz = 0; cz < 3; ++cz) {
                     const int z = big_ax(st[2], cz, B2, wz);
                     const int rk = z / slab;
                     const int zb = (z - rk * slab) * B1;
                     auto row = [&](float *rc) {
+#pragma unroll
                         for (int cy = 0; cy < 3; ++cy) {
-                            const int y = big_ax(st[1], cy, B1, wy);
+                            float *rw = rc + (zb + big_ax(st[1], cy, B1, wy)) * B0;
                             const float wyz = w[2][cz] * w[1][cy];
+#pragma unroll
                             for (int cx = 0; cx < 3; ++cx) {
-                                const int x = big_ax(st[0], cx, B0, wx);
-                                const int idx = (zb + y) * B0 + x;
                                 const float ww = wyz * w[0][cx];
+#pragma unroll
                                 for (int q = 0; q < 3; ++q) {
-                                    if (DET)
-                                        atomicAdd(reinterpret_cast<int *>(rc + q * cap + idx),
-                                                  __float2int_rn((ww * gv[q]) * S));
-                                    else
-                                        atomicAdd(rc + q * cap + idx, ww * gv[q]);
+                                    float *c = rw + q * cap + xs[cx];
+                                    if (DET) atomicAdd(reinterpret_cast<int *>(c), __float2int_rn((ww * gv[q]) * S));
+                                    else atomicAdd(c, ww * gv[q]);
                                 }
                             }
                         }
@@ -2073,13 +2089,16 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
             }
             cl.sync();   // spreading done everywhere
             if (DET) {
+                ucarry = 0.f;
                 for (int i = tid; i < H.ncell; i += kBigT) {
                     if (!((tb[i >> 5] >> (i & 31)) & 1u)) continue;
                     for (int q = 0; q < 3; ++q) {
                         float *c = cells + q * cap + i;
                         const int v = *reinterpret_cast<const int *>(c);
                         if (abs(v) > (1 << 28)) set_err(bp.err, IBM_EBIT_FIXEDPOINT);
-                        *c = (float)v * inv;
+                        const float f = (float)v * inv;
+                        *c = f;
+                        ucarry = fmaxf(ucarry, fabsf(f));
                     }
                 }
                 cl.sync();   // back in FP32 before the next interpolation
@@ -2098,18 +2117,15 @@ __global__ void __launch_bounds__(kBigT, 1) k_big_cluster(BigParams bp) {
                 uw[q * ncs + g] = v;
             }
         }
-        // ---- loads: each particle's markers added in order, FP32 within 32-marker chunks, FP64 across
+        // ---- loads: one warp of the thread-block cluster per (particle, component): each 32-marker
+        // chunk summed in FP32 by the warp, the chunks added in marker order in FP64
         __threadfence();
         cl.sync();
-        if (rank == 0) {
-            for (int j = tid; j < np * 6; j += kBigT) {
-                const int i = j / 6, q = j % 6;
-                double sum = 0.0;
-                for (int c0 = s_pref[i]; c0 < s_pref[i + 1]; c0 += 32) {
-                    float cs = 0.f;
-                    for (int m = c0; m < c0 + 32; ++m) cs += eb[9 * m + 3 + q];
-                    sum += (double)cs;
-                }
+        for (int j = rank * (kBigT / 32) + wid; j < np * 6; j += K * (kBigT / 32)) {
+            const int i = j / 6, q = j - 6 * (j / 6);
+            double sum = 0.0;
+            for (int c0 = s_pref[i]; c0 < s_pref[i + 1]; c0 += 32) sum += (double)warp_sum(eb[9 * (c0 + lane) + 3 + q]);
+            if (lane == 0) {
                 const int p = s_pid[i];
                 if (q < 3) bp.FD[3 * p + q] += sum;
                 else bp.TD[3 * p + q - 3] += sum;
@@ -2213,7 +2229,7 @@ static bool big_config(int *smem_out, int *grid) {
 
 template <int K, bool DET>
 static ibm_status big_launch_t(ibm_ctx *ctx, ClusterScratch *S, BigParams bp, int grid, const int *list, int c_n,
-                               int c_work) {
+                               int c_work, cudaStream_t stream) {
     bp.big_list = list;
     bp.c_n = c_n;
     bp.c_work = c_work;
@@ -2221,7 +2237,7 @@ static ibm_status big_launch_t(ibm_ctx *ctx, ClusterScratch *S, BigParams bp, in
     cfg.gridDim = dim3(K * grid);
     cfg.blockDim = dim3(kBigT);
     cfg.dynamicSmemBytes = (size_t)S->big_smem;
-    cfg.stream = ctx->stream;
+    cfg.stream = stream;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = K;
@@ -2260,8 +2276,16 @@ static ibm_status big_clusters(ibm_ctx *ctx, ClusterScratch *S, float finv, bool
         }
     }
     if (S->big_k == 0) return IBM_OK;
-    // scratch per slot: K * kBigT * kBigKR markers; the two launches run one after the other and share it
-    const size_t mk = std::max((size_t)S->big_grid8 * 8, (size_t)S->big_grid16 * 16) * kBigT * kBigKR;
+    const bool both = S->big_grid8 > 0 && S->big_grid16 > 0;
+    if (both && !S->big_side) {
+        CK(cudaStreamCreateWithFlags(&S->big_side, cudaStreamNonBlocking), "side stream");
+        CK(cudaEventCreateWithFlags(&S->big_fork, cudaEventDisableTiming), "fork event");
+        CK(cudaEventCreateWithFlags(&S->big_join, cudaEventDisableTiming), "join event");
+    }
+    // scratch per slot: K * kBigT * kBigKR markers; the 8-CTA slots first, then the 16-CTA ones
+    // (the two launches run at the same time)
+    const size_t mk8 = (size_t)S->big_grid8 * 8 * kBigT * kBigKR;
+    const size_t mk = mk8 + (size_t)S->big_grid16 * 16 * kBigT * kBigKR;
     const size_t rec = mk * 2 * sizeof(uint4);
     const size_t part = mk * 9 * sizeof(float);
     const size_t wl = mk * sizeof(int);
@@ -2309,12 +2333,30 @@ static ibm_status big_clusters(ibm_ctx *ctx, ClusterScratch *S, float finv, bool
     bp.cap_cells = S->big_cells;
     bp.finv = finv;
     ibm_status st = IBM_OK;
-    if (S->big_grid8)
-        st = det ? big_launch_t<8, true>(ctx, S, bp, S->big_grid8, S->big_list, C_NBIG8, C_WORK8)
-                 : big_launch_t<8, false>(ctx, S, bp, S->big_grid8, S->big_list, C_NBIG8, C_WORK8);
-    if (st == IBM_OK && S->big_grid16)
-        st = det ? big_launch_t<16, true>(ctx, S, bp, S->big_grid16, S->big_list16, C_NBIG16, C_WORK16)
-                 : big_launch_t<16, false>(ctx, S, bp, S->big_grid16, S->big_list16, C_NBIG16, C_WORK16);
+    if (S->big_grid16) {
+        // the larger clusters first (they need 16 free SMs of one GPC), on the side stream when both run
+        BigParams b16 = bp;
+        b16.rec = S->big_rec + 2 * mk8;
+        b16.part = S->big_part + 9 * mk8;
+        b16.wlist = S->big_wl + mk8;
+        cudaStream_t s16 = sm;
+        if (both) {
+            CK(cudaEventRecord(S->big_fork, sm), "fork");
+            CK(cudaStreamWaitEvent(S->big_side, S->big_fork, 0), "fork wait");
+            s16 = S->big_side;
+        }
+        st = det ? big_launch_t<16, true>(ctx, S, b16, S->big_grid16, S->big_list16, C_NBIG16, C_WORK16, s16)
+                 : big_launch_t<16, false>(ctx, S, b16, S->big_grid16, S->big_list16, C_NBIG16, C_WORK16, s16);
+    }
+    if (st == IBM_OK && S->big_grid8)
+        st = det ? big_launch_t<8, true>(ctx, S, bp, S->big_grid8, S->big_list, C_NBIG8, C_WORK8, sm)
+                 : big_launch_t<8, false>(ctx, S, bp, S->big_grid8, S->big_list, C_NBIG8, C_WORK8, sm);
+    if (both) {
+        // join even after a failed launch, so that a stream capture stays well formed
+        const cudaError_t e1 = cudaEventRecord(S->big_join, S->big_side);
+        const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(sm, S->big_join, 0) : e1;
+        if (st == IBM_OK && e2 != cudaSuccess) st = ibm_cuda_check(ctx, e2, "join");
+    }
     if (st != IBM_OK) return st;
     ctx->launches += 2 + (S->big_grid8 > 0) + (S->big_grid16 > 0);
     *fb_list = S->fb_list2;
