@@ -2277,10 +2277,19 @@ static ibm_status big_clusters(ibm_ctx *ctx, ClusterScratch *S, float finv, bool
     }
     if (S->big_k == 0) return IBM_OK;
     const bool both = S->big_grid8 > 0 && S->big_grid16 > 0;
-    if (both && !S->big_side) {
-        CK(cudaStreamCreateWithFlags(&S->big_side, cudaStreamNonBlocking), "side stream");
-        CK(cudaEventCreateWithFlags(&S->big_fork, cudaEventDisableTiming), "fork event");
-        CK(cudaEventCreateWithFlags(&S->big_join, cudaEventDisableTiming), "join event");
+    if (both) {
+        // each made once; one that failed before is tried again on the next step
+        if (!S->big_side) {
+            cudaStream_t st = nullptr;
+            CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "side stream");
+            S->big_side = st;
+        }
+        for (cudaEvent_t *ev : {&S->big_fork, &S->big_join})
+            if (!*ev) {
+                cudaEvent_t e = nullptr;
+                CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "fork/join event");
+                *ev = e;
+            }
     }
     // scratch per slot: K * kBigT * kBigKR markers; the 8-CTA slots first, then the 16-CTA ones
     // (the two launches run at the same time)
